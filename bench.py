@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: density-matrix amplitude-updates per second on the 14-qubit superconducting-grid workload.
+
+Workload: a 2 x 7 grid of transmon-like qubits (n = 14, complex64 state of 2.15 GB), depth-60 brickwork of
+native ZX(pi/2) cross-resonance gates and Rz.SX.Rz layers, static ZZ crosstalk (50 kHz) on idle grid edges,
+T1 log-uniform in 50-200 us with T2 = 0.7 T1 as passive decay after every sublayer, and a 2 % readout flip
+(6494 native ops; seeded synthetic program from workloads.config2_sc_grid).  One step = reset to |0><0|,
+the whole program through the plain unfused kernels (one pass over the state per native op), then the
+FP64 reductions (14-qubit Z-basis probabilities, trace, purity) read back to the host.
+
+Metric: amplitude-updates/s = sum over the program's native ops of 4^n, divided by the time.  The state
+(2.15 GB) is larger than L2 (129 MB), so no L2 flush is needed between steps.
+
+The JSON line also reports the fused path (stages of ops on shared-memory tiles) and the plain FP64
+(complex128) path on a sample of the same program, the roofline of the dominant kernel, the oracle timed
+on the host cores, and the SM clocks sampled during the timed region.
+
+--impl reference times the FP64 numpy oracle on the host cores on a bounded sample of the same workload.
+With --gpus N > 1 every rank runs an independent replica of the workload (the path has no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "density-matrix amplitude-updates/s (sum over native ops of 4^n per second)"
+UNIT = "amp-updates/s"
+WORKLOAD = ("superconducting-like 2x7 grid, 14 qubits, depth-60 ZX(pi/2)+Rz/SX brickwork, ZZ crosstalk 50 kHz, "
+            "T1/T2 idle decay, readout flip 2e-2; complex64 state; plain unfused kernels")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vqd", choices=["vqd", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the fused / FP64 / oracle side measurements")
+    ap.add_argument("--error", action="store_true", help="also measure the complex64 error against an FP64 run")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- oracle (host) timing
+def oracle_rate(prog, n_ops: int):
+    """Time the FP64 numpy oracle on the first n_ops native ops of prog at full size."""
+    from oracle import evolve
+    t = time.perf_counter()
+    evolve.run_program(prog, max_ops=n_ops)
+    dt = time.perf_counter() - t
+    return n_ops * 4.0 ** prog.n / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from workloads import config2_sc_grid
+    prog = config2_sc_grid()
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_rate(prog, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(prog, per_step)
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step * 4.0 ** prog.n / dt
+    cores = os.cpu_count()
+    sample = f"first {per_step} native ops of the 14-qubit program at full size per step (FP64 numpy oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def load_traffic(kernel_class: str):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary, if the kernel source still
+    matches the hash recorded with the counters; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel_class)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2306_07342_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["bytes_per_launch"] if h == rec["source_sha256_16"] else None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2306_07342_gb300 import build as _b
+    if rank == 0:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2306_07342_gb300 import vqd
+    from workloads import config2_sc_grid
+
+    prog = config2_sc_grid()
+    n = prog.n
+    native = vqd.native_ops(prog.ops)
+    units_per_step = len(prog.ops) * 4.0 ** n
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def make_step(ctx, path, ops=native):
+        def step():
+            vqd.vqd_init_zero(ctx, 0)
+            if path == "plain":
+                vqd.vqd_apply_native(ctx, 0, ops)
+            else:
+                vqd.vqd_run_program(ctx, 0, ops)
+            vqd.vqd_prob(ctx, 0, list(range(n)))
+            vqd.vqd_trace(ctx, 0)
+            vqd.vqd_purity(ctx, 0)
+        return step
+
+    def timed(step, steps, warmup, ctx, clocks=None):
+        for _ in range(warmup):
+            step()
+        vqd.vqd_profile(ctx, 0)
+        vqd.vqd_profile_reset(ctx)
+        vqd.vqd_profile(ctx, 2)
+        sync_all()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        stats = vqd.vqd_profile_read(ctx)
+        vqd.vqd_profile(ctx, 0)
+        return ms, stats, ck
+
+    def roofline(stats, steps):
+        kern = {k: v for k, v in stats.items() if k not in ("reduce", "init")}
+        dom = max(kern, key=lambda k: kern[k]["total_ms"])
+        s = kern[dom]
+        per_launch_bytes = s["alg_bytes"] / s["launches"]
+        avg_ms = s["total_ms"] / s["launches"]
+        achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+        total_ms = sum(v["total_ms"] for v in stats.values())
+        return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": load_traffic(dom), "kernel": dom,
+                     "peak_source": peak_src, "launches": s["launches"] // max(1, steps),
+                     "share_of_kernel_time": s["total_ms"] / total_ms if total_ms else None,
+                     "alg_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms}
+
+    # ---- headline: plain complex64 kernels
+    ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
+    clocks = ClockSampler(local)
+    ms, stats, ck = timed(make_step(ctx, "plain"), args.steps, args.warmup, ctx, clocks)
+    value = world * args.steps * units_per_step / (ms * 1e-3)
+    dom, roof = roofline(stats, args.steps)
+    launches = int(sum(v["launches"] for v in stats.values()) / args.steps)
+
+    # ---- end to end through the C ABI with host buffers (wall clock; results read back every step)
+    step = make_step(ctx, "plain")
+    sync_all()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * args.steps * units_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(native.nbytes), "d2h_bytes_per_step": int(8 * 2 ** n + 16 + 8),
+           "note": "wall clock through vqd_init_zero/vqd_apply_native/vqd_prob/vqd_trace/vqd_purity; the native "
+                   "op list is a host array marshalled into kernel parameters; results copied to host every step"}
+
+    extra = {}
+    if not args.no_extra:
+        # ---- fused path, complex64
+        fms, fstats, _ = timed(make_step(ctx, "fused"), args.steps, 1, ctx)
+        fdom, froof = roofline(fstats, args.steps)
+        extra["fused_c64"] = {"value": world * args.steps * units_per_step / (fms * 1e-3), "unit": UNIT,
+                              "ms_per_step": fms / args.steps, "speedup_vs_plain": ms / fms,
+                              "stages_per_step": fstats.get("fused_stage", {}).get("launches", 0) // args.steps,
+                              "roofline": froof}
+    vqd.vqd_destroy(ctx)
+    if not args.no_extra:
+        # ---- plain FP64 (complex128) kernels on the first two layers of the program
+        layer_ops = len(prog.ops) // prog.meta["depth"]
+        sample = native[:2 * layer_ops]
+        ctx64 = vqd.vqd_create(n, vqd.VQD_F64, sh)
+        dms, dstats, _ = timed(make_step(ctx64, "plain", sample), 1, 1, ctx64)
+        ddom, droof = roofline(dstats, 1)
+        kern_ms = sum(v["total_ms"] for k, v in dstats.items() if k not in ("reduce", "init"))
+        fp64_rate = len(sample) * 4.0 ** n / (kern_ms * 1e-3)
+        droof["bound"] = "alu" if ddom in ("sup1", "uni2", "sup2") else "hbm"
+        extra["plain_f64_sample"] = {"value": world * fp64_rate, "unit": UNIT,
+                                     "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
+                                     "roofline_hbm": droof,
+                                     "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
+                                                   for k, v in dstats.items()}}
+        vqd.vqd_destroy(ctx64)
+
+    cpu = None
+    if rank == 0 and not args.no_extra:
+        rate, dt = oracle_rate(prog, 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first 2 native ops of the 14-qubit program at full size, FP64 numpy, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": n, "native_ops": len(prog.ops), "state_bytes": 8 * 4 ** n,
+                       "l2": "inputs larger than L2 (2.15 GB state vs 129 MB L2), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": ck, "paths": extra,
+            "per_class": {k: {"launches": v["launches"] // args.steps, "avg_ms": v["total_ms"] / v["launches"]}
+                          for k, v in stats.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * vqd.h - C ABI of libvqd: density-matrix emulation of a noisy quantum device on one GPU.
+ *
+ * The library evolves an n-qubit density matrix rho through a device's native gates
+ * (rho <- U rho U^dagger) and noise processes (rho <- sum_k K_k rho K_k^dagger), as the
+ * paper's Sec. 2 describes the emulation of a device specification: an ideal circuit is
+ * turned into a sequence of unitary and decohering operators which are applied to the
+ * density matrix.  It ends with Z-basis probabilities, Pauli expectation values, trace
+ * and purity (the quantities reported in Sec. 4-8).
+ *
+ * Conventions (fixed here; the paper leaves them open)
+ *   - Qubit q is bit q of a basis index (little-endian).
+ *   - Matrices are row-major FP64 complex (vqd_c128).  For an operation on
+ *     targets[0..k-1], the 2^k x 2^k matrix index is little-endian over targets:
+ *     targets[0] is its least significant bit.
+ *   - Superoperators are 4^k x 4^k, index s = r | (c << k) where r / c are the row /
+ *     column indices of the k-qubit block; S = sum_k conj(K_k) (x) K_k (conj factor on
+ *     the high, column part).
+ *   - The state of an n-qubit instance is 4^n amplitudes, amplitude rho[r][c] at index
+ *     r + (c << n) (column-major vectorisation).  vqd_get_state / vqd_set_state use this
+ *     layout.
+ *   - Rotations R_s(theta) = exp(-i theta s / 2); SX = Rx(pi/2).
+ *
+ * Precision: VQD_F64 stores complex128 and computes in FP64.  VQD_F32 stores complex64 and
+ * computes in FP32.  Operators are always composed on the host in FP64; every reduction
+ * (probabilities, expectation values, trace, purity) accumulates in FP64.
+ *
+ * Errors: every int-returning call returns 0 (VQD_OK) or a negative VQD_E* code and never
+ * throws.  vqd_last_error(ctx) gives a human-readable message (ctx may be NULL for errors
+ * raised before a context exists).  After VQD_EDEVICE the context should be destroyed.
+ *
+ * Ownership and streams: the caller owns every host array; each call copies what it needs
+ * before returning.  Apply / init / run calls are asynchronous on the context's CUDA stream;
+ * reductions and get_state synchronise that stream.  A context is not thread-safe.
+ */
+#ifndef VQD_H
+#define VQD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VQD_OK 0
+#define VQD_EINVAL (-1)  /* bad argument: k, target out of range or repeated, n too large, bad op code */
+#define VQD_ENOMEM (-2)  /* device or host allocation failed */
+#define VQD_ENOTCP (-3)  /* matrix is not unitary / Kraus set not trace non-increasing (tol 1e-10) */
+#define VQD_EDEVICE (-4) /* CUDA error (message in vqd_last_error) */
+#define VQD_ENOTSUP (-5) /* operation not supported in this configuration */
+
+typedef enum { VQD_F64 = 0, VQD_F32 = 1 } vqd_prec;
+
+typedef struct {
+  double re, im;
+} vqd_c128;
+
+typedef struct vqd_ctx* vqd_t;
+
+/* Largest qubit count of one instance (4^16 amplitudes: 68.7 GB complex128, 34.4 GB complex64). */
+#define VQD_MAX_QUBITS 16
+
+/* ------------------------------------------------------------------------------------------
+ * Native operations: the device vocabulary compiled by the library's device compiler.
+ * Parameters: angles in radians, durations in microseconds, frequencies in MHz.
+ * The numeric codes are part of the ABI.
+ * ---------------------------------------------------------------------------------------- */
+typedef enum {
+  /* native gates (unitaries) */
+  VQD_OP_RX = 0,        /* q0; theta                                                          */
+  VQD_OP_RY = 1,        /* q0; theta                                                          */
+  VQD_OP_RZ = 2,        /* q0; theta (virtual Z of Sec. 8 is still a unitary here)            */
+  VQD_OP_SX = 3,        /* q0; sqrt(X) := Rx(pi/2)                                            */
+  VQD_OP_H = 4,         /* q0; Hadamard                                                       */
+  VQD_OP_U = 5,         /* q0; phi, Omega, Delta, t: Raman U(phi, Delta, t), Sec. 6 Eq. (u)    */
+  VQD_OP_R = 6,         /* q0; theta, phi: Eq. (u) with Delta = 0, Omega t = theta            */
+  VQD_OP_CZ = 7,        /* q0,q1                                                              */
+  VQD_OP_CPH = 8,       /* q0,q1; phi: diag(1,1,1,e^{i phi}), Sec. 7                          */
+  VQD_OP_CZPHI = 9,     /* q0,q1; phi: Rydberg CZ(phi) = diag(1,e^{i phi},e^{i phi},e^{i(2phi-pi)}), Sec. 6 */
+  VQD_OP_ZX = 10,       /* q0 = control, q1 = target; theta: exp(-i theta/2 Z X), Sec. 8      */
+  VQD_OP_ZZ = 11,       /* q0,q1; theta: exp(-i theta/2 Z Z), Sec. 8                          */
+  VQD_OP_XX = 12,       /* q0,q1; theta: Molmer-Sorensen exp(-i theta/2 X X), Sec. 4           */
+  VQD_OP_ZZPHASE = 13,  /* q0,q1; alpha: exp(-i alpha Z Z), Sec. 3.4 Eq. (weak_dephasing_zz)   */
+  VQD_OP_ZZ_IDLE = 14,  /* q0,q1; dt, xi: static ZZ crosstalk, alpha = pi xi dt / 2            */
+  VQD_OP_CRZ_XTALK = 15,/* q0 = control, q1; alpha: conditional Rz, Eq. (weak_dephasing)       */
+  VQD_OP_EXCHANGE = 16, /* q0,q1; theta: exp(-i (XX+YY+ZZ) theta/4), Eq. (exchange_pauli)      */
+  /* noise processes (Kraus channels) */
+  VQD_OP_DEPOL1 = 17,   /* q0; p in [0,3/4], Eq. (depol1)                                     */
+  VQD_OP_DEPOL2 = 18,   /* q0,q1; p in [0,15/16], Eq. (depol2): p/15 on each of 15 Paulis      */
+  VQD_OP_DEPH1 = 19,    /* q0; p in [0,1/2], Eq. (deph1)                                      */
+  VQD_OP_DEPH2 = 20,    /* q0,q1; p in [0,3/4], Eq. (deph2)                                   */
+  VQD_OP_AMP = 21,      /* q0; p in [0,1], Eq. (damp)                                         */
+  VQD_OP_BITFLIP = 22,  /* q0; b in [0,1/2], Eq. (bf)                                         */
+  VQD_OP_BITFLIP2 = 23, /* q0,q1; b in [0,3/4], Eq. (bf2)                                     */
+  VQD_OP_GAMP = 24,     /* q0; dt, T1, p0: generalised damping, Eq. (gdamp)                   */
+  VQD_OP_IDLE = 25,     /* q0; dt, T1, T2: amp(1-e^{-dt/T1}) then deph(1/2(1-e^{-dt/T2})), Eqs. (ampt1),(depht2) */
+  VQD_OP_IDLE_DEPOL = 26,/* q0; dt, T1, T2: depol(3/4(1-e^{-dt/T1})) then the T2 dephasing, Eq. (depolt1) */
+  VQD_OP_STDERR1 = 27,  /* q0; Fbar, x: deph(p) o depol(q) from the average fidelity, App. B   */
+  VQD_OP_STDERR2 = 28,  /* q0,q1; Fbar, x: two-qubit standard error, App. B                   */
+  VQD_OP_AMPDEPH2 = 29, /* q0,q1; dt, T1, T2: the T1/T2 decay of both qubits as one 2-qubit channel */
+  VQD_OP_LEAK_INIT = 30,/* q0; gamma: CPTN L = diag(sqrt(1-gamma), 1), Sec. 6                 */
+  VQD_OP_LEAK_CZ = 31,  /* q0,q1; alpha, beta: CPTN K of Eq. (czleak)                          */
+  VQD_OP_COUNT = 32
+} vqd_op_code;
+
+typedef struct {
+  int32_t code;   /* vqd_op_code */
+  int32_t nq;     /* number of qubits (must match the code) */
+  int32_t q[2];   /* target qubits, q[0] = least significant bit of the matrix index */
+  double par[4];  /* parameters in the order listed above; unused entries ignored */
+} vqd_native_op;  /* 48 bytes */
+
+/* Flags for compilation and run calls (bitwise or). */
+#define VQD_T2_IS_TOTAL 1u  /* read T2 as the total coherence time: dephase with T_phi, 1/T2 = 1/(2T1) + 1/T_phi */
+#define VQD_NO_CHECK 2u     /* skip the unitarity / CPTN checks of apply_unitary / apply_kraus */
+
+/* ------------------------------------------------------------------------------------------
+ * Contexts and states
+ * ---------------------------------------------------------------------------------------- */
+
+/* Bytes of device memory one n-qubit state occupies in precision prec. */
+size_t vqd_state_bytes(int n, int prec);
+
+/* One n-qubit state (1 <= n <= VQD_MAX_QUBITS) in library-allocated device memory, initialised
+ * to |0..0><0..0|.  stream is a cudaStream_t (NULL = legacy default stream).  The library owns
+ * the memory; vqd_destroy frees it. */
+int vqd_create(int n, int prec, void* stream, vqd_t* out);
+
+/* count independent instances (n[i] qubits each, 1..VQD_MAX_QUBITS) packed in one allocation;
+ * every call that takes `inst` addresses one of them.  All start in |0..0><0..0|. */
+int vqd_create_batch(int count, const int* n, int prec, void* stream, vqd_t* out);
+
+/* One n-qubit state living in caller-owned device memory `dev_state` (>= vqd_state_bytes(n,prec)
+ * bytes, 16-byte aligned), e.g. a torch tensor.  The state is NOT initialised; the caller keeps
+ * the memory alive until vqd_destroy. */
+int vqd_create_on(int n, int prec, void* dev_state, size_t bytes, void* stream, vqd_t* out);
+
+void vqd_destroy(vqd_t ctx);
+int vqd_num_instances(vqd_t ctx);
+int vqd_num_qubits(vqd_t ctx, int inst);
+/* Device address of instance inst's amplitudes (layout above). */
+void* vqd_state_ptr(vqd_t ctx, int inst);
+int vqd_sync(vqd_t ctx);
+const char* vqd_last_error(vqd_t ctx);
+
+/* Initial states (asynchronous). */
+int vqd_init_zero(vqd_t ctx, int inst);                       /* |0..0><0..0|                    */
+int vqd_init_classical(vqd_t ctx, int inst, uint64_t basis);  /* |x><x|, x < 2^n                 */
+/* Thermal product state of Sec. 8 Eq. (thermalstate): (x)_j ((1-e_j)|0><0| + e_j|1><1|) where
+ * e_j = excited[j] in [0,1] is qubit j's excited population. */
+int vqd_init_product_diag(vqd_t ctx, int inst, const double* excited);
+
+/* ------------------------------------------------------------------------------------------
+ * Applying operators (asynchronous; one pass over the state per call)
+ * ---------------------------------------------------------------------------------------- */
+
+/* rho <- U rho U^dagger, U is 2^k x 2^k (k = 1 or 2) on distinct targets.  ENOTCP if U is not
+ * unitary within 1e-10 (unless VQD_NO_CHECK is set with vqd_set_flags). */
+int vqd_apply_unitary(vqd_t ctx, int inst, int k, const int* targets, const vqd_c128* U);
+
+/* rho <- sum_j K_j rho K_j^dagger, nK operators of 2^k x 2^k stored one after another
+ * (general Kraus map, Sec. 2).  ENOTCP if sum_j K_j^dagger K_j exceeds I by more than 1e-10
+ * (CPTN maps such as the leakage operators of Sec. 6 are accepted). */
+int vqd_apply_kraus(vqd_t ctx, int inst, int k, const int* targets, int nK, const vqd_c128* K);
+
+/* vec-group <- S vec-group with the 4^k x 4^k superoperator S (index convention above);
+ * no positivity check. */
+int vqd_apply_superop(vqd_t ctx, int inst, int k, const int* targets, const vqd_c128* S);
+
+/* Compile each native op with the device compiler and apply it with one pass over the state
+ * (the plain, unfused path).  flags: VQD_T2_IS_TOTAL. */
+int vqd_apply_native(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, unsigned flags);
+
+/* Same result as vqd_apply_native, through the fused path: consecutive ops are grouped into
+ * stages acting on at most `fuse_qubits` qubits (2..VQD_MAX_FUSE); each stage is one pass over
+ * the state in which the stage's tiles are staged in shared memory and all of its ops are
+ * applied there.  fuse_qubits <= 0 picks the library default. */
+#define VQD_MAX_FUSE 6
+int vqd_run_program(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags);
+
+/* Batched path: instance i of a batch context runs ops[offsets[i] .. offsets[i+1]) (native ops),
+ * all instances in ONE persistent kernel launch (each CTA takes whole instances from a queue,
+ * largest first).  offsets has count+1 entries. */
+int vqd_run_batch(vqd_t ctx, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags);
+
+/* ------------------------------------------------------------------------------------------
+ * Device compiler (host only, no GPU needed)
+ * ---------------------------------------------------------------------------------------- */
+
+/* Compile one native op.  On return *is_unitary says which form `mat` holds: the 2^k x 2^k
+ * unitary (is_unitary = 1, 4^k entries used) or the 4^k x 4^k superoperator of the channel
+ * (is_unitary = 0, 16^k entries used).  `mat` must hold 256 entries.  targets receives the k
+ * qubits. */
+int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int* k, int* targets,
+                   vqd_c128* mat);
+
+/* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
+ * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
+int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);
+
+/* ------------------------------------------------------------------------------------------
+ * Reductions (synchronous; FP64 accumulation, fixed summation order)
+ * ---------------------------------------------------------------------------------------- */
+
+/* Marginal Z-basis probabilities of qubits[0..m-1] (distinct; m <= n, 2^m outputs):
+ * out[v] = sum of Re rho[x][x] over basis states x whose bits on qubits spell v (qubits[0]
+ * = least significant bit of v). */
+int vqd_prob(vqd_t ctx, int inst, int m, const int* qubits, double* out);
+
+/* *out = Re sum_t coeffs[t] tr(P_t rho); paulis is nterms x n bytes, paulis[t*n + q] in
+ * {0=I, 1=X, 2=Y, 3=Z} is the factor on qubit q. */
+int vqd_expect(vqd_t ctx, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out);
+
+/* tr rho (not renormalised: trace-decreasing leakage channels leave it below 1). */
+int vqd_trace(vqd_t ctx, int inst, double* re_out, double* im_out);
+
+/* tr(rho^dagger rho) = sum |rho_ij|^2 (equals tr rho^2 for Hermitian rho). */
+int vqd_purity(vqd_t ctx, int inst, double* out);
+
+/* Copy instance inst to / from host, FP64 complex, layout above (4^n entries). */
+int vqd_get_state(vqd_t ctx, int inst, vqd_c128* host_out);
+int vqd_set_state(vqd_t ctx, int inst, const vqd_c128* host_in);
+
+/* ------------------------------------------------------------------------------------------
+ * Launch accounting: per kernel class, the number of launches, their summed device time
+ * (CUDA events recorded on the context stream around every launch while enabled) and the
+ * algorithmic bytes they move.  Used to report achieved bandwidth against the roofline.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+  char name[32];       /* kernel class */
+  int64_t launches;
+  double total_ms;     /* summed CUDA-event durations (0 unless timing was enabled) */
+  double alg_bytes;    /* algorithmic bytes: 2 x state bytes per pass (read + write once) */
+  double amp_updates;  /* sum over original (pre-fusion) ops of the amplitudes they update */
+} vqd_kstat;
+
+/* mode 0: off; 1: count launches only; 2: count and time every launch with CUDA events. */
+int vqd_profile(vqd_t ctx, int mode);
+int vqd_profile_reset(vqd_t ctx);
+int vqd_profile_read(vqd_t ctx, int max, vqd_kstat* out, int* n_out);
+
+/* Global flags for the checks of apply_unitary / apply_kraus (VQD_NO_CHECK). */
+int vqd_set_flags(vqd_t ctx, unsigned flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VQD_H */

@@ -88,6 +88,29 @@ def apply_unitary(rho: np.ndarray, qubits: Sequence[int], U: np.ndarray, method:
     return apply_kraus(rho, qubits, [U], method)
 
 
+def apply_superop(rho: np.ndarray, qubits: Sequence[int], S: np.ndarray) -> np.ndarray:
+    """Apply a k-qubit superoperator S (4^k x 4^k, index s = r | c << k over the target bits) by its
+    definition: for every assignment of the other row and column bits, the 4^k amplitudes
+    rho[r, c] spanned by the target bits are replaced by S times them."""
+    n = int(round(np.log2(rho.shape[0])))
+    k = len(qubits)
+    dim = 2 ** n
+    mask = sum(1 << q for q in qubits)
+    out = np.empty_like(rho)
+    offs = [sum(((s >> j) & 1) << q for j, q in enumerate(qubits)) for s in range(2 ** k)]
+    rbase = [r for r in range(dim) if not (r & mask)]
+    rr = np.array([[rb | o for o in offs] for rb in rbase])          # (groups, 2^k) row indices
+    for cb in rbase:
+        cc = [cb | o for o in offs]
+        # group vector g[s] with s = r | c << k
+        g = np.stack([rho[rr[:, r], cc[c]] for c in range(2 ** k) for r in range(2 ** k)], axis=1)
+        h = g @ S.T
+        for c in range(2 ** k):
+            for r in range(2 ** k):
+                out[rr[:, r], cc[c]] = h[:, r | (c << k)]
+    return out
+
+
 def embed(M: np.ndarray, qubits: Sequence[int], n: int) -> np.ndarray:
     """Full 2^n x 2^n operator acting as M on ``qubits`` and as identity elsewhere.
 

@@ -1,0 +1,586 @@
+// C ABI of libvqd (declared in include/vqd.h): contexts, argument checks, launch accounting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fused.h"
+#include "kernels.h"
+#include "vqd_internal.h"
+
+using namespace vqd;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct KClass {
+  const char* name;
+};
+enum StatClass { SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2, SC_FUSED, SC_BATCH, SC_REDUCE, SC_INIT, SC_COUNT };
+const char* kStatNames[SC_COUNT] = {"elem", "sup1", "uni2", "sup2", "fused_stage", "batch", "reduce", "init"};
+
+struct Stat {
+  int64_t launches = 0;
+  double ms = 0, bytes = 0, amp_updates = 0;
+};
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();  // clear a sticky-free error so later calls can report their own
+  throw Error(e == cudaErrorMemoryAllocation ? VQD_ENOMEM : VQD_EDEVICE,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct vqd_ctx {
+  int prec = VQD_F64;
+  size_t esize = 16;
+  std::vector<int> n;
+  std::vector<size_t> off;  // byte offset of each instance
+  char* base = nullptr;
+  bool owns = false;
+  size_t total = 0;
+  cudaStream_t stream = nullptr;
+  double* d_scratch = nullptr;
+  double* d_out = nullptr;
+  double* h_out = nullptr;
+  std::string err;
+  unsigned flags = 0;
+  // launch accounting
+  int prof = 0;
+  Stat stats[SC_COUNT];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpool;
+  std::vector<int> pending;  // class of the launch timed by evpool[i]
+  FusedCache fused;          // device buffers reused by the fused and batched paths
+
+  char* ptr(int inst) { return base + off[inst]; }
+  size_t bytes(int inst) const { return vqd_state_bytes(n[inst], prec); }
+};
+
+static void set_err(vqd_ctx* c, const std::string& m) {
+  if (c) c->err = m;
+  g_err = m;
+}
+
+#define API_BEGIN try {
+#define API_END(ctx)                                   \
+  }                                                    \
+  catch (const Error& e) {                             \
+    set_err(ctx, e.what());                            \
+    return e.code;                                     \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    set_err(ctx, "host allocation failed");            \
+    return VQD_ENOMEM;                                 \
+  }                                                    \
+  catch (const std::exception& e) {                    \
+    set_err(ctx, e.what());                            \
+    return VQD_EINVAL;                                 \
+  }                                                    \
+  return VQD_OK;
+
+static void harvest(vqd_ctx* c) {
+  if (c->pending.empty()) return;
+  cuda_check(cudaStreamSynchronize(c->stream), "synchronise for timing");
+  for (size_t i = 0; i < c->pending.size(); i++) {
+    float ms = 0;
+    cuda_check(cudaEventElapsedTime(&ms, c->evpool[i].first, c->evpool[i].second), "event timing");
+    c->stats[c->pending[i]].ms += ms;
+  }
+  c->pending.clear();
+}
+
+// Run `launch` (which enqueues kernels on c->stream) with launch accounting for class `cls`.
+template <class F>
+static void timed(vqd_ctx* c, int cls, double bytes, double amp_updates, int64_t launches, F&& launch) {
+  if (c->prof == 2) {
+    if (c->pending.size() >= 4096) harvest(c);
+    size_t i = c->pending.size();
+    if (i >= c->evpool.size()) {
+      cudaEvent_t a, b;
+      cuda_check(cudaEventCreate(&a), "event create");
+      cuda_check(cudaEventCreate(&b), "event create");
+      c->evpool.emplace_back(a, b);
+    }
+    cuda_check(cudaEventRecord(c->evpool[i].first, c->stream), "event record");
+    cuda_check(launch(), kStatNames[cls]);
+    cuda_check(cudaEventRecord(c->evpool[i].second, c->stream), "event record");
+    c->pending.push_back(cls);
+  } else {
+    cuda_check(launch(), kStatNames[cls]);
+  }
+  if (c->prof) {
+    Stat& s = c->stats[cls];
+    s.launches += launches;
+    s.bytes += bytes;
+    s.amp_updates += amp_updates;
+  }
+}
+
+static vqd_ctx* need_ctx(vqd_t c) {
+  if (!c) throw Error(VQD_EINVAL, "NULL context");
+  return c;
+}
+static void need_inst(vqd_ctx* c, int inst) {
+  if (inst < 0 || inst >= (int)c->n.size()) throw Error(VQD_EINVAL, "instance index out of range");
+}
+static void need_targets(vqd_ctx* c, int inst, int k, const int* t) {
+  if (k < 1 || k > 2) throw Error(VQD_EINVAL, "k must be 1 or 2");
+  if (!t) throw Error(VQD_EINVAL, "NULL targets");
+  for (int j = 0; j < k; j++) {
+    if (t[j] < 0 || t[j] >= c->n[inst]) throw Error(VQD_EINVAL, "target qubit out of range");
+    for (int i = 0; i < j; i++)
+      if (t[i] == t[j]) throw Error(VQD_EINVAL, "repeated target qubit");
+  }
+}
+
+static void apply_op(vqd_ctx* c, int inst, const Op& op) {
+  Pass p = classify(op);
+  const int n = c->n[inst];
+  static const int cls_of[4] = {SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2};
+  timed(c, cls_of[p.kind], 2.0 * c->bytes(inst), op.weight * std::ldexp(1.0, 2 * n), 1,
+        [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
+}
+
+static std::vector<cd> to_cd(const vqd_c128* m, size_t cnt) {
+  std::vector<cd> v(cnt);
+  for (size_t i = 0; i < cnt; i++) v[i] = cd(m[i].re, m[i].im);
+  return v;
+}
+
+static void alloc_aux(vqd_ctx* c) {
+  cuda_check(cudaMalloc(&c->d_scratch, sizeof(double) * reduce_scratch_doubles()), "scratch allocation");
+  cuda_check(cudaMalloc(&c->d_out, sizeof(double) * reduce_out_doubles()), "result allocation");
+  cuda_check(cudaMallocHost(&c->h_out, sizeof(double) * reduce_out_doubles()), "pinned result allocation");
+}
+
+static void free_ctx(vqd_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& e : c->evpool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  fused_cache_free(c->fused);
+  if (c->owns && c->base) cudaFree(c->base);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->d_out) cudaFree(c->d_out);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  delete c;
+}
+
+static vqd_ctx* make_ctx(int count, const int* n, int prec, void* stream, void* dev, size_t dev_bytes) {
+  if (prec != VQD_F64 && prec != VQD_F32) throw Error(VQD_EINVAL, "precision must be VQD_F64 or VQD_F32");
+  if (count < 1) throw Error(VQD_EINVAL, "count must be >= 1");
+  std::unique_ptr<vqd_ctx, void (*)(vqd_ctx*)> c(new vqd_ctx, free_ctx);
+  c->prec = prec;
+  c->esize = prec == VQD_F32 ? 8 : 16;
+  c->stream = (cudaStream_t)stream;
+  size_t total = 0;
+  for (int i = 0; i < count; i++) {
+    if (n[i] < 1 || n[i] > VQD_MAX_QUBITS) throw Error(VQD_EINVAL, "qubit count outside 1..16");
+    c->n.push_back(n[i]);
+    c->off.push_back(total);
+    total += (vqd_state_bytes(n[i], prec) + 255) / 256 * 256;
+  }
+  c->total = total;
+  if (dev) {
+    if (dev_bytes < vqd_state_bytes(n[0], prec)) throw Error(VQD_EINVAL, "device buffer too small");
+    if ((uintptr_t)dev % 16) throw Error(VQD_EINVAL, "device buffer must be 16-byte aligned");
+    c->base = (char*)dev;
+    c->owns = false;
+  } else {
+    cuda_check(cudaMalloc(&c->base, total), "state allocation");
+    c->owns = true;
+  }
+  alloc_aux(c.get());
+  return c.release();
+}
+
+// ================================================================== exported API
+extern "C" {
+
+size_t vqd_state_bytes(int n, int prec) {
+  if (n < 1 || n > VQD_MAX_QUBITS) return 0;
+  return (size_t)(prec == VQD_F32 ? 8 : 16) << (2 * n);
+}
+
+int vqd_create(int n, int prec, void* stream, vqd_t* out) {
+  vqd_ctx* c = nullptr;
+  API_BEGIN
+  if (!out) throw Error(VQD_EINVAL, "NULL output handle");
+  *out = nullptr;
+  c = make_ctx(1, &n, prec, stream, nullptr, 0);
+  cuda_check(launch_init_classical(c->prec, c->ptr(0), n, 0, c->stream), "init");
+  *out = c;
+  API_END(nullptr)
+}
+
+int vqd_create_batch(int count, const int* n, int prec, void* stream, vqd_t* out) {
+  API_BEGIN
+  if (!out || !n) throw Error(VQD_EINVAL, "NULL argument");
+  *out = nullptr;
+  vqd_ctx* c = make_ctx(count, n, prec, stream, nullptr, 0);
+  for (int i = 0; i < count; i++) cuda_check(launch_init_classical(c->prec, c->ptr(i), n[i], 0, c->stream), "init");
+  *out = c;
+  API_END(nullptr)
+}
+
+int vqd_create_on(int n, int prec, void* dev_state, size_t bytes, void* stream, vqd_t* out) {
+  API_BEGIN
+  if (!out || !dev_state) throw Error(VQD_EINVAL, "NULL argument");
+  *out = nullptr;
+  *out = make_ctx(1, &n, prec, stream, dev_state, bytes);
+  API_END(nullptr)
+}
+
+void vqd_destroy(vqd_t c) { free_ctx(c); }
+
+int vqd_num_instances(vqd_t c) { return c ? (int)c->n.size() : VQD_EINVAL; }
+int vqd_num_qubits(vqd_t c, int inst) {
+  if (!c || inst < 0 || inst >= (int)c->n.size()) return VQD_EINVAL;
+  return c->n[inst];
+}
+void* vqd_state_ptr(vqd_t c, int inst) {
+  if (!c || inst < 0 || inst >= (int)c->n.size()) return nullptr;
+  return c->ptr(inst);
+}
+
+int vqd_sync(vqd_t c) {
+  API_BEGIN
+  need_ctx(c);
+  cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  API_END(c)
+}
+
+const char* vqd_last_error(vqd_t c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+int vqd_set_flags(vqd_t c, unsigned flags) {
+  API_BEGIN
+  need_ctx(c)->flags = flags;
+  API_END(c)
+}
+
+int vqd_init_zero(vqd_t c, int inst) { return vqd_init_classical(c, inst, 0); }
+
+int vqd_init_classical(vqd_t c, int inst, uint64_t basis) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (basis >= (1ull << c->n[inst])) throw Error(VQD_EINVAL, "basis state out of range");
+  timed(c, SC_INIT, (double)c->bytes(inst), 0, 1,
+        [&] { return launch_init_classical(c->prec, c->ptr(inst), c->n[inst], basis, c->stream); });
+  API_END(c)
+}
+
+int vqd_init_product_diag(vqd_t c, int inst, const double* e) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (!e) throw Error(VQD_EINVAL, "NULL populations");
+  for (int q = 0; q < c->n[inst]; q++)
+    if (!(e[q] >= 0 && e[q] <= 1)) throw Error(VQD_EINVAL, "excited population outside [0,1]");
+  timed(c, SC_INIT, (double)c->bytes(inst), 0, 1,
+        [&] { return launch_init_product_diag(c->prec, c->ptr(inst), c->n[inst], e, c->stream); });
+  API_END(c)
+}
+
+int vqd_apply_unitary(vqd_t c, int inst, int k, const int* t, const vqd_c128* U) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  need_targets(c, inst, k, t);
+  if (!U) throw Error(VQD_EINVAL, "NULL matrix");
+  Op op;
+  op.unitary = true;
+  op.k = k;
+  for (int j = 0; j < k; j++) op.q[j] = t[j];
+  op.m = to_cd(U, (size_t)1 << (2 * k));
+  if (!(c->flags & VQD_NO_CHECK)) check_unitary(k, op.m.data());
+  apply_op(c, inst, op);
+  API_END(c)
+}
+
+int vqd_apply_kraus(vqd_t c, int inst, int k, const int* t, int nK, const vqd_c128* K) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  need_targets(c, inst, k, t);
+  if (!K || nK < 1 || nK > 1024) throw Error(VQD_EINVAL, "need 1..1024 Kraus operators");
+  std::vector<cd> ks = to_cd(K, (size_t)nK << (2 * k));
+  if (!(c->flags & VQD_NO_CHECK)) check_cptn(k, nK, ks.data());
+  Op op;
+  op.unitary = false;
+  op.k = k;
+  for (int j = 0; j < k; j++) op.q[j] = t[j];
+  op.m = superop_from_kraus(k, nK, ks.data());
+  apply_op(c, inst, op);
+  API_END(c)
+}
+
+int vqd_apply_superop(vqd_t c, int inst, int k, const int* t, const vqd_c128* S) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  need_targets(c, inst, k, t);
+  if (!S) throw Error(VQD_EINVAL, "NULL matrix");
+  Op op;
+  op.unitary = false;
+  op.k = k;
+  for (int j = 0; j < k; j++) op.q[j] = t[j];
+  op.m = to_cd(S, (size_t)1 << (4 * k));
+  apply_op(c, inst, op);
+  API_END(c)
+}
+
+static std::vector<Op> compile_list(vqd_ctx* c, int inst, int nops, const vqd_native_op* ops, unsigned flags) {
+  if (nops < 0 || (nops > 0 && !ops)) throw Error(VQD_EINVAL, "bad op list");
+  std::vector<Op> out;
+  out.reserve(nops);
+  for (int i = 0; i < nops; i++) {
+    int ar = native_arity(ops[i].code);
+    if (ar < 1) throw Error(VQD_EINVAL, "unknown native op code at index " + std::to_string(i));
+    need_targets(c, inst, ar, ops[i].q);
+    out.push_back(compile_native(ops[i], flags));
+  }
+  return out;
+}
+
+int vqd_apply_native(vqd_t c, int inst, int nops, const vqd_native_op* ops, unsigned flags) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  std::vector<Op> list = compile_list(c, inst, nops, ops, flags);
+  for (const Op& op : list) apply_op(c, inst, op);
+  API_END(c)
+}
+
+int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  std::vector<Op> list = compile_list(c, inst, nops, ops, flags);
+  const int n = c->n[inst];
+  FusedPlan plan = plan_fused(list, n, c->prec, fuse_qubits);
+  upload_plan(c->fused, plan, c->prec, c->stream);
+  for (size_t s = 0; s < plan.stages.size(); s++) {
+    timed(c, SC_FUSED, 2.0 * c->bytes(inst), plan.stages[s].weight * std::ldexp(1.0, 2 * n), 1,
+          [&] { return launch_stage(c->fused, plan, (int)s, c->prec, c->ptr(inst), n, c->stream); });
+  }
+  API_END(c)
+}
+
+int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags) {
+  API_BEGIN
+  need_ctx(c);
+  if (!offsets) throw Error(VQD_EINVAL, "NULL offsets");
+  const int count = (int)c->n.size();
+  std::vector<std::vector<Op>> lists(count);
+  for (int i = 0; i < count; i++) {
+    if (offsets[i + 1] < offsets[i]) throw Error(VQD_EINVAL, "offsets must be non-decreasing");
+    lists[i] = compile_list(c, i, (int)(offsets[i + 1] - offsets[i]), ops + offsets[i], flags);
+  }
+  BatchPlan plan = plan_batch(lists, c->n, c->off, c->prec, fuse_qubits);
+  upload_batch(c->fused, plan, c->prec, c->stream);
+  double bytes = 0, upd = 0;
+  for (int i = 0; i < count; i++) {
+    bytes += 2.0 * c->bytes(i) * plan.passes[i];
+    upd += (double)lists[i].size() * std::ldexp(1.0, 2 * c->n[i]);
+  }
+  timed(c, SC_BATCH, bytes, upd, 1, [&] { return launch_batch(c->fused, plan, c->prec, c->base, c->stream); });
+  cuda_check(batch_status(c->fused, c->stream), "batched kernel");
+  API_END(c)
+}
+
+int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int* k, int* targets, vqd_c128* mat) {
+  API_BEGIN
+  if (!op || !is_unitary || !k || !targets || !mat) throw Error(VQD_EINVAL, "NULL argument");
+  Op o = compile_native(*op, flags);
+  *is_unitary = o.unitary ? 1 : 0;
+  *k = o.k;
+  for (int j = 0; j < o.k; j++) targets[j] = o.q[j];
+  for (size_t i = 0; i < o.m.size(); i++) mat[i] = {o.m[i].real(), o.m[i].imag()};
+  API_END(nullptr)
+}
+
+int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
+  API_BEGIN
+  if (!p || !q) throw Error(VQD_EINVAL, "NULL output");
+  stderr_params(nq, fbar, x, p, q);
+  API_END(nullptr)
+}
+
+static void fetch(vqd_ctx* c, size_t cnt) {
+  cuda_check(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream), "D2H result");
+  cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+}
+
+int vqd_prob(vqd_t c, int inst, int m, const int* qubits, double* out) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  const int n = c->n[inst];
+  if (m < 1 || m > n || !qubits || !out) throw Error(VQD_EINVAL, "bad qubit list");
+  unsigned used = 0;
+  for (int j = 0; j < m; j++) {
+    if (qubits[j] < 0 || qubits[j] >= n || (used >> qubits[j] & 1)) throw Error(VQD_EINVAL, "bad or repeated qubit");
+    used |= 1u << qubits[j];
+  }
+  timed(c, SC_REDUCE, std::ldexp(1.0, n) * c->esize, 0, 2,
+        [&] { return launch_prob(c->prec, c->ptr(inst), n, m, qubits, c->d_scratch, c->d_out, c->stream); });
+  fetch(c, (size_t)1 << m);
+  std::memcpy(out, c->h_out, sizeof(double) << m);
+  API_END(c)
+}
+
+int vqd_expect(vqd_t c, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (nterms < 0 || (nterms > 0 && (!paulis || !coeffs)) || !out) throw Error(VQD_EINVAL, "bad Pauli sum");
+  const int n = c->n[inst];
+  double total = 0;
+  for (int t0 = 0; t0 < nterms; t0 += kExpectTermsPerLaunch) {
+    int cnt = std::min(kExpectTermsPerLaunch, nterms - t0);
+    std::vector<uint32_t> xm(cnt), zy(cnt);
+    std::vector<int> ny(cnt);
+    for (int t = 0; t < cnt; t++) {
+      uint32_t x = 0, z = 0;
+      int y = 0;
+      for (int q = 0; q < n; q++) {
+        uint8_t s = paulis[(size_t)(t0 + t) * n + q];
+        if (s > 3) throw Error(VQD_EINVAL, "Pauli code must be 0..3");
+        if (s == 1 || s == 2) x |= 1u << q;
+        if (s == 2 || s == 3) z |= 1u << q;
+        if (s == 2) y++;
+      }
+      xm[t] = x;
+      zy[t] = z;
+      ny[t] = y;
+    }
+    timed(c, SC_REDUCE, cnt * std::ldexp(1.0, n) * c->esize, 0, 3, [&] {
+      return launch_expect(c->prec, c->ptr(inst), n, cnt, xm.data(), zy.data(), c->d_scratch, c->d_out, c->stream);
+    });
+    fetch(c, 2 * (size_t)cnt);
+    // P|c> = i^{#Y} (-1)^{popc(c & zy)} |c ^ x>, so tr(P rho) = i^{#Y} sum_c (-1)^{...} rho[c][c ^ x]
+    for (int t = 0; t < cnt; t++) {
+      cd s(c->h_out[t], c->h_out[cnt + t]);
+      static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+      total += coeffs[t0 + t] * (ipow[ny[t] & 3] * s).real();
+    }
+  }
+  *out = total;
+  API_END(c)
+}
+
+int vqd_trace(vqd_t c, int inst, double* re, double* im) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (!re) throw Error(VQD_EINVAL, "NULL output");
+  timed(c, SC_REDUCE, std::ldexp(1.0, c->n[inst]) * c->esize, 0, 2,
+        [&] { return launch_trace(c->prec, c->ptr(inst), c->n[inst], c->d_scratch, c->d_out, c->stream); });
+  fetch(c, 2);
+  *re = c->h_out[0];
+  if (im) *im = c->h_out[1];
+  API_END(c)
+}
+
+int vqd_purity(vqd_t c, int inst, double* out) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (!out) throw Error(VQD_EINVAL, "NULL output");
+  timed(c, SC_REDUCE, (double)c->bytes(inst), 0, 2,
+        [&] { return launch_purity(c->prec, c->ptr(inst), c->n[inst], c->d_scratch, c->d_out, c->stream); });
+  fetch(c, 1);
+  *out = c->h_out[0];
+  API_END(c)
+}
+
+int vqd_get_state(vqd_t c, int inst, vqd_c128* host) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (!host) throw Error(VQD_EINVAL, "NULL output");
+  const size_t N = (size_t)1 << (2 * c->n[inst]);
+  if (c->prec == VQD_F64) {
+    cuda_check(cudaMemcpyAsync(host, c->ptr(inst), N * 16, cudaMemcpyDeviceToHost, c->stream), "D2H state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  } else {
+    std::vector<float> tmp(2 * N);
+    cuda_check(cudaMemcpyAsync(tmp.data(), c->ptr(inst), N * 8, cudaMemcpyDeviceToHost, c->stream), "D2H state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+    for (size_t i = 0; i < N; i++) host[i] = {tmp[2 * i], tmp[2 * i + 1]};
+  }
+  API_END(c)
+}
+
+int vqd_set_state(vqd_t c, int inst, const vqd_c128* host) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (!host) throw Error(VQD_EINVAL, "NULL input");
+  const size_t N = (size_t)1 << (2 * c->n[inst]);
+  if (c->prec == VQD_F64) {
+    cuda_check(cudaMemcpyAsync(c->ptr(inst), host, N * 16, cudaMemcpyHostToDevice, c->stream), "H2D state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  } else {
+    std::vector<float> tmp(2 * N);
+    for (size_t i = 0; i < N; i++) {
+      tmp[2 * i] = (float)host[i].re;
+      tmp[2 * i + 1] = (float)host[i].im;
+    }
+    cuda_check(cudaMemcpyAsync(c->ptr(inst), tmp.data(), N * 8, cudaMemcpyHostToDevice, c->stream), "H2D state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  API_END(c)
+}
+
+int vqd_profile(vqd_t c, int mode) {
+  API_BEGIN
+  need_ctx(c);
+  if (mode < 0 || mode > 2) throw Error(VQD_EINVAL, "mode must be 0, 1 or 2");
+  harvest(c);
+  c->prof = mode;
+  API_END(c)
+}
+
+int vqd_profile_reset(vqd_t c) {
+  API_BEGIN
+  need_ctx(c);
+  harvest(c);
+  for (auto& s : c->stats) s = Stat();
+  API_END(c)
+}
+
+int vqd_profile_read(vqd_t c, int max, vqd_kstat* out, int* n_out) {
+  API_BEGIN
+  need_ctx(c);
+  if (!n_out || (max > 0 && !out)) throw Error(VQD_EINVAL, "NULL output");
+  harvest(c);
+  int cnt = 0;
+  for (int i = 0; i < SC_COUNT; i++) {
+    if (c->stats[i].launches == 0) continue;
+    if (cnt < max) {
+      vqd_kstat& k = out[cnt];
+      std::memset(&k, 0, sizeof(k));
+      std::strncpy(k.name, kStatNames[i], sizeof(k.name) - 1);
+      k.launches = c->stats[i].launches;
+      k.total_ms = c->stats[i].ms;
+      k.alg_bytes = c->stats[i].bytes;
+      k.amp_updates = c->stats[i].amp_updates;
+    }
+    cnt++;
+  }
+  *n_out = cnt;
+  API_END(c)
+}
+
+}  // extern "C"

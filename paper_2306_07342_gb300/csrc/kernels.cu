@@ -1,0 +1,545 @@
+// Plain-path kernels of libvqd: one pass over the state per operator, FP64 reductions, init.
+//
+// State layout: amplitude rho[r][c] of an n-qubit instance at index r + (c << n).  An operator
+// on k qubits q touches, for every assignment of the other 2n - 2k index bits, the group of 4^k
+// amplitudes spanned by the row bits q and the column bits q + n.  Each thread owns whole groups,
+// loads them once from HBM, applies the operator in registers and stores them once: 2 x state
+// bytes of DRAM traffic per pass, the algorithmic minimum for one operator.
+//
+// Coefficients arrive as kernel parameters (constant bank, broadcast to the warp).  Each
+// coefficient carries a type flag (zero / one / real / imaginary / complex) that is uniform
+// across the grid; the SPARSE instantiations branch on it so that structured operators (Pauli
+// and damping channels, rotations whose entries are real or imaginary) issue only the
+// multiply-adds they need.  That matters for FP64, whose FMA rate on this GPU is about 1/58 of
+// FP32; the dense instantiations keep straight-line FMA code for FP32.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace vqd {
+namespace dev {
+
+template <class T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+template <class T> using cx = typename V2<T>::t;
+
+enum { FL_ZERO = 0, FL_ONE = 1, FL_REAL = 2, FL_IMAG = 3, FL_CPLX = 4 };
+
+template <class T>
+__device__ __forceinline__ void cmac_flag(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
+  if (fl == FL_ZERO) return;
+  if (fl == FL_ONE) { acc.x += x.x; acc.y += x.y; return; }
+  if (fl == FL_REAL) { acc.x = fma(c.x, x.x, acc.x); acc.y = fma(c.x, x.y, acc.y); return; }
+  if (fl == FL_IMAG) { acc.x = fma(-c.y, x.y, acc.x); acc.y = fma(c.y, x.x, acc.y); return; }
+  acc.x = fma(c.x, x.x, acc.x);
+  acc.x = fma(-c.y, x.y, acc.x);
+  acc.y = fma(c.x, x.y, acc.y);
+  acc.y = fma(c.y, x.x, acc.y);
+}
+
+template <class T>
+__device__ __forceinline__ void cmac(cx<T>& acc, const cx<T>& c, const cx<T>& x) {
+  acc.x = fma(c.x, x.x, acc.x);
+  acc.x = fma(-c.y, x.y, acc.x);
+  acc.y = fma(c.x, x.y, acc.y);
+  acc.y = fma(c.y, x.x, acc.y);
+}
+
+template <bool SPARSE, class T>
+__device__ __forceinline__ void mac(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
+  if (SPARSE) cmac_flag<T>(acc, c, fl, x);
+  else cmac<T>(acc, c, x);
+}
+
+// Insert a zero bit at each of the NB ascending positions pos[] into g.
+template <int NB>
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t g, const int* pos) {
+#pragma unroll
+  for (int i = 0; i < NB; i++) {
+    const uint64_t lo = g & ((1ull << pos[i]) - 1ull);
+    g = ((g >> pos[i]) << (pos[i] + 1)) | lo;
+  }
+  return g;
+}
+
+template <int G>
+struct Group {
+  uint64_t off[G];  // member offsets, member index s = r | c << k
+  int pos[4];       // ascending positions of the 2k group bits
+};
+
+template <class T> struct Sup1P { Group<4> g; cx<T> s[16]; unsigned char fl[16]; };
+template <class T> struct Uni2P { Group<16> g; cx<T> u[16]; cx<T> uc[16]; unsigned char fl[16]; };
+template <class T> struct Sup2P { Group<16> g; cx<T> s[256]; unsigned char fl[256]; };
+template <class T> struct ElemP { cx<T> f[16]; int pos[4]; int nb; };
+
+#define GRID_STRIDE_LOOP(i, count)                                                         \
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, _st = (uint64_t)gridDim.x * blockDim.x; \
+       i < (count); i += _st)
+
+// ---- one-qubit operator as a 4x4 superoperator
+template <class T, bool SPARSE>
+__global__ void __launch_bounds__(256) k_sup1(cx<T>* __restrict__ st, uint64_t ngroups, const Sup1P<T> P) {
+  GRID_STRIDE_LOOP(g, ngroups) {
+    const uint64_t base = insert_zeros<2>(g, P.g.pos);
+    cx<T> x[4], y[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) x[s] = st[base + P.g.off[s]];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      y[i].x = 0; y[i].y = 0;
+#pragma unroll
+      for (int j = 0; j < 4; j++) mac<SPARSE, T>(y[i], P.s[i * 4 + j], P.fl[i * 4 + j], x[j]);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; s++) st[base + P.g.off[s]] = y[s];
+  }
+}
+
+// ---- two-qubit unitary: A <- U A U^dagger on the 4x4 block A[r][c] = amplitude r | c << 2
+template <class T, bool SPARSE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_uni2(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
+  GRID_STRIDE_LOOP(g, ngroups) {
+    const uint64_t base = insert_zeros<4>(g, P.g.pos);
+    cx<T> A[16], B[16];
+#pragma unroll
+    for (int s = 0; s < 16; s++) A[s] = st[base + P.g.off[s]];
+    // B = U A : B[r][c] = sum_m U[r][m] A[m][c]
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        cx<T> acc; acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) mac<SPARSE, T>(acc, P.u[r * 4 + m], P.fl[r * 4 + m], A[m | (c << 2)]);
+        B[r | (c << 2)] = acc;
+      }
+    // A = B U^dagger : A[r][c] = sum_m B[r][m] conj(U[c][m])
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        cx<T> acc; acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) mac<SPARSE, T>(acc, P.uc[c * 4 + m], P.fl[c * 4 + m], B[r | (m << 2)]);
+        A[r | (c << 2)] = acc;
+      }
+#pragma unroll
+    for (int s = 0; s < 16; s++) st[base + P.g.off[s]] = A[s];
+  }
+}
+
+// ---- two-qubit channel as a 16x16 superoperator
+template <class T, bool SPARSE>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && SPARSE) ? 2 : 1) k_sup2(cx<T>* __restrict__ st, uint64_t ngroups, const Sup2P<T> P) {
+  GRID_STRIDE_LOOP(g, ngroups) {
+    const uint64_t base = insert_zeros<4>(g, P.g.pos);
+    cx<T> x[16];
+#pragma unroll
+    for (int s = 0; s < 16; s++) x[s] = st[base + P.g.off[s]];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      cx<T> acc; acc.x = 0; acc.y = 0;
+#pragma unroll
+      for (int j = 0; j < 16; j++) mac<SPARSE, T>(acc, P.s[i * 16 + j], P.fl[i * 16 + j], x[j]);
+      st[base + P.g.off[i]] = acc;
+    }
+  }
+}
+
+// ---- diagonal superoperator: every amplitude times a factor chosen by its 2k group bits.
+// Four consecutive amplitudes per thread (vector loads); REAL when every factor is real.
+template <class T, bool REAL>
+__device__ __forceinline__ void scale(cx<T>& v, const cx<T>& f) {
+  if (REAL) { v.x *= f.x; v.y *= f.x; }
+  else { const T re = v.x * f.x - v.y * f.y; v.y = v.x * f.y + v.y * f.x; v.x = re; }
+}
+template <class T, bool REAL>
+__global__ void __launch_bounds__(256) k_elem(cx<T>* __restrict__ st, uint64_t nquads, const ElemP<T> P) {
+  GRID_STRIDE_LOOP(qd, nquads) {
+    const uint64_t i0 = qd * 4;
+    cx<T> v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = st[i0 + j];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const uint64_t i = i0 + j;
+      int s = 0;
+      for (int b = 0; b < P.nb; b++) s |= (int)((i >> P.pos[b]) & 1ull) << b;
+      scale<T, REAL>(v[j], P.f[s]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) st[i0 + j] = v[j];
+  }
+}
+
+// ---- initial states
+struct DiagProductP { double e[VQD_MAX_QUBITS]; };
+template <class T>
+__global__ void k_set_diag_product(cx<T>* __restrict__ st, int n, const DiagProductP P) {
+  const uint64_t dim = 1ull << n;
+  GRID_STRIDE_LOOP(x, dim) {
+    double p = 1.0;
+#pragma unroll
+    for (int q = 0; q < VQD_MAX_QUBITS; q++)
+      if (q < n) p *= ((x >> q) & 1ull) ? P.e[q] : 1.0 - P.e[q];
+    cx<T> v; v.x = (T)p; v.y = 0;
+    st[x * (dim + 1)] = v;
+  }
+}
+template <class T>
+__global__ void k_set_one(cx<T>* __restrict__ st, uint64_t idx) {
+  cx<T> v; v.x = 1; v.y = 0;
+  st[idx] = v;
+}
+
+// ---- reductions (FP64 accumulation, fixed order: grid-stride per thread, then a block tree)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = 0;
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_purity(const cx<T>* __restrict__ st, uint64_t N, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0;
+  GRID_STRIDE_LOOP(i, N) {
+    const cx<T> v = st[i];
+    const double re = (double)v.x, im = (double)v.y;
+    acc = fma(re, re, fma(im, im, acc));
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_trace(const cx<T>* __restrict__ st, int n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const uint64_t dim = 1ull << n;
+  double re = 0, im = 0;
+  GRID_STRIDE_LOOP(x, dim) {
+    const cx<T> v = st[x * (dim + 1)];
+    re += (double)v.x;
+    im += (double)v.y;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = re; part[2 * blockIdx.x + 1] = im; }
+}
+
+struct ProbP { int meas[16]; int rest[16]; int m, nr; };
+// thread (v, ch) sums chunk ch of bin v: basis states x = deposit(v -> measured) | deposit(u -> rest)
+template <class T>
+__global__ void __launch_bounds__(256) k_prob(const cx<T>* __restrict__ st, int n, ProbP P, uint64_t chunks,
+                                              uint64_t chunk_len, double* __restrict__ part) {
+  const uint64_t dim = 1ull << n;
+  const uint64_t nbins = 1ull << P.m;
+  GRID_STRIDE_LOOP(t, nbins * chunks) {
+    const uint64_t v = t / chunks, ch = t % chunks;
+    uint64_t xv = 0;
+    for (int j = 0; j < P.m; j++) xv |= ((v >> j) & 1ull) << P.meas[j];
+    double acc = 0;
+    for (uint64_t u = ch * chunk_len; u < (ch + 1) * chunk_len; u++) {
+      uint64_t x = xv;
+      for (int j = 0; j < P.nr; j++) x |= ((u >> j) & 1ull) << P.rest[j];
+      acc += (double)st[x * (dim + 1)].x;
+    }
+    part[t] = acc;
+  }
+}
+
+struct ExpectP { uint32_t xm[kExpectTermsPerLaunch]; uint32_t zy[kExpectTermsPerLaunch]; };
+// block (b, t): partial of sum_c (-1)^popc(c & zy_t) rho[c][c ^ x_t]
+template <class T>
+__global__ void __launch_bounds__(256) k_expect(const cx<T>* __restrict__ st, int n, const ExpectP P,
+                                                double* __restrict__ part) {
+  __shared__ double sh[32];
+  const uint64_t dim = 1ull << n;
+  const int t = blockIdx.y;
+  const uint32_t xm = P.xm[t], zy = P.zy[t];
+  double re = 0, im = 0;
+  GRID_STRIDE_LOOP(c, dim) {
+    const cx<T> v = st[c + ((c ^ xm) << n)];
+    const double sg = (__popcll(c & zy) & 1) ? -1.0 : 1.0;
+    re = fma(sg, (double)v.x, re);
+    im = fma(sg, (double)v.y, im);
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    part[(size_t)(t * gridDim.x + blockIdx.x) * 2] = re;
+    part[(size_t)(t * gridDim.x + blockIdx.x) * 2 + 1] = im;
+  }
+}
+
+// out[v] = sum_j part[v * nparts + j], one block per value.
+__global__ void __launch_bounds__(256) k_sum_rows(const double* __restrict__ part, uint64_t nparts, int stride_v,
+                                                  int stride_j, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (uint64_t j = threadIdx.x; j < nparts; j += blockDim.x) acc += part[(uint64_t)blockIdx.x * stride_v + j * stride_j];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+}  // namespace dev
+
+// ================================================================== host launchers
+using namespace dev;
+
+static int g_nsm = 0;
+int num_sms() {
+  if (!g_nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (g_nsm <= 0) g_nsm = 1;
+  }
+  return g_nsm;
+}
+
+template <class K>
+static unsigned grid_for(K kernel, uint64_t work, int block = 256) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm <= 0) per_sm = 1;
+  uint64_t full = (uint64_t)per_sm * num_sms();
+  uint64_t need = (work + block - 1) / block;
+  return (unsigned)std::max<uint64_t>(1, std::min(full, need));
+}
+
+static int flag_of(cd c) {
+  if (c == 0.0) return FL_ZERO;
+  if (c == 1.0) return FL_ONE;
+  if (c.imag() == 0.0) return FL_REAL;
+  if (c.real() == 0.0) return FL_IMAG;
+  return FL_CPLX;
+}
+
+template <class T>
+static cx<T> to_cx(cd c) {
+  cx<T> v;
+  v.x = (T)c.real();
+  v.y = (T)c.imag();
+  return v;
+}
+
+// Group geometry for k targets q on an n-qubit state: member s = r | c << k at offset
+// sum_j r_j 2^{q_j} + c_j 2^{q_j + n}; the 2k bits sorted ascending for zero insertion.
+template <int G>
+static Group<G> make_group(int n, int k, const int* q) {
+  Group<G> g;
+  int nb = 2 * k;
+  int bits[4];
+  for (int j = 0; j < k; j++) { bits[j] = q[j]; bits[j + k] = q[j] + n; }
+  for (int s = 0; s < G; s++) {
+    uint64_t o = 0;
+    for (int b = 0; b < nb; b++)
+      if ((s >> b) & 1) o |= 1ull << bits[b];
+    g.off[s] = o;
+  }
+  std::sort(bits, bits + nb);
+  for (int b = 0; b < 4; b++) g.pos[b] = b < nb ? bits[b] : 0;
+  return g;
+}
+
+// Does the sparse instantiation pay off?  Count multiply-adds it would issue vs the dense one.
+static bool use_sparse(const std::vector<cd>& c, bool fp64) {
+  int dense = 4 * (int)c.size(), sparse = 0;
+  for (const cd& x : c) {
+    int f = flag_of(x);
+    sparse += f == FL_ZERO ? 0 : f == FL_ONE ? 2 : f == FL_CPLX ? 4 : 2;
+  }
+  return fp64 ? sparse < dense : 2 * sparse < dense;
+}
+
+template <class T>
+static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s) {
+  const uint64_t N = 1ull << (2 * n);
+  const bool fp64 = sizeof(T) == 8;
+  if (p.kind == KK_ELEM) {
+    ElemP<T> P;
+    std::memset(&P, 0, sizeof(P));
+    int bits[4];
+    for (int j = 0; j < p.k; j++) { bits[j] = p.q[j]; bits[j + p.k] = p.q[j] + n; }
+    P.nb = 2 * p.k;
+    for (int b = 0; b < 4; b++) P.pos[b] = b < P.nb ? bits[b] : 0;
+    bool real = true;
+    for (size_t i = 0; i < p.coef.size(); i++) {
+      P.f[i] = to_cx<T>(p.coef[i]);
+      if (p.coef[i].imag() != 0.0) real = false;
+    }
+    const uint64_t nq = N / 4;
+    if (real) k_elem<T, true><<<grid_for(k_elem<T, true>, nq), 256, 0, s>>>(st, nq, P);
+    else k_elem<T, false><<<grid_for(k_elem<T, false>, nq), 256, 0, s>>>(st, nq, P);
+    return cudaGetLastError();
+  }
+  if (p.kind == KK_SUP1) {
+    Sup1P<T> P;
+    P.g = make_group<4>(n, 1, p.q);
+    for (int i = 0; i < 16; i++) { P.s[i] = to_cx<T>(p.coef[i]); P.fl[i] = (unsigned char)flag_of(p.coef[i]); }
+    const uint64_t ng = N / 4;
+    if (use_sparse(p.coef, fp64)) k_sup1<T, true><<<grid_for(k_sup1<T, true>, ng), 256, 0, s>>>(st, ng, P);
+    else k_sup1<T, false><<<grid_for(k_sup1<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    return cudaGetLastError();
+  }
+  if (p.kind == KK_UNI2) {
+    Uni2P<T> P;
+    P.g = make_group<16>(n, 2, p.q);
+    for (int i = 0; i < 16; i++) {
+      P.u[i] = to_cx<T>(p.coef[i]);
+      P.uc[i] = to_cx<T>(std::conj(p.coef[i]));
+      P.fl[i] = (unsigned char)flag_of(p.coef[i]);
+    }
+    // conj keeps the flag class except ONE stays ONE; an entry equal to 1 has conj 1 as well.
+    const uint64_t ng = N / 16;
+    if (use_sparse(p.coef, fp64)) k_uni2<T, true><<<grid_for(k_uni2<T, true>, ng), 256, 0, s>>>(st, ng, P);
+    else k_uni2<T, false><<<grid_for(k_uni2<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    return cudaGetLastError();
+  }
+  if (p.kind == KK_SUP2) {
+    Sup2P<T> P;
+    P.g = make_group<16>(n, 2, p.q);
+    for (int i = 0; i < 256; i++) { P.s[i] = to_cx<T>(p.coef[i]); P.fl[i] = (unsigned char)flag_of(p.coef[i]); }
+    const uint64_t ng = N / 16;
+    if (use_sparse(p.coef, fp64)) k_sup2<T, true><<<grid_for(k_sup2<T, true>, ng), 256, 0, s>>>(st, ng, P);
+    else k_sup2<T, false><<<grid_for(k_sup2<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s) {
+  if (prec == VQD_F32) return launch_pass_t<float>((cx<float>*)state, n, p, s);
+  return launch_pass_t<double>((cx<double>*)state, n, p, s);
+}
+
+template <class T>
+static cudaError_t init_classical_t(cx<T>* st, int n, uint64_t basis, cudaStream_t s) {
+  const uint64_t dim = 1ull << n;
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(cx<T>) * dim * dim, s);
+  if (e != cudaSuccess) return e;
+  k_set_one<T><<<1, 1, 0, s>>>(st, basis * (dim + 1));
+  return cudaGetLastError();
+}
+cudaError_t launch_init_classical(int prec, void* state, int n, uint64_t basis, cudaStream_t s) {
+  if (prec == VQD_F32) return init_classical_t<float>((cx<float>*)state, n, basis, s);
+  return init_classical_t<double>((cx<double>*)state, n, basis, s);
+}
+
+template <class T>
+static cudaError_t init_product_t(cx<T>* st, int n, const double* e, cudaStream_t s) {
+  const uint64_t dim = 1ull << n;
+  cudaError_t err = cudaMemsetAsync(st, 0, sizeof(cx<T>) * dim * dim, s);
+  if (err != cudaSuccess) return err;
+  DiagProductP P;
+  for (int q = 0; q < VQD_MAX_QUBITS; q++) P.e[q] = q < n ? e[q] : 0.0;
+  k_set_diag_product<T><<<grid_for(k_set_diag_product<T>, dim), 256, 0, s>>>(st, n, P);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_product_diag(int prec, void* state, int n, const double* excited, cudaStream_t s) {
+  if (prec == VQD_F32) return init_product_t<float>((cx<float>*)state, n, excited, s);
+  return init_product_t<double>((cx<double>*)state, n, excited, s);
+}
+
+// Scratch: reduction partials.  kMaxParts bounds the blocks of one reduction launch.
+static const uint64_t kMaxParts = 2048;
+static const uint64_t kProbThreads = 1ull << 16;
+size_t reduce_scratch_doubles() {
+  return std::max<size_t>(2 * kMaxParts * kExpectTermsPerLaunch, kProbThreads);
+}
+size_t reduce_out_doubles() { return (1u << VQD_MAX_QUBITS) + 2 * kExpectTermsPerLaunch; }
+
+static unsigned reduce_blocks(uint64_t work) {
+  uint64_t b = (work + 255) / 256;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, std::min<uint64_t>(kMaxParts, 8ull * num_sms())));
+}
+
+template <class T>
+static cudaError_t purity_t(const cx<T>* st, int n, double* scratch, double* out, cudaStream_t s) {
+  const uint64_t N = 1ull << (2 * n);
+  unsigned nb = reduce_blocks(N);
+  k_purity<T><<<nb, 256, 0, s>>>(st, N, scratch);
+  k_sum_rows<<<1, 256, 0, s>>>(scratch, nb, 0, 1, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_purity(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s) {
+  if (prec == VQD_F32) return purity_t<float>((const cx<float>*)state, n, scratch, out, s);
+  return purity_t<double>((const cx<double>*)state, n, scratch, out, s);
+}
+
+template <class T>
+static cudaError_t trace_t(const cx<T>* st, int n, double* scratch, double* out, cudaStream_t s) {
+  unsigned nb = reduce_blocks(1ull << n);
+  k_trace<T><<<nb, 256, 0, s>>>(st, n, scratch);
+  k_sum_rows<<<2, 256, 0, s>>>(scratch, nb, 1, 2, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_trace(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s) {
+  if (prec == VQD_F32) return trace_t<float>((const cx<float>*)state, n, scratch, out, s);
+  return trace_t<double>((const cx<double>*)state, n, scratch, out, s);
+}
+
+template <class T>
+static cudaError_t prob_t(const cx<T>* st, int n, int m, const int* qubits, double* scratch, double* out,
+                          cudaStream_t s) {
+  ProbP P;
+  std::memset(&P, 0, sizeof(P));
+  P.m = m;
+  unsigned used = 0;
+  for (int j = 0; j < m; j++) { P.meas[j] = qubits[j]; used |= 1u << qubits[j]; }
+  P.nr = 0;
+  for (int q = 0; q < n; q++)
+    if (!(used >> q & 1)) P.rest[P.nr++] = q;
+  const uint64_t bins = 1ull << m, per_bin = 1ull << P.nr;
+  uint64_t chunks = std::min<uint64_t>(per_bin, std::max<uint64_t>(1, kProbThreads / bins));
+  const uint64_t len = per_bin / chunks;
+  k_prob<T><<<grid_for(k_prob<T>, bins * chunks), 256, 0, s>>>(st, n, P, chunks, len, scratch);
+  k_sum_rows<<<(unsigned)bins, 256, 0, s>>>(scratch, chunks, (int)chunks, 1, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_prob(int prec, const void* state, int n, int m, const int* qubits, double* scratch, double* out,
+                        cudaStream_t s) {
+  if (prec == VQD_F32) return prob_t<float>((const cx<float>*)state, n, m, qubits, scratch, out, s);
+  return prob_t<double>((const cx<double>*)state, n, m, qubits, scratch, out, s);
+}
+
+template <class T>
+static cudaError_t expect_t(const cx<T>* st, int n, int nterms, const uint32_t* xm, const uint32_t* zy,
+                            double* scratch, double* out, cudaStream_t s) {
+  ExpectP P;
+  std::memset(&P, 0, sizeof(P));
+  for (int t = 0; t < nterms; t++) { P.xm[t] = xm[t]; P.zy[t] = zy[t]; }
+  unsigned nb = std::min<unsigned>(reduce_blocks(1ull << n), (unsigned)(kMaxParts));
+  dim3 grid(nb, nterms);
+  k_expect<T><<<grid, 256, 0, s>>>(st, n, P, scratch);
+  // value 2t + j sums part[(t * nb + b) * 2 + j] over b: row stride 2 nb for t, but j interleaves;
+  // launch one row-sum per (t, j) with base offset (t * nb) * 2 + j and element stride 2.
+  for (int j = 0; j < 2; j++) {
+    // out[2t + j]: use a strided view: part + j, row stride 2 nb, element stride 2
+    k_sum_rows<<<nterms, 256, 0, s>>>(scratch + j, nb, (int)(2 * nb), 2, out + (size_t)j * nterms);
+  }
+  return cudaGetLastError();
+}
+cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const uint32_t* xmask, const uint32_t* zymask,
+                          double* scratch, double* out, cudaStream_t s) {
+  if (prec == VQD_F32) return expect_t<float>((const cx<float>*)state, n, nterms, xmask, zymask, scratch, out, s);
+  return expect_t<double>((const cx<double>*)state, n, nterms, xmask, zymask, scratch, out, s);
+}
+
+}  // namespace vqd

@@ -1,0 +1,35 @@
+// Host-callable launchers of the libvqd kernels (implemented in kernels.cu / fused.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "vqd_internal.h"
+
+namespace vqd {
+
+// Launch one plain-path pass over an n-qubit state (complex64 if prec == VQD_F32, else complex128).
+cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s);
+
+// Initialisation.
+cudaError_t launch_init_classical(int prec, void* state, int n, uint64_t basis, cudaStream_t s);
+cudaError_t launch_init_product_diag(int prec, void* state, int n, const double* excited, cudaStream_t s);
+
+// Reductions: each writes its partial sums to `scratch` (device, >= scratch_need(...) doubles)
+// and its final values to `out` (device).  Deterministic summation order.
+size_t reduce_scratch_doubles();
+size_t reduce_out_doubles();
+cudaError_t launch_trace(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s);      // out[0..1]
+cudaError_t launch_purity(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s);     // out[0]
+cudaError_t launch_prob(int prec, const void* state, int n, int m, const int* qubits, double* scratch, double* out,
+                        cudaStream_t s);                                                                          // out[0..2^m)
+// Up to kExpectTermsPerLaunch terms: xmask / zymask per term; out[2t], out[2t+1] = sum of
+// (-1)^popc(c & zymask) rho[c][c ^ xmask] (re, im) for term t.
+constexpr int kExpectTermsPerLaunch = 64;
+cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const uint32_t* xmask,
+                          const uint32_t* zymask, double* scratch, double* out, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace vqd

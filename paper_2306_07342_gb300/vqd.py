@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libvqd (include/vqd.h): the same entry points, arguments marshalled only.
+
+Every computation happens in the library's CUDA kernels.  Loading fails loudly when libvqd.so is
+missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvqd.so")
+
+VQD_F64, VQD_F32 = 0, 1
+VQD_T2_IS_TOTAL, VQD_NO_CHECK = 1, 2
+VQD_OK, VQD_EINVAL, VQD_ENOMEM, VQD_ENOTCP, VQD_EDEVICE, VQD_ENOTSUP = 0, -1, -2, -3, -4, -5
+VQD_MAX_QUBITS = 16
+VQD_MAX_FUSE = 6
+
+# Native op codes, in the order of the header's vqd_op_code enum.
+OP_CODES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
+            "crz_xtalk", "exchange", "depol1", "depol2", "deph1", "deph2", "amp", "bitflip", "bitflip2", "gamp",
+            "idle", "idle_depol", "stderr1", "stderr2", "ampdeph2", "leak_init", "leak_cz"]
+OP_CODE = {name: i for i, name in enumerate(OP_CODES)}
+
+NATIVE_OP_DTYPE = np.dtype([("code", "<i4"), ("nq", "<i4"), ("q", "<i4", (2,)), ("par", "<f8", (4,))])
+assert NATIVE_OP_DTYPE.itemsize == 48
+
+
+class c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class kstat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double)]
+
+
+class VQDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libvqd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libvqd.so not built at {LIB_PATH}; run paper_2306_07342_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, U, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_size_t
+        sig = {
+            "vqd_state_bytes": (S, [I, I]),
+            "vqd_create": (I, [I, I, P, ctypes.POINTER(P)]),
+            "vqd_create_batch": (I, [I, P, I, P, ctypes.POINTER(P)]),
+            "vqd_create_on": (I, [I, I, P, S, P, ctypes.POINTER(P)]),
+            "vqd_destroy": (None, [P]),
+            "vqd_num_instances": (I, [P]),
+            "vqd_num_qubits": (I, [P, I]),
+            "vqd_state_ptr": (P, [P, I]),
+            "vqd_sync": (I, [P]),
+            "vqd_last_error": (ctypes.c_char_p, [P]),
+            "vqd_set_flags": (I, [P, U]),
+            "vqd_init_zero": (I, [P, I]),
+            "vqd_init_classical": (I, [P, I, ctypes.c_uint64]),
+            "vqd_init_product_diag": (I, [P, I, P]),
+            "vqd_apply_unitary": (I, [P, I, I, P, P]),
+            "vqd_apply_kraus": (I, [P, I, I, P, I, P]),
+            "vqd_apply_superop": (I, [P, I, I, P, P]),
+            "vqd_apply_native": (I, [P, I, I, P, U]),
+            "vqd_run_program": (I, [P, I, I, P, I, U]),
+            "vqd_run_batch": (I, [P, P, P, I, U]),
+            "vqd_compile_op": (I, [P, U, P, P, P, P]),
+            "vqd_stderr_params": (I, [I, D, D, P, P]),
+            "vqd_prob": (I, [P, I, I, P, P]),
+            "vqd_expect": (I, [P, I, I, P, P, P]),
+            "vqd_trace": (I, [P, I, P, P]),
+            "vqd_purity": (I, [P, I, P]),
+            "vqd_get_state": (I, [P, I, P]),
+            "vqd_set_state": (I, [P, I, P]),
+            "vqd_profile": (I, [P, I]),
+            "vqd_profile_reset": (I, [P]),
+            "vqd_profile_read": (I, [P, I, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != VQD_OK:
+        msg = lib().vqd_last_error(ctx)
+        raise VQDError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(m) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(m, dtype=np.complex128))
+
+
+def _i32(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+
+
+def native_ops(ops: Iterable) -> np.ndarray:
+    """Marshal NativeOp(name, qubits, params) records into the C struct array."""
+    ops = list(ops)
+    arr = np.zeros(len(ops), dtype=NATIVE_OP_DTYPE)
+    for i, o in enumerate(ops):
+        arr[i]["code"] = OP_CODE[o.name]
+        arr[i]["nq"] = len(o.qubits)
+        arr[i]["q"][: len(o.qubits)] = o.qubits
+        arr[i]["par"][: len(o.params)] = o.params
+    return arr
+
+
+# ---------------------------------------------------------------- entry points (same names as the C ABI)
+def vqd_state_bytes(n: int, prec: int) -> int:
+    return lib().vqd_state_bytes(n, prec)
+
+
+def vqd_create(n: int, prec: int = VQD_F64, stream: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().vqd_create(n, prec, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def vqd_create_batch(ns: Sequence[int], prec: int = VQD_F64, stream: int = 0):
+    a = _i32(ns)
+    h = ctypes.c_void_p()
+    _check(lib().vqd_create_batch(len(a), _ptr(a), prec, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def vqd_create_on(n: int, prec: int, dev_ptr: int, nbytes: int, stream: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().vqd_create_on(n, prec, ctypes.c_void_p(dev_ptr), nbytes, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def vqd_destroy(ctx):
+    lib().vqd_destroy(ctx)
+
+
+def vqd_num_qubits(ctx, inst: int = 0) -> int:
+    return lib().vqd_num_qubits(ctx, inst)
+
+
+def vqd_state_ptr(ctx, inst: int = 0) -> int:
+    return lib().vqd_state_ptr(ctx, inst)
+
+
+def vqd_sync(ctx):
+    _check(lib().vqd_sync(ctx), ctx)
+
+
+def vqd_set_flags(ctx, flags: int):
+    _check(lib().vqd_set_flags(ctx, flags), ctx)
+
+
+def vqd_init_zero(ctx, inst: int = 0):
+    _check(lib().vqd_init_zero(ctx, inst), ctx)
+
+
+def vqd_init_classical(ctx, inst: int, basis: int):
+    _check(lib().vqd_init_classical(ctx, inst, basis), ctx)
+
+
+def vqd_init_product_diag(ctx, inst: int, excited: Sequence[float]):
+    e = np.ascontiguousarray(np.asarray(excited, dtype=np.float64))
+    _check(lib().vqd_init_product_diag(ctx, inst, _ptr(e)), ctx)
+
+
+def vqd_apply_unitary(ctx, inst: int, targets: Sequence[int], U):
+    t, m = _i32(targets), _c128(U)
+    _check(lib().vqd_apply_unitary(ctx, inst, len(t), _ptr(t), _ptr(m)), ctx)
+
+
+def vqd_apply_kraus(ctx, inst: int, targets: Sequence[int], kraus):
+    t = _i32(targets)
+    m = _c128(np.stack([np.asarray(K) for K in kraus]))
+    _check(lib().vqd_apply_kraus(ctx, inst, len(t), _ptr(t), len(m), _ptr(m)), ctx)
+
+
+def vqd_apply_superop(ctx, inst: int, targets: Sequence[int], S):
+    t, m = _i32(targets), _c128(S)
+    _check(lib().vqd_apply_superop(ctx, inst, len(t), _ptr(t), _ptr(m)), ctx)
+
+
+def vqd_apply_native(ctx, inst: int, ops, flags: int = 0):
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    _check(lib().vqd_apply_native(ctx, inst, len(a), _ptr(a), flags), ctx)
+
+
+def vqd_run_program(ctx, inst: int, ops, fuse_qubits: int = 0, flags: int = 0):
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    _check(lib().vqd_run_program(ctx, inst, len(a), _ptr(a), fuse_qubits, flags), ctx)
+
+
+def vqd_run_batch(ctx, programs_ops: Sequence, fuse_qubits: int = 0, flags: int = 0):
+    arrays = [p if isinstance(p, np.ndarray) else native_ops(p) for p in programs_ops]
+    offsets = np.zeros(len(arrays) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([len(a) for a in arrays])
+    allops = np.concatenate(arrays) if arrays else np.zeros(0, dtype=NATIVE_OP_DTYPE)
+    allops = np.ascontiguousarray(allops)
+    _check(lib().vqd_run_batch(ctx, _ptr(offsets), _ptr(allops), fuse_qubits, flags), ctx)
+
+
+def vqd_compile_op(op, flags: int = 0):
+    """Returns ("U", qubits, U) or ("S", qubits, S) from the library's device compiler (host only)."""
+    a = native_ops([op])
+    isu, k = ctypes.c_int(), ctypes.c_int()
+    t = np.zeros(2, dtype=np.int32)
+    m = np.zeros(256, dtype=np.complex128)
+    _check(lib().vqd_compile_op(_ptr(a), flags, ctypes.byref(isu), ctypes.byref(k), _ptr(t), _ptr(m)))
+    kk = k.value
+    if isu.value:
+        return "U", tuple(t[:kk]), m[: 4 ** kk].reshape(2 ** kk, 2 ** kk)
+    return "S", tuple(t[:kk]), m[: 16 ** kk].reshape(4 ** kk, 4 ** kk)
+
+
+def vqd_stderr_params(nq: int, fbar: float, x: float):
+    p, q = ctypes.c_double(), ctypes.c_double()
+    _check(lib().vqd_stderr_params(nq, fbar, x, ctypes.byref(p), ctypes.byref(q)))
+    return p.value, q.value
+
+
+def vqd_prob(ctx, inst: int, qubits: Sequence[int]) -> np.ndarray:
+    q = _i32(qubits)
+    out = np.zeros(2 ** len(q), dtype=np.float64)
+    _check(lib().vqd_prob(ctx, inst, len(q), _ptr(q), _ptr(out)), ctx)
+    return out
+
+
+def vqd_expect(ctx, inst: int, paulis, coeffs) -> float:
+    p = np.ascontiguousarray(np.asarray(paulis, dtype=np.uint8))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    out = ctypes.c_double()
+    _check(lib().vqd_expect(ctx, inst, len(c), _ptr(p), _ptr(c), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def vqd_trace(ctx, inst: int = 0) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib().vqd_trace(ctx, inst, ctypes.byref(re), ctypes.byref(im)), ctx)
+    return complex(re.value, im.value)
+
+
+def vqd_purity(ctx, inst: int = 0) -> float:
+    out = ctypes.c_double()
+    _check(lib().vqd_purity(ctx, inst, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def vqd_get_state(ctx, inst: int = 0) -> np.ndarray:
+    """Flat 4^n complex128 vector v[r + (c << n)] = rho[r][c]."""
+    n = vqd_num_qubits(ctx, inst)
+    out = np.zeros(4 ** n, dtype=np.complex128)
+    _check(lib().vqd_get_state(ctx, inst, _ptr(out)), ctx)
+    return out
+
+
+def vqd_set_state(ctx, inst: int, flat) -> None:
+    a = _c128(flat).reshape(-1)
+    _check(lib().vqd_set_state(ctx, inst, _ptr(a)), ctx)
+
+
+def vqd_profile(ctx, mode: int):
+    _check(lib().vqd_profile(ctx, mode), ctx)
+
+
+def vqd_profile_reset(ctx):
+    _check(lib().vqd_profile_reset(ctx), ctx)
+
+
+def vqd_profile_read(ctx) -> dict:
+    arr = (kstat * 16)()
+    n = ctypes.c_int()
+    _check(lib().vqd_profile_read(ctx, 16, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(n)), ctx)
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
+                                   "alg_bytes": arr[i].alg_bytes, "amp_updates": arr[i].amp_updates}
+            for i in range(min(n.value, 16))}
+
+
+def rho_from_flat(flat: np.ndarray) -> np.ndarray:
+    """Matrix rho[r, c] from the library's flat layout (a view conversion, no arithmetic)."""
+    dim = int(round(np.sqrt(flat.size)))
+    return np.ascontiguousarray(flat.reshape(dim, dim).T)

@@ -1,0 +1,111 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared symbol, and its device
+compiler (host code) agrees with the oracle's compiler.  No GPU call is made here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import compile as oc
+from workloads.circuits import OP_NAMES, NativeOp, random_program, _random_params, _rng
+
+from ._lib import get_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vqd.h")
+
+
+@pytest.fixture(scope="module")
+def vqd():
+    return get_lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vqd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(vqd):
+    names = declared_functions()
+    assert len(names) >= 30
+    L = ctypes.CDLL(vqd.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_op_code_tables_agree():
+    """The header enum, the binding's code list and the workload vocabulary name the same ops in one order."""
+    from paper_2306_07342_gb300 import vqd as b
+    src = open(HEADER).read()
+    enum = re.findall(r"VQD_OP_([A-Z0-9_]+)\s*=\s*(\d+)", src)
+    enum = [(name.lower(), int(v)) for name, v in enum if name != "COUNT"]
+    assert [v for _, v in enum] == list(range(len(enum)))
+    assert [name for name, _ in enum] == b.OP_CODES == list(OP_NAMES)
+
+
+def oracle_superop(steps):
+    """Compose the oracle's compiled steps (applied in order) into one superoperator, index r | c << k."""
+    k = len(steps[0][1])
+    d = 2 ** k
+    S = np.eye(d * d, dtype=complex)
+    for kind, _, m in steps:
+        ks = [m] if kind == "U" else m
+        Sk = np.zeros((d * d, d * d), dtype=complex)
+        for K in ks:
+            Sk += np.kron(K.conj(), K)      # vec(K X K^dag) = (conj(K) (x) K) vec(X), column-major vec
+        S = Sk @ S
+    return S
+
+
+@pytest.mark.parametrize("name", list(OP_NAMES))
+def test_device_compiler_matches_oracle(vqd, name):
+    r = _rng(1234 + list(OP_NAMES).index(name))
+    nq = OP_NAMES[name][0]
+    for trial in range(4):
+        params = _random_params(r, name)
+        qs = (0,) if nq == 1 else (1, 0)
+        op = NativeOp(name, qs, params)
+        for flags in (0, vqd.VQD_T2_IS_TOTAL):
+            if flags and name not in ("idle", "idle_depol", "ampdeph2"):
+                continue
+            if flags and params[2] > 2 * params[1]:
+                continue
+            kind, t, M = vqd.vqd_compile_op(op, flags)
+            steps = oc.compile_op(name, qs, params, bool(flags))
+            assert t == qs
+            if kind == "U":
+                assert len(steps) == 1 and steps[0][0] == "U"
+                assert np.abs(M - steps[0][2]).max() < 1e-13, name
+            else:
+                assert np.abs(M - oracle_superop(steps)).max() < 1e-13, name
+
+
+@pytest.mark.parametrize("nq", [1, 2])
+def test_stderr_params_match_oracle(vqd, nq):
+    for fbar, x in [(0.999, 0.3), (0.99, 0.0), (0.95, 1.0), (0.97, 0.75)]:
+        got = vqd.vqd_stderr_params(nq, fbar, x)
+        want = oc.stderr_params(fbar, x, nq)
+        assert abs(got[0] - want[0]) < 1e-15 and abs(got[1] - want[1]) < 1e-15
+
+
+def test_compile_rejects_bad_ops(vqd):
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_compile_op(NativeOp("depol1", (0,), (0.9,)))          # p > 3/4
+    assert e.value.code == vqd.VQD_EINVAL
+    a = vqd.native_ops([NativeOp("rx", (0,), (0.1,))])
+    a[0]["code"] = 99
+    isu, k = ctypes.c_int(), ctypes.c_int()
+    t = np.zeros(2, np.int32)
+    m = np.zeros(256, np.complex128)
+    rc = vqd.lib().vqd_compile_op(a.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(isu), ctypes.byref(k),
+                                  t.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p))
+    assert rc == vqd.VQD_EINVAL
+
+
+def test_state_bytes(vqd):
+    assert vqd.vqd_state_bytes(14, vqd.VQD_F32) == 8 * 4 ** 14
+    assert vqd.vqd_state_bytes(16, vqd.VQD_F64) == 16 * 4 ** 16
+    assert vqd.vqd_state_bytes(17, vqd.VQD_F64) == 0

@@ -1,0 +1,310 @@
+"""GPU parity: libvqd (through its C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 states must match within 1e-12 max-abs; FP32 states within tol_f32(#ops) (see tests/_lib.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import evolve, measure
+from oracle import compile as oc
+from workloads import config1_chain6, config2_sc_grid, config3_ion_alltoall, config5_spin_chain
+from workloads.circuits import NativeOp, OP_NAMES, Program, random_program
+
+from ._lib import TOL_F64, get_lib, rand_kraus, rand_state, rand_unitary, tol_f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vqd():
+    return get_lib()
+
+
+PRECS = ["f64", "f32"]
+
+
+def prec_code(vqd, p):
+    return vqd.VQD_F64 if p == "f64" else vqd.VQD_F32
+
+
+def tol(p, nops):
+    return TOL_F64 if p == "f64" else tol_f32(nops)
+
+
+def gpu_state(vqd, ctx, inst=0):
+    return vqd.rho_from_flat(vqd.vqd_get_state(ctx, inst))
+
+
+def make_ctx(vqd, n, p, rho=None):
+    ctx = vqd.vqd_create(n, prec_code(vqd, p))
+    if rho is not None:
+        vqd.vqd_set_state(ctx, 0, evolve.to_device_layout(rho))
+    return ctx
+
+
+# ---------------------------------------------------------------- single operators, every kernel class
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("n", [1, 3, 7])
+def test_one_qubit_operators(vqd, p, n):
+    rng = np.random.default_rng(100 + n)
+    rho = rand_state(n, rng)
+    ctx = make_ctx(vqd, n, p, rho)
+    try:
+        for q in range(n):
+            U = rand_unitary(2, rng)
+            vqd.vqd_apply_unitary(ctx, 0, [q], U)
+            rho = evolve.apply_unitary(rho, (q,), U)
+            ks = rand_kraus(2, 3, rng)
+            vqd.vqd_apply_kraus(ctx, 0, [q], ks)
+            rho = evolve.apply_kraus(rho, (q,), ks)
+            D = np.diag(np.exp(1j * rng.uniform(0, 6, 2)))      # diagonal -> elementwise kernel
+            vqd.vqd_apply_unitary(ctx, 0, [q], D)
+            rho = evolve.apply_unitary(rho, (q,), D)
+            ks = oc.amp(0.3)                                       # real sparse superoperator
+            vqd.vqd_apply_kraus(ctx, 0, [q], ks)
+            rho = evolve.apply_kraus(rho, (q,), ks)
+        got = gpu_state(vqd, ctx)
+        assert np.abs(got - rho).max() < tol(p, 4 * n)
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("n,targets", [(2, (0, 1)), (2, (1, 0)), (5, (4, 1)), (7, (2, 6)), (7, (6, 5))])
+def test_two_qubit_operators(vqd, p, n, targets):
+    rng = np.random.default_rng(200 + n + targets[0])
+    rho = rand_state(n, rng)
+    ctx = make_ctx(vqd, n, p, rho)
+    try:
+        U = rand_unitary(4, rng)
+        vqd.vqd_apply_unitary(ctx, 0, targets, U)
+        rho = evolve.apply_unitary(rho, targets, U)
+        ks = rand_kraus(4, 3, rng)
+        vqd.vqd_apply_kraus(ctx, 0, targets, ks)
+        rho = evolve.apply_kraus(rho, targets, ks)
+        D = np.diag(np.exp(1j * rng.uniform(0, 6, 4)))
+        vqd.vqd_apply_unitary(ctx, 0, targets, D)
+        rho = evolve.apply_unitary(rho, targets, D)
+        ks = oc.deph2(0.2)                                         # diagonal superoperator
+        vqd.vqd_apply_kraus(ctx, 0, targets, ks)
+        rho = evolve.apply_kraus(rho, targets, ks)
+        S = sum(np.kron(K.conj(), K) for K in rand_kraus(4, 2, rng))
+        vqd.vqd_apply_superop(ctx, 0, targets, S)
+        want = evolve.apply_superop(rho, targets, S)
+        got = gpu_state(vqd, ctx)
+        assert np.abs(got - want).max() < tol(p, 5)
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- native programs, plain and fused
+def run_gpu(vqd, prog, p, path, fuse=0, max_ops=None):
+    ops = prog.ops if max_ops is None else prog.ops[:max_ops]
+    ctx = vqd.vqd_create(prog.n, prec_code(vqd, p))
+    try:
+        if prog.init_excited:
+            vqd.vqd_init_product_diag(ctx, 0, prog.init_excited)
+        if path == "plain":
+            vqd.vqd_apply_native(ctx, 0, ops)
+        else:
+            vqd.vqd_run_program(ctx, 0, ops, fuse)
+        rho = gpu_state(vqd, ctx)
+        red = {"probs": vqd.vqd_prob(ctx, 0, list(range(prog.n))), "trace": vqd.vqd_trace(ctx, 0),
+               "purity": vqd.vqd_purity(ctx, 0)}
+        return rho, red
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_config1_chain6_full(vqd, p, path):
+    """Six-qubit chain, 200 gates (~680 native ops), complex128 and complex64."""
+    prog = config1_chain6()
+    want = evolve.run_program(prog)
+    got, red = run_gpu(vqd, prog, p, path)
+    t = tol(p, len(prog.ops))
+    assert np.abs(got - want).max() < t
+    assert np.abs(red["probs"] - measure.probs(want, range(6))).max() < t
+    assert abs(red["trace"] - measure.trace(want)) < t
+    assert abs(red["purity"] - measure.purity(want)) < t
+
+
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("path,fuse", [("plain", 0), ("fused", 2), ("fused", 4), ("fused", 5), ("fused", 6)])
+def test_random_programs_every_op_kind(vqd, p, path, fuse):
+    """Every native op kind on n = 8 (16 index bits: the fused path needs several stages and tiles)."""
+    prog = random_program(77 + fuse, 8, 160)
+    want = evolve.run_program(prog)
+    got, _ = run_gpu(vqd, prog, p, path, fuse)
+    assert np.abs(got - want).max() < tol(p, len(prog.ops))
+
+
+@pytest.mark.parametrize("p", PRECS)
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_config2_grid_reduced(vqd, p, path):
+    """The superconducting-grid workload on a 2 x 4 grid (n = 8), depth 12."""
+    prog = config2_sc_grid(seed=9, rows=2, cols=4, depth=12)
+    want = evolve.run_program(prog)
+    got, red = run_gpu(vqd, prog, p, path)
+    t = tol(p, len(prog.ops))
+    assert np.abs(got - want).max() < t
+    assert np.abs(red["probs"] - measure.probs(want, range(8))).max() < t
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_config3_and_5_shapes_reduced(vqd, p):
+    for prog in (config3_ion_alltoall(seed=4, n=7, n_gates=60), config5_spin_chain(seed=6, n=7, n_gates=80)):
+        want = evolve.run_program(prog)
+        for path in ("plain", "fused"):
+            got, _ = run_gpu(vqd, prog, p, path)
+            assert np.abs(got - want).max() < tol(p, len(prog.ops)), (prog.meta["config"], path)
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_thermal_init_and_t2_flag(vqd, p):
+    prog = random_program(5, 4, 40)
+    prog.init_excited = (0.032, 0.021, 0.008, 0.009)
+    want = evolve.run_program(prog)
+    got, _ = run_gpu(vqd, prog, p, "plain")
+    assert np.abs(got - want).max() < tol(p, 40)
+    # VQD_T2_IS_TOTAL reads T2 as the total coherence time
+    prog = Program(2, [NativeOp("h", (0,)), NativeOp("idle", (0,), (3.0, 40.0, 25.0))])
+    ctx = vqd.vqd_create(2, prec_code(vqd, p))
+    try:
+        vqd.vqd_apply_native(ctx, 0, prog.ops, vqd.VQD_T2_IS_TOTAL)
+        got = gpu_state(vqd, ctx)
+    finally:
+        vqd.vqd_destroy(ctx)
+    want = evolve.run_program(prog, t2_is_total=True)
+    assert np.abs(got - want).max() < tol(p, 2)
+    assert abs(got[0, 1] - 0.5 * math.exp(-3.0 / 25.0)) < tol(p, 2)
+
+
+# ---------------------------------------------------------------- reductions
+@pytest.mark.parametrize("p", PRECS)
+def test_reductions(vqd, p):
+    rng = np.random.default_rng(31)
+    n = 6
+    rho = rand_state(n, rng)
+    ctx = make_ctx(vqd, n, p, rho)
+    try:
+        rho_dev = gpu_state(vqd, ctx)           # the stored state (rounded to FP32 in f32 mode)
+        t = 1e-13 if p == "f64" else 1e-12
+        for qs in ([0], [5, 2], [1, 3, 4], list(range(n)), [4, 0, 5, 1, 2, 3]):
+            assert np.abs(vqd.vqd_prob(ctx, 0, qs) - measure.probs(rho_dev, qs)).max() < t
+        codes = rng.integers(0, 4, size=(70, n)).astype(np.uint8)   # > 64 terms: two launches
+        coeffs = rng.normal(size=70)
+        assert abs(vqd.vqd_expect(ctx, 0, codes, coeffs) - measure.expect(rho_dev, codes, coeffs)) < 1e-12
+        assert abs(vqd.vqd_trace(ctx, 0) - measure.trace(rho_dev)) < t
+        assert abs(vqd.vqd_purity(ctx, 0) - measure.purity(rho_dev)) < t
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- batched persistent path
+@pytest.mark.parametrize("p", PRECS)
+def test_batch_matches_per_instance_oracle(vqd, p):
+    from workloads import config4_neutral_batch
+    progs = config4_neutral_batch(seed=8, count=10, n_lo=3, n_hi=8, depth=3)
+    ctx = vqd.vqd_create_batch([q.n for q in progs], prec_code(vqd, p))
+    try:
+        vqd.vqd_run_batch(ctx, [q.ops for q in progs])
+        for i, prog in enumerate(progs):
+            want = evolve.run_program(prog)
+            got = gpu_state(vqd, ctx, i)
+            assert np.abs(got - want).max() < tol(p, len(prog.ops)), i
+            assert abs(vqd.vqd_trace(ctx, i) - 1) < tol(p, len(prog.ops))
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- argument checks and error codes
+def test_error_codes(vqd):
+    ctx = vqd.vqd_create(3, vqd.VQD_F64)
+    try:
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_apply_unitary(ctx, 0, [3], np.eye(2))           # target out of range
+        assert e.value.code == vqd.VQD_EINVAL
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_apply_unitary(ctx, 0, [1, 1], np.eye(4))        # repeated target
+        assert e.value.code == vqd.VQD_EINVAL
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_apply_unitary(ctx, 0, [0], np.array([[1, 1], [0, 1]]))
+        assert e.value.code == vqd.VQD_ENOTCP
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_apply_kraus(ctx, 0, [0], [np.eye(2), 0.5 * np.eye(2)])   # sum K^dag K = 1.25 I
+        assert e.value.code == vqd.VQD_ENOTCP
+        vqd.vqd_apply_kraus(ctx, 0, [0], oc.leak_init(0.1))          # CPTN is accepted
+        assert abs(vqd.vqd_trace(ctx, 0) - 0.9) < 1e-15
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_prob(ctx, 0, [0, 0])
+        assert e.value.code == vqd.VQD_EINVAL
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_run_program(ctx, 0, [NativeOp("rx", (0,), (0.1,))], 9)
+        assert e.value.code == vqd.VQD_EINVAL
+    finally:
+        vqd.vqd_destroy(ctx)
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_create(17, vqd.VQD_F32)
+
+
+def test_create_on_caller_memory(vqd):
+    torch = pytest.importorskip("torch")
+    n = 5
+    buf = torch.zeros(2 * 4 ** n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = vqd.vqd_create_on(n, vqd.VQD_F32, buf.data_ptr(), buf.numel() * 4, stream)
+    try:
+        vqd.vqd_init_zero(ctx, 0)
+        vqd.vqd_apply_native(ctx, 0, [NativeOp("h", (q,)) for q in range(n)])
+        torch.cuda.synchronize()
+        v = buf.view(-1, 2).cpu().numpy()
+        assert np.allclose(v[:, 0], 1.0 / 2 ** n, atol=1e-7) and np.allclose(v[:, 1], 0, atol=1e-7)
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- full-size workload (14 qubits)
+@pytest.fixture(scope="module")
+def config2_full_sample():
+    """A full-size (14-qubit) sample of the benchmark program: its first three ops plus the first
+    op of every other kind it uses (ZZ crosstalk, T1/T2 idle, ZX, readout flip), run by the oracle."""
+    prog = config2_sc_grid()
+    picked = list(prog.ops[:3])
+    for name in ("zz_idle", "idle", "zx", "bitflip"):
+        picked.append(next(o for o in prog.ops if o.name == name))
+    sample = Program(prog.n, picked)
+    return sample, evolve.run_program(sample)
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_config2_full_size_sample_and_invariants(vqd, path, config2_full_sample):
+    """At the full 14-qubit size: a sample program element by element against the oracle, and the whole
+    program (complex64, the benchmark configuration) against properties that hold at any size."""
+    sample, want = config2_full_sample
+    got, _ = run_gpu(vqd, sample, "f32", path)
+    assert np.abs(got - want).max() < tol_f32(len(sample.ops))
+    del got
+    prog = config2_sc_grid()
+    ctx = vqd.vqd_create(prog.n, vqd.VQD_F32)
+    try:
+        if path == "plain":
+            vqd.vqd_apply_native(ctx, 0, prog.ops)
+        else:
+            vqd.vqd_run_program(ctx, 0, prog.ops)
+        tr = vqd.vqd_trace(ctx, 0)
+        assert abs(tr - 1) < 1e-4                              # CPTP program: trace 1
+        pr = vqd.vqd_prob(ctx, 0, list(range(14)))
+        assert pr.min() > -1e-6 and abs(pr.sum() - tr.real) < 1e-9
+        pur = vqd.vqd_purity(ctx, 0)
+        assert 2.0 ** -14 - 1e-9 <= pur <= 1.0 + 1e-6
+        # Hermiticity on sampled entries: rho[r][c] = conj(rho[c][r])
+        flat = vqd.vqd_get_state(ctx, 0)
+        rng = np.random.default_rng(3)
+        r, c = rng.integers(0, 2 ** 14, 4096), rng.integers(0, 2 ** 14, 4096)
+        assert np.abs(flat[r + (c << 14)] - np.conj(flat[c + (r << 14)])).max() < 1e-6
+    finally:
+        vqd.vqd_destroy(ctx)

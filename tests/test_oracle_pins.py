@@ -127,6 +127,16 @@ def test_kraus_matches_brute_superoperator(n, targets, nk):
     assert np.allclose(evolve.to_device_layout(got), S @ evolve.to_device_layout(rho), atol=1e-13)
 
 
+def test_superop_application_matches_kraus_form():
+    """A superoperator built as sum conj(K) (x) K (index r | c << k) acts like the Kraus map itself."""
+    rng = np.random.default_rng(17)
+    for n, qs in [(3, (1,)), (4, (3, 0)), (4, (1, 2))]:
+        ks = rand_kraus(2 ** len(qs), 3, rng)
+        S = sum(np.kron(K.conj(), K) for K in ks)
+        rho = rand_state(n, rng)
+        assert np.abs(evolve.apply_superop(rho, qs, S) - evolve.apply_kraus(rho, qs, ks)).max() < 1e-14
+
+
 def test_tensor_and_dense_methods_agree_on_random_program():
     prog = random_program(7, 5, 120)
     a = evolve.run_program(prog, "tensor")
