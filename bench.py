@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--impl", default="vqd", choices=["vqd", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the fused / FP64 / oracle side measurements")
     ap.add_argument("--error", action="store_true", help="also measure the complex64 error against an FP64 run")
+    ap.add_argument("--rows", type=int, default=2, help="grid rows (profiling cases only; the benchmark is 2x7)")
+    ap.add_argument("--cols", type=int, default=7)
+    ap.add_argument("--depth", type=int, default=60)
+    ap.add_argument("--path", default="plain", choices=["plain", "fused"],
+                    help="path of the headline measurement (profiling cases; the benchmark is plain)")
     return ap.parse_args()
 
 
@@ -178,7 +183,7 @@ def main():
     from paper_2306_07342_gb300 import vqd
     from workloads import config2_sc_grid
 
-    prog = config2_sc_grid()
+    prog = config2_sc_grid(rows=args.rows, cols=args.cols, depth=args.depth)
     n = prog.n
     native = vqd.native_ops(prog.ops)
     units_per_step = len(prog.ops) * 4.0 ** n
@@ -253,13 +258,13 @@ def main():
     # ---- headline: plain complex64 kernels
     ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
     clocks = ClockSampler(local)
-    ms, stats, ck = timed(make_step(ctx, "plain"), args.steps, args.warmup, ctx, clocks)
+    ms, stats, ck = timed(make_step(ctx, args.path), args.steps, args.warmup, ctx, clocks)
     value = world * args.steps * units_per_step / (ms * 1e-3)
     dom, roof = roofline(stats, args.steps)
     launches = int(sum(v["launches"] for v in stats.values()) / args.steps)
 
     # ---- end to end through the C ABI with host buffers (wall clock; results read back every step)
-    step = make_step(ctx, "plain")
+    step = make_step(ctx, args.path)
     sync_all()
     t0 = time.perf_counter()
     for _ in range(args.steps):

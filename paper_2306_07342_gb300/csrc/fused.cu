@@ -37,6 +37,133 @@ static int stage_bit_count(uint32_t qmask, int L) {
   return c;
 }
 
+// ---------------------------------------------------------------- composition inside a stage
+// Operators of one stage are merged into composites acting on at most two qubits, in FP64: a run of
+// operators whose qubits stay within one pair becomes a single 4^k x 4^k superoperator (or a
+// 2^k x 2^k unitary when every member is unitary).  Open composites are kept on pairwise disjoint
+// qubit sets; an operator that would join qubits of composites into more than two qubits first
+// emits them.  Every qubit therefore sees its operators in program order.
+struct Composite {
+  int k = 0;
+  int q[2] = {0, 0};
+  bool unitary = true;
+  std::vector<cd> m;
+  double weight = 0;
+};
+
+// Matrix of an operator on qubits `from` (k1) re-expressed on qubits `to` (k2, from within to),
+// identity on the extra qubit.  Unitaries are 2^k square; superoperators 4^k with s = r | c << k.
+static std::vector<cd> embed_on(const std::vector<cd>& m, bool unitary, int k1, const int* from, int k2,
+                                const int* to) {
+  int pos[2] = {0, 0};
+  unsigned mask = 0;
+  for (int j = 0; j < k1; j++) {
+    for (int i = 0; i < k2; i++)
+      if (to[i] == from[j]) pos[j] = i;
+    mask |= 1u << pos[j];
+  }
+  auto sub = [&](int x) {
+    int v = 0;
+    for (int j = 0; j < k1; j++) v |= ((x >> pos[j]) & 1) << j;
+    return v;
+  };
+  const int d2 = 1 << k2, d1 = 1 << k1;
+  if (unitary) {
+    std::vector<cd> o(d2 * d2, 0.0);
+    for (int i = 0; i < d2; i++)
+      for (int j = 0; j < d2; j++)
+        if ((i & ~mask) == (j & ~mask)) o[i * d2 + j] = m[sub(i) * d1 + sub(j)];
+    return o;
+  }
+  const int D2 = d2 * d2, D1 = d1 * d1;
+  std::vector<cd> o(D2 * D2, 0.0);
+  for (int a = 0; a < D2; a++)
+    for (int b = 0; b < D2; b++) {
+      int ra = a & (d2 - 1), ca = a >> k2, rb = b & (d2 - 1), cb = b >> k2;
+      if ((ra & ~mask) != (rb & ~mask) || (ca & ~mask) != (cb & ~mask)) continue;
+      o[a * D2 + b] = m[(sub(ra) | (sub(ca) << k1)) * D1 + (sub(rb) | (sub(cb) << k1))];
+    }
+  return o;
+}
+
+static std::vector<cd> matmul(const std::vector<cd>& a, const std::vector<cd>& b, int d) {
+  std::vector<cd> c(d * d, 0.0);
+  for (int i = 0; i < d; i++)
+    for (int l = 0; l < d; l++) {
+      const cd x = a[i * d + l];
+      if (x == 0.0) continue;
+      for (int j = 0; j < d; j++) c[i * d + j] += x * b[l * d + j];
+    }
+  return c;
+}
+
+static Op composite_to_op(const Composite& c) {
+  Op o;
+  o.k = c.k;
+  o.q[0] = c.q[0];
+  o.q[1] = c.q[1];
+  o.unitary = c.unitary;
+  o.m = c.m;
+  o.weight = c.weight;
+  return o;
+}
+
+static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vector<int>& idx) {
+  std::vector<Op> out;
+  std::vector<Composite> open;
+  for (int i : idx) {
+    const Op& op = ops[i];
+    std::vector<int> hit;
+    int uq[4], nu = 0;
+    for (int j = 0; j < op.k; j++) uq[nu++] = op.q[j];
+    for (size_t x = 0; x < open.size(); x++) {
+      bool inter = false;
+      for (int a = 0; a < open[x].k; a++)
+        for (int j = 0; j < op.k; j++)
+          if (open[x].q[a] == op.q[j]) inter = true;
+      if (!inter) continue;
+      hit.push_back((int)x);
+      for (int a = 0; a < open[x].k; a++) {
+        bool seen = false;
+        for (int u = 0; u < nu; u++)
+          if (uq[u] == open[x].q[a]) seen = true;
+        if (!seen && nu < 4) uq[nu++] = open[x].q[a];
+      }
+    }
+    Composite c;
+    if (nu <= 2) {  // merge the operator with every composite it touches
+      c.k = nu;
+      for (int u = 0; u < nu; u++) c.q[u] = uq[u];
+      c.unitary = op.unitary;
+      for (int x : hit) c.unitary = c.unitary && open[x].unitary;
+      const int d = c.unitary ? (1 << nu) : (1 << (2 * nu));
+      c.m.assign((size_t)d * d, 0.0);
+      for (int a = 0; a < d; a++) c.m[a * d + a] = 1.0;
+      for (int x : hit) {  // disjoint composites commute: their product in any order
+        const Composite& h = open[x];
+        std::vector<cd> hm = (c.unitary || !h.unitary) ? h.m : superop_from_unitary(h.k, h.m.data());
+        c.m = matmul(embed_on(hm, c.unitary, h.k, h.q, nu, c.q), c.m, d);
+        c.weight += h.weight;
+      }
+      std::vector<cd> om = (c.unitary || !op.unitary) ? op.m : superop_from_unitary(op.k, op.m.data());
+      c.m = matmul(embed_on(om, c.unitary, op.k, op.q, nu, c.q), c.m, d);
+      c.weight += op.weight;
+    } else {  // emit what it touches and start afresh
+      for (int x : hit) out.push_back(composite_to_op(open[x]));
+      c.k = op.k;
+      c.q[0] = op.q[0];
+      c.q[1] = op.q[1];
+      c.unitary = op.unitary;
+      c.m = op.m;
+      c.weight = op.weight;
+    }
+    for (int h = (int)hit.size() - 1; h >= 0; h--) open.erase(open.begin() + hit[h]);
+    open.push_back(std::move(c));
+  }
+  for (const Composite& c : open) out.push_back(composite_to_op(c));
+  return out;
+}
+
 static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::vector<int>& idx, uint32_t qmask,
                         int n, int prec, bool whole) {
   StageDesc sd;
@@ -61,8 +188,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
     }
   }
   sd.op_begin = (int)plan.ops.size();
-  for (int i : idx) {
-    const Op& op = ops[i];
+  const std::vector<Op> merged = compose_stage(ops, idx);
+  for (const Op& op : merged) {
     Pass p = classify(op);
     TileOp t;
     std::memset(&t, 0, sizeof(t));
@@ -214,6 +341,14 @@ __device__ __forceinline__ uint32_t insert_zeros32(uint32_t g, const int* pos) {
   return g;
 }
 
+// Shared-memory position of tile element l: the low bits (one 128-byte row) are XORed with the
+// row number, so that the strided member accesses of an operator on a low tile bit spread over
+// all banks.  A permutation within each row; identity for tiles of one row.
+template <class T>
+__device__ __forceinline__ uint32_t sw(uint32_t l) {
+  return sizeof(T) == 4 ? l ^ ((l >> 4) & 15u) : l ^ ((l >> 3) & 7u);
+}
+
 // Deposit the low bits of t at the positions pos[0..cnt) (ascending).
 __device__ __forceinline__ uint64_t deposit(uint64_t t, const int* pos, int cnt) {
   uint64_t r = 0;
@@ -236,8 +371,8 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
   for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
   uint64_t hi = 0;
   for (uint32_t l = threadIdx.x; l < size; l += 256) {
-    if (LOAD) sm[l] = st[base + lo + hi];
-    else st[base + lo + hi] = sm[l];
+    if (LOAD) sm[sw<T>(l)] = st[base + lo + hi];
+    else st[base + lo + hi] = sm[sw<T>(l)];
     hi = ((hi | ~M) + 1ull) & M;
   }
 }
@@ -258,7 +393,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
       for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
         const uint32_t b = insert_zeros32<2>(g, op.lsorted);
 #pragma unroll
-        for (int s = 0; s < 4; s++) sm[b | moff[s]] = cmul<T>(sm[b | moff[s]], f[s]);
+        for (int s = 0; s < 4; s++) sm[sw<T>(b | moff[s])] = cmul<T>(sm[sw<T>(b | moff[s])], f[s]);
       }
     } else {  // KK_SUP1
       cx<T> a[16];
@@ -268,14 +403,14 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
         const uint32_t b = insert_zeros32<2>(g, op.lsorted);
         cx<T> x[4];
 #pragma unroll
-        for (int s = 0; s < 4; s++) x[s] = sm[b | moff[s]];
+        for (int s = 0; s < 4; s++) x[s] = sm[sw<T>(b | moff[s])];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
           cx<T> y;
           y.x = 0; y.y = 0;
 #pragma unroll
           for (int j = 0; j < 4; j++) cmac<T>(y, a[i * 4 + j], x[j]);
-          sm[b | moff[i]] = y;
+          sm[sw<T>(b | moff[i])] = y;
         }
       }
     }
@@ -296,7 +431,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
     for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
       const uint32_t b = insert_zeros32<4>(g, op.lsorted);
 #pragma unroll
-      for (int s = 0; s < 16; s++) sm[b | moff[s]] = cmul<T>(sm[b | moff[s]], csm[s]);
+      for (int s = 0; s < 16; s++) sm[sw<T>(b | moff[s])] = cmul<T>(sm[sw<T>(b | moff[s])], csm[s]);
     }
   } else if (op.kind == KK_UNI2) {
     cx<T> u[16];
@@ -306,7 +441,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
       const uint32_t b = insert_zeros32<4>(g, op.lsorted);
       cx<T> A[16], B[16];
 #pragma unroll
-      for (int s = 0; s < 16; s++) A[s] = sm[b | moff[s]];
+      for (int s = 0; s < 16; s++) A[s] = sm[sw<T>(b | moff[s])];
 #pragma unroll
       for (int r = 0; r < 4; r++)
 #pragma unroll
@@ -329,7 +464,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
             uc.y = -uc.y;
             cmac<T>(acc, uc, B[r | (m << 2)]);
           }
-          sm[b | moff[r | (c << 2)]] = acc;
+          sm[sw<T>(b | moff[r | (c << 2)])] = acc;
         }
     }
   } else {  // KK_SUP2: coefficients read from shared memory (broadcast), one output row at a time
@@ -337,7 +472,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
       const uint32_t b = insert_zeros32<4>(g, op.lsorted);
       cx<T> x[16];
 #pragma unroll
-      for (int s = 0; s < 16; s++) x[s] = sm[b | moff[s]];
+      for (int s = 0; s < 16; s++) x[s] = sm[sw<T>(b | moff[s])];
 #pragma unroll 1
       for (int i = 0; i < 16; i++) {
         cx<T> y;
@@ -348,7 +483,7 @@ __device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, co
 #pragma unroll
         for (int j = 0; j < 4; j++)
           if (i >> j & 1) o |= 1u << op.lbit[j];
-        sm[b | o] = y;
+        sm[sw<T>(b | o)] = y;
       }
     }
   }

@@ -76,7 +76,6 @@ struct Group {
 template <class T> struct Sup1P { Group<4> g; cx<T> s[16]; unsigned char fl[16]; };
 template <class T> struct Uni2P { Group<16> g; cx<T> u[16]; cx<T> uc[16]; unsigned char fl[16]; };
 template <class T> struct Sup2P { Group<16> g; cx<T> s[256]; unsigned char fl[256]; };
-template <class T> struct ElemP { cx<T> f[16]; int pos[4]; int nb; };
 
 #define GRID_STRIDE_LOOP(i, count)                                                         \
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, _st = (uint64_t)gridDim.x * blockDim.x; \
@@ -101,25 +100,27 @@ __global__ void __launch_bounds__(256) k_sup1(cx<T>* __restrict__ st, uint64_t n
   }
 }
 
-// ---- two-qubit unitary: A <- U A U^dagger on the 4x4 block A[r][c] = amplitude r | c << 2
+// ---- two-qubit unitary: A <- U A U^dagger on the 4x4 block A[r][c] = amplitude r | c << 2.
+// Column c of B = U A needs only column c of A, so A is consumed one column at a time and only B
+// (16 amplitudes) stays live; then row r of U A U^dagger needs only row r of B.
 template <class T, bool SPARSE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_uni2(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_uni2(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
   GRID_STRIDE_LOOP(g, ngroups) {
     const uint64_t base = insert_zeros<4>(g, P.g.pos);
-    cx<T> A[16], B[16];
+    cx<T> B[16];
 #pragma unroll
-    for (int s = 0; s < 16; s++) A[s] = st[base + P.g.off[s]];
-    // B = U A : B[r][c] = sum_m U[r][m] A[m][c]
+    for (int c = 0; c < 4; c++) {
+      cx<T> a[4];
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+      for (int m = 0; m < 4; m++) a[m] = st[base + P.g.off[m | (c << 2)]];
 #pragma unroll
-      for (int c = 0; c < 4; c++) {
+      for (int r = 0; r < 4; r++) {
         cx<T> acc; acc.x = 0; acc.y = 0;
 #pragma unroll
-        for (int m = 0; m < 4; m++) mac<SPARSE, T>(acc, P.u[r * 4 + m], P.fl[r * 4 + m], A[m | (c << 2)]);
+        for (int m = 0; m < 4; m++) mac<SPARSE, T>(acc, P.u[r * 4 + m], P.fl[r * 4 + m], a[m]);
         B[r | (c << 2)] = acc;
       }
-    // A = B U^dagger : A[r][c] = sum_m B[r][m] conj(U[c][m])
+    }
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
@@ -127,10 +128,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_uni2(cx<T>* __r
         cx<T> acc; acc.x = 0; acc.y = 0;
 #pragma unroll
         for (int m = 0; m < 4; m++) mac<SPARSE, T>(acc, P.uc[c * 4 + m], P.fl[c * 4 + m], B[r | (m << 2)]);
-        A[r | (c << 2)] = acc;
+        st[base + P.g.off[r | (c << 2)]] = acc;
       }
-#pragma unroll
-    for (int s = 0; s < 16; s++) st[base + P.g.off[s]] = A[s];
   }
 }
 
@@ -152,29 +151,36 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && SPARSE) ? 2 : 1) k_sup
   }
 }
 
-// ---- diagonal superoperator: every amplitude times a factor chosen by its 2k group bits.
-// Four consecutive amplitudes per thread (vector loads); REAL when every factor is real.
+// ---- diagonal superoperator: every member s of a group is scaled by its own factor f[s].
+// Same group walk as the dense kernels, so the factor index is static and the factors stay in
+// registers; REAL when every factor is real (dephasing-type channels).
 template <class T, bool REAL>
 __device__ __forceinline__ void scale(cx<T>& v, const cx<T>& f) {
   if (REAL) { v.x *= f.x; v.y *= f.x; }
-  else { const T re = v.x * f.x - v.y * f.y; v.y = v.x * f.y + v.y * f.x; v.x = re; }
+  else { const T re = fma(v.x, f.x, -v.y * f.y); v.y = fma(v.x, f.y, v.y * f.x); v.x = re; }
+}
+template <class T> struct Diag1P { Group<4> g; cx<T> f[4]; };
+template <class T> struct Diag2P { Group<16> g; cx<T> f[16]; };
+template <class T, bool REAL>
+__global__ void __launch_bounds__(256) k_diag1(cx<T>* __restrict__ st, uint64_t ngroups, const Diag1P<T> P) {
+  GRID_STRIDE_LOOP(g, ngroups) {
+    const uint64_t base = insert_zeros<2>(g, P.g.pos);
+    cx<T> x[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) x[s] = st[base + P.g.off[s]];
+#pragma unroll
+    for (int s = 0; s < 4; s++) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
+  }
 }
 template <class T, bool REAL>
-__global__ void __launch_bounds__(256) k_elem(cx<T>* __restrict__ st, uint64_t nquads, const ElemP<T> P) {
-  GRID_STRIDE_LOOP(qd, nquads) {
-    const uint64_t i0 = qd * 4;
-    cx<T> v[4];
+__global__ void __launch_bounds__(256) k_diag2(cx<T>* __restrict__ st, uint64_t ngroups, const Diag2P<T> P) {
+  GRID_STRIDE_LOOP(g, ngroups) {
+    const uint64_t base = insert_zeros<4>(g, P.g.pos);
+    cx<T> x[16];
 #pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = st[i0 + j];
+    for (int s = 0; s < 16; s++) x[s] = st[base + P.g.off[s]];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const uint64_t i = i0 + j;
-      int s = 0;
-      for (int b = 0; b < P.nb; b++) s |= (int)((i >> P.pos[b]) & 1ull) << b;
-      scale<T, REAL>(v[j], P.f[s]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; j++) st[i0 + j] = v[j];
+    for (int s = 0; s < 16; s++) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
   }
 }
 
@@ -373,20 +379,24 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
   const uint64_t N = 1ull << (2 * n);
   const bool fp64 = sizeof(T) == 8;
   if (p.kind == KK_ELEM) {
-    ElemP<T> P;
-    std::memset(&P, 0, sizeof(P));
-    int bits[4];
-    for (int j = 0; j < p.k; j++) { bits[j] = p.q[j]; bits[j + p.k] = p.q[j] + n; }
-    P.nb = 2 * p.k;
-    for (int b = 0; b < 4; b++) P.pos[b] = b < P.nb ? bits[b] : 0;
     bool real = true;
-    for (size_t i = 0; i < p.coef.size(); i++) {
-      P.f[i] = to_cx<T>(p.coef[i]);
-      if (p.coef[i].imag() != 0.0) real = false;
+    for (const cd& c : p.coef)
+      if (c.imag() != 0.0) real = false;
+    if (p.k == 1) {
+      Diag1P<T> P;
+      P.g = make_group<4>(n, 1, p.q);
+      for (int i = 0; i < 4; i++) P.f[i] = to_cx<T>(p.coef[i]);
+      const uint64_t ng = N / 4;
+      if (real) k_diag1<T, true><<<grid_for(k_diag1<T, true>, ng), 256, 0, s>>>(st, ng, P);
+      else k_diag1<T, false><<<grid_for(k_diag1<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    } else {
+      Diag2P<T> P;
+      P.g = make_group<16>(n, 2, p.q);
+      for (int i = 0; i < 16; i++) P.f[i] = to_cx<T>(p.coef[i]);
+      const uint64_t ng = N / 16;
+      if (real) k_diag2<T, true><<<grid_for(k_diag2<T, true>, ng), 256, 0, s>>>(st, ng, P);
+      else k_diag2<T, false><<<grid_for(k_diag2<T, false>, ng), 256, 0, s>>>(st, ng, P);
     }
-    const uint64_t nq = N / 4;
-    if (real) k_elem<T, true><<<grid_for(k_elem<T, true>, nq), 256, 0, s>>>(st, nq, P);
-    else k_elem<T, false><<<grid_for(k_elem<T, false>, nq), 256, 0, s>>>(st, nq, P);
     return cudaGetLastError();
   }
   if (p.kind == KK_SUP1) {
