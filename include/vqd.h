@@ -223,6 +223,34 @@ int vqd_get_state(vqd_t ctx, int inst, vqd_c128* host_out);
 int vqd_set_state(vqd_t ctx, int inst, const vqd_c128* host_in);
 
 /* ------------------------------------------------------------------------------------------
+ * Allocation-free reduction (the paper has no counterpart: this serves callers of the library)
+ *
+ * vqd_prob_static computes the same marginal Z-basis probabilities as vqd_prob, for callers that
+ * cannot allocate device memory: a host process whose framework's memory pool already owns all of
+ * the GPU's memory, or a latency-critical loop that must not pay for the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  It needs no context and calls no cudaMalloc,
+ * cudaFree or any other allocating routine.  Its partial sums live in a file-scope device array of
+ * 2^14 doubles (128 KB), which every GPU that loads libvqd holds until the process exits.
+ *
+ *   dev_state  device address of an n-qubit state in the layout above (complex64 if prec ==
+ *              VQD_F32, else complex128); read only.
+ *   qubits     host array of m distinct qubits, 1 <= m <= VQD_PROB_STATIC_MAX_M (qubits[0] is the
+ *              least significant bit of the output index, as in vqd_prob).
+ *   dev_out    DEVICE array of 2^m doubles, written on `stream` (a cudaStream_t; NULL = legacy
+ *              default stream).  The call is asynchronous: synchronise the stream before reading.
+ *
+ * Returns VQD_OK, VQD_EINVAL (bad argument, or m above VQD_PROB_STATIC_MAX_M: the static scratch
+ * holds at most 2^14 partial sums) or VQD_EDEVICE; the message is in vqd_last_error(NULL).
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and keeps it; make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites what the previous one left there: calls that
+ * overlap on the GPU (other streams, or other host threads) race, so serialise them.
+ * ---------------------------------------------------------------------------------------- */
+#define VQD_PROB_STATIC_MAX_M 14
+int vqd_prob_static(const void* dev_state, int n, int prec, int m, const int* qubits, double* dev_out,
+                    void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Launch accounting: per kernel class, the number of launches, their summed device time
  * (CUDA events recorded on the context stream around every launch while enabled) and the
  * algorithmic bytes they move.  Used to report achieved bandwidth against the roofline.

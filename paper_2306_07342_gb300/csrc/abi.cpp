@@ -203,6 +203,13 @@ static vqd_ctx* make_ctx(int count, const int* n, int prec, void* stream, void* 
   return c.release();
 }
 
+namespace vqd {
+int report_static_error(int code, const char* msg) {
+  set_err(nullptr, msg);
+  return code;
+}
+}  // namespace vqd
+
 // ================================================================== exported API
 extern "C" {
 

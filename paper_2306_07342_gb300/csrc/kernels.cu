@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -552,4 +553,79 @@ cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const 
   return expect_t<double>((const cx<double>*)state, n, nterms, xmask, zymask, scratch, out, s);
 }
 
+// ================================================================== allocation-free probabilities
+// vqd_prob_static: the marginal-probability reduction with its partial sums in a file-scope device
+// array instead of memory from cudaMalloc.  Every GPU that loads the library holds this array
+// (128 KB) until the process exits.  Host code must not use the array's name as a device address;
+// the address comes from cudaGetSymbolAddress, taken once per device with that device current.
+static const int kStaticPartials = 1 << 14;
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+static std::mutex g_static_mu;
+static double* g_static_ptr[64] = {nullptr};
+
+static cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_partials);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = (double*)p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t prob_static_t(const cx<T>* st, int n, int m, const int* qubits, double* scratch, double* out,
+                                 cudaStream_t s) {
+  ProbP P;
+  std::memset(&P, 0, sizeof(P));
+  P.m = m;
+  unsigned used = 0;
+  for (int j = 0; j < m; j++) { P.meas[j] = qubits[j]; used |= 1u << qubits[j]; }
+  for (int q = 0; q < n; q++)
+    if (!(used >> q & 1)) P.rest[P.nr++] = q;
+  const uint64_t bins = 1ull << m, per_bin = 1ull << P.nr;
+  // bins * chunks <= kStaticPartials (bins <= kStaticPartials is checked by the caller)
+  const uint64_t chunks = std::min<uint64_t>(per_bin, (uint64_t)kStaticPartials / bins);
+  k_prob<T><<<grid_for(k_prob<T>, bins * chunks), 256, 0, s>>>(st, n, P, chunks, per_bin / chunks, scratch);
+  k_sum_rows<<<(unsigned)bins, 256, 0, s>>>(scratch, chunks, (int)chunks, 1, out);
+  return cudaGetLastError();
+}
+
 }  // namespace vqd
+
+extern "C" int vqd_prob_static(const void* dev_state, int n, int prec, int m, const int* qubits, double* dev_out,
+                               void* stream) {
+  using namespace vqd;
+  if (!dev_state || !qubits || !dev_out) return report_static_error(VQD_EINVAL, "vqd_prob_static: NULL argument");
+  if (n < 1 || n > VQD_MAX_QUBITS) return report_static_error(VQD_EINVAL, "vqd_prob_static: n outside 1..16");
+  if (prec != VQD_F64 && prec != VQD_F32) return report_static_error(VQD_EINVAL, "vqd_prob_static: bad precision");
+  if (m < 1 || m > n) return report_static_error(VQD_EINVAL, "vqd_prob_static: need 1 <= m <= n measured qubits");
+  if (m > VQD_PROB_STATIC_MAX_M)
+    return report_static_error(VQD_EINVAL,
+                               "vqd_prob_static: more than 14 measured qubits; its static scratch holds 2^14 partial sums");
+  unsigned used = 0;
+  for (int j = 0; j < m; j++) {
+    if (qubits[j] < 0 || qubits[j] >= n || (used >> qubits[j] & 1))
+      return report_static_error(VQD_EINVAL, "vqd_prob_static: measured qubit out of range or repeated");
+    used |= 1u << qubits[j];
+  }
+  double* scratch = nullptr;
+  cudaError_t e = static_scratch(&scratch);
+  if (e == cudaSuccess) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == VQD_F32) e = prob_static_t<float>((const cx<float>*)dev_state, n, m, qubits, scratch, dev_out, s);
+    else e = prob_static_t<double>((const cx<double>*)dev_state, n, m, qubits, scratch, dev_out, s);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return report_static_error(VQD_EDEVICE, cudaGetErrorString(e));
+  }
+  return VQD_OK;
+}

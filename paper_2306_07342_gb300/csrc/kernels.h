@@ -32,4 +32,7 @@ cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const 
 
 int num_sms();
 
+// Records the message of a failed vqd_prob_static call for vqd_last_error(NULL); returns code.
+int report_static_error(int code, const char* msg);
+
 }  // namespace vqd

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "vqd_profile": (I, [P, I]),
             "vqd_profile_reset": (I, [P]),
             "vqd_profile_read": (I, [P, I, P, P]),
+            "vqd_prob_static": (I, [P, I, I, I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -275,6 +276,16 @@ def vqd_get_state(ctx, inst: int = 0) -> np.ndarray:
 def vqd_set_state(ctx, inst: int, flat) -> None:
     a = _c128(flat).reshape(-1)
     _check(lib().vqd_set_state(ctx, inst, _ptr(a)), ctx)
+
+
+VQD_PROB_STATIC_MAX_M = 14
+
+
+def vqd_prob_static(dev_state: int, n: int, prec: int, qubits: Sequence[int], dev_out: int, stream: int = 0):
+    """Allocation-free marginal probabilities into a caller-owned DEVICE array of 2^m doubles (asynchronous)."""
+    q = _i32(qubits)
+    _check(lib().vqd_prob_static(ctypes.c_void_p(dev_state), n, prec, len(q), _ptr(q), ctypes.c_void_p(dev_out),
+                                 ctypes.c_void_p(stream)))
 
 
 def vqd_profile(ctx, mode: int):
