@@ -195,6 +195,12 @@ int vqd_run_batch(vqd_t ctx, const int64_t* offsets, const vqd_native_op* ops, i
 int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int* k, int* targets,
                    vqd_c128* mat);
 
+/* Plan of the fused path for an n-qubit program, without running it (host only).  info[0..7] =
+ * {stages (one pass over the state each), blocks (one shared-memory sweep each), operators after
+ * composition that are diagonal / 1-qubit superoperators / 2-qubit unitaries / 2-qubit
+ * superoperators, largest tile (index bits), original operators}. */
+int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags, int64_t* info);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);

@@ -401,7 +401,6 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
     upd += (double)lists[i].size() * std::ldexp(1.0, 2 * c->n[i]);
   }
   timed(c, SC_BATCH, bytes, upd, 1, [&] { return launch_batch(c->fused, plan, c->prec, c->base, c->stream); });
-  cuda_check(batch_status(c->fused, c->stream), "batched kernel");
   API_END(c)
 }
 
@@ -413,6 +412,37 @@ int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int
   *k = o.k;
   for (int j = 0; j < o.k; j++) targets[j] = o.q[j];
   for (size_t i = 0; i < o.m.size(); i++) mat[i] = {o.m[i].real(), o.m[i].imag()};
+  API_END(nullptr)
+}
+
+int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags,
+                  int64_t* info) {
+  API_BEGIN
+  if (!info || n < 1 || n > VQD_MAX_QUBITS || nops < 0 || (nops > 0 && !ops)) throw Error(VQD_EINVAL, "bad argument");
+  if (prec != VQD_F64 && prec != VQD_F32) throw Error(VQD_EINVAL, "bad precision");
+  std::vector<Op> list;
+  list.reserve(nops);
+  for (int i = 0; i < nops; i++) {
+    int ar = native_arity(ops[i].code);
+    if (ar < 1) throw Error(VQD_EINVAL, "unknown native op code");
+    for (int j = 0; j < ar; j++)
+      if (ops[i].q[j] < 0 || ops[i].q[j] >= n || (j == 1 && ops[i].q[1] == ops[i].q[0]))
+        throw Error(VQD_EINVAL, "bad target qubit");
+    list.push_back(compile_native(ops[i], flags));
+  }
+  FusedPlan plan = plan_fused(list, n, prec, fuse_qubits);
+  for (int i = 0; i < 8; i++) info[i] = 0;
+  info[0] = (int64_t)plan.stages.size();
+  info[1] = (int64_t)plan.blocks.size();
+  for (const BlockOp& t : plan.ops) {
+    const int cls = (t.kind == BK_DIAG_A || t.kind == BK_DIAG_B || t.kind == BK_DIAG2) ? 0
+                    : (t.kind == BK_SUP1_A || t.kind == BK_SUP1_B)                     ? 1
+                    : t.kind == BK_UNI2                                                ? 2
+                                                                                       : 3;
+    info[2 + cls] += 1;
+  }
+  info[6] = plan.max_bits;
+  info[7] = nops;
   API_END(nullptr)
 }
 

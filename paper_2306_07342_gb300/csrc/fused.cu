@@ -3,8 +3,11 @@
 // A stage owns a set Q of at most `fuse_qubits` qubits.  Its tile holds the 2^m amplitudes that
 // share one assignment of every index bit outside B = {q, q + n : q in Q} u {low row bits}; the
 // low row bits are carried along so that each tile is made of runs of >= 64 contiguous bytes
-// (full DRAM sectors).  A CTA loads a tile once, applies every operator of the stage to it in
-// shared memory, and stores it once: one pass over HBM per stage instead of one per operator.
+// (full DRAM sectors).  A CTA loads a tile once, applies every operator of the stage to it, and
+// stores it once: one pass over HBM per stage instead of one per operator.  Inside the tile the
+// operators are grouped into blocks on one qubit or one pair of qubits; a thread holds the 4 or 16
+// amplitudes of a block's group in registers and applies all of the block's operators to them, so
+// that shared memory is swept once per block, not once per operator.
 //
 // Stages are formed greedily in program order with a commuting lookahead: an operator that does
 // not fit the current stage is deferred, and later operators may still join the stage as long
@@ -26,7 +29,7 @@ namespace vqd {
 
 int tile_bits_budget(int prec) { return prec == VQD_F32 ? 13 : 12; }  // 64 KB tiles
 static int passenger_bits(int prec) { return prec == VQD_F32 ? 3 : 2; }  // 64-byte runs
-static int default_fuse(int prec) { (void)prec; return 5; }
+static int default_fuse(int prec) { (void)prec; return 6; }
 
 static int popc(uint32_t x) { return __builtin_popcount(x); }
 
@@ -37,20 +40,7 @@ static int stage_bit_count(uint32_t qmask, int L) {
   return c;
 }
 
-// ---------------------------------------------------------------- composition inside a stage
-// Operators of one stage are merged into composites acting on at most two qubits, in FP64: a run of
-// operators whose qubits stay within one pair becomes a single 4^k x 4^k superoperator (or a
-// 2^k x 2^k unitary when every member is unitary).  Open composites are kept on pairwise disjoint
-// qubit sets; an operator that would join qubits of composites into more than two qubits first
-// emits them.  Every qubit therefore sees its operators in program order.
-struct Composite {
-  int k = 0;
-  int q[2] = {0, 0};
-  bool unitary = true;
-  std::vector<cd> m;
-  double weight = 0;
-};
-
+// ---------------------------------------------------------------- operator algebra (FP64, host)
 // Matrix of an operator on qubits `from` (k1) re-expressed on qubits `to` (k2, from within to),
 // identity on the extra qubit.  Unitaries are 2^k square; superoperators 4^k with s = r | c << k.
 static std::vector<cd> embed_on(const std::vector<cd>& m, bool unitary, int k1, const int* from, int k2,
@@ -97,20 +87,48 @@ static std::vector<cd> matmul(const std::vector<cd>& a, const std::vector<cd>& b
   return c;
 }
 
-static Op composite_to_op(const Composite& c) {
-  Op o;
-  o.k = c.k;
-  o.q[0] = c.q[0];
-  o.q[1] = c.q[1];
-  o.unitary = c.unitary;
-  o.m = c.m;
-  o.weight = c.weight;
-  return o;
+static bool is_diag(const Op& op) {
+  const int d = op.unitary ? (1 << op.k) : (1 << (2 * op.k));
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++)
+      if (i != j && op.m[(size_t)i * d + j] != 0.0) return false;
+  return true;
+}
+static bool is_dense2(const Op& op) { return op.k == 2 && !op.unitary && !is_diag(op); }
+
+// second o first, on the union of their qubits (at most two).
+static Op compose(const Op& first, const Op& second) {
+  Op r;
+  int u[2], nu = 0;
+  for (int j = 0; j < first.k; j++) u[nu++] = first.q[j];
+  for (int j = 0; j < second.k; j++) {
+    bool seen = false;
+    for (int i = 0; i < nu; i++) seen = seen || u[i] == second.q[j];
+    if (!seen) u[nu++] = second.q[j];
+  }
+  r.k = nu;
+  r.q[0] = u[0];
+  r.q[1] = nu > 1 ? u[1] : 0;
+  r.unitary = first.unitary && second.unitary;
+  auto lift = [&](const Op& o) {
+    std::vector<cd> m = (r.unitary || !o.unitary) ? o.m : superop_from_unitary(o.k, o.m.data());
+    return embed_on(m, r.unitary, o.k, o.q, nu, r.q);
+  };
+  const int d = r.unitary ? (1 << nu) : (1 << (2 * nu));
+  r.m = matmul(lift(second), lift(first), d);
+  r.weight = first.weight + second.weight;
+  return r;
 }
 
+// ---------------------------------------------------------------- composition inside a stage
+// The stage's operators are merged into composites on at most two qubits, in FP64.  Open
+// composites are kept on pairwise disjoint qubit sets; an operator merges with the composites it
+// touches when their qubits and its own number at most two, otherwise it first emits them, so
+// every qubit sees its operators in program order.  A merge that would build a dense two-qubit
+// superoperator out of cheaper pieces is refused: applied in shared memory it costs 16 complex
+// MACs and 16 coefficient loads per amplitude, more than the pieces.
 static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vector<int>& idx) {
-  std::vector<Op> out;
-  std::vector<Composite> open;
+  std::vector<Op> out, open;
   for (int i : idx) {
     const Op& op = ops[i];
     std::vector<int> hit;
@@ -119,53 +137,80 @@ static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vect
     for (size_t x = 0; x < open.size(); x++) {
       bool inter = false;
       for (int a = 0; a < open[x].k; a++)
-        for (int j = 0; j < op.k; j++)
-          if (open[x].q[a] == op.q[j]) inter = true;
+        for (int j = 0; j < op.k; j++) inter = inter || open[x].q[a] == op.q[j];
       if (!inter) continue;
       hit.push_back((int)x);
       for (int a = 0; a < open[x].k; a++) {
         bool seen = false;
-        for (int u = 0; u < nu; u++)
-          if (uq[u] == open[x].q[a]) seen = true;
+        for (int u = 0; u < nu; u++) seen = seen || uq[u] == open[x].q[a];
         if (!seen && nu < 4) uq[nu++] = open[x].q[a];
       }
     }
-    Composite c;
-    if (nu <= 2) {  // merge the operator with every composite it touches
-      c.k = nu;
-      for (int u = 0; u < nu; u++) c.q[u] = uq[u];
-      c.unitary = op.unitary;
-      for (int x : hit) c.unitary = c.unitary && open[x].unitary;
-      const int d = c.unitary ? (1 << nu) : (1 << (2 * nu));
-      c.m.assign((size_t)d * d, 0.0);
-      for (int a = 0; a < d; a++) c.m[a * d + a] = 1.0;
-      for (int x : hit) {  // disjoint composites commute: their product in any order
-        const Composite& h = open[x];
-        std::vector<cd> hm = (c.unitary || !h.unitary) ? h.m : superop_from_unitary(h.k, h.m.data());
-        c.m = matmul(embed_on(hm, c.unitary, h.k, h.q, nu, c.q), c.m, d);
-        c.weight += h.weight;
+    bool merged = false;
+    if (nu <= 2 && !hit.empty()) {
+      Op c = open[hit[0]];
+      bool dense_in = is_dense2(c) || is_dense2(op);
+      for (size_t h = 1; h < hit.size(); h++) {
+        dense_in = dense_in || is_dense2(open[hit[h]]);
+        c = compose(c, open[hit[h]]);  // disjoint composites commute
       }
-      std::vector<cd> om = (c.unitary || !op.unitary) ? op.m : superop_from_unitary(op.k, op.m.data());
-      c.m = matmul(embed_on(om, c.unitary, op.k, op.q, nu, c.q), c.m, d);
-      c.weight += op.weight;
-    } else {  // emit what it touches and start afresh
-      for (int x : hit) out.push_back(composite_to_op(open[x]));
-      c.k = op.k;
-      c.q[0] = op.q[0];
-      c.q[1] = op.q[1];
-      c.unitary = op.unitary;
-      c.m = op.m;
-      c.weight = op.weight;
+      c = compose(c, op);
+      if (!(is_dense2(c) && !dense_in)) {
+        for (int h = (int)hit.size() - 1; h >= 0; h--) open.erase(open.begin() + hit[h]);
+        open.push_back(std::move(c));
+        merged = true;
+      }
     }
-    for (int h = (int)hit.size() - 1; h >= 0; h--) open.erase(open.begin() + hit[h]);
-    open.push_back(std::move(c));
+    if (!merged) {
+      for (int x : hit) out.push_back(open[x]);
+      for (int h = (int)hit.size() - 1; h >= 0; h--) open.erase(open.begin() + hit[h]);
+      open.push_back(op);
+    }
   }
-  for (const Composite& c : open) out.push_back(composite_to_op(c));
+  for (Op& c : open) out.push_back(std::move(c));
   return out;
+}
+
+// Coefficients of one member inside a block on qubits bq (nq of them); returns the kind.
+static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& out) {
+  if (op.k == 1) {
+    const bool on_b = nq == 2 && op.q[0] == bq[1];
+    if (is_diag(op)) {  // factor of member t = r | c << 1
+      for (int t = 0; t < 4; t++) {
+        const int r = t & 1, c = t >> 1;
+        out.push_back(op.unitary ? op.m[r * 2 + r] * std::conj(op.m[c * 2 + c]) : op.m[t * 5]);
+      }
+      return on_b ? BK_DIAG_B : BK_DIAG_A;
+    }
+    std::vector<cd> S = op.unitary ? superop_from_unitary(1, op.m.data()) : op.m;
+    out.insert(out.end(), S.begin(), S.end());
+    return on_b ? BK_SUP1_B : BK_SUP1_A;
+  }
+  std::vector<cd> m = embed_on(op.m, op.unitary, 2, op.q, 2, bq);  // qubit order of the block
+  if (is_diag(op)) {  // factor of member t = r | c << 2
+    for (int t = 0; t < 16; t++) {
+      const int r = t & 3, c = t >> 2;
+      out.push_back(op.unitary ? m[r * 4 + r] * std::conj(m[c * 4 + c]) : m[t * 17]);
+    }
+    return BK_DIAG2;
+  }
+  out.insert(out.end(), m.begin(), m.end());
+  return op.unitary ? BK_UNI2 : BK_SUP2;
 }
 
 static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::vector<int>& idx, uint32_t qmask,
                         int n, int prec, bool whole) {
+  // Blocks, members and their coefficients first: a stage whose coefficients overflow the shared
+  // memory budget is split in two (each half is a valid stage on the same tile).
+  const std::vector<Op> comp = compose_stage(ops, idx);
+  size_t ncoef = 0;
+  for (const Op& o : comp) ncoef += is_diag(o) ? (o.k == 1 ? 4 : 16) : (o.k == 1 ? 16 : (o.unitary ? 16 : 256));
+  if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap) && idx.size() > 1) {
+    std::vector<int> a(idx.begin(), idx.begin() + idx.size() / 2), b(idx.begin() + idx.size() / 2, idx.end());
+    build_stage(plan, ops, a, qmask, n, prec, whole);
+    build_stage(plan, ops, b, qmask, n, prec, whole);
+    return;
+  }
   StageDesc sd;
   std::memset(&sd, 0, sizeof(sd));
   bool in_tile[2 * VQD_MAX_QUBITS] = {false};
@@ -187,32 +232,36 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
       sd.rest[sd.nrest++] = b;
     }
   }
+  sd.block_begin = (int)plan.blocks.size();
+  sd.coef_begin = (int)plan.coef.size();
   sd.op_begin = (int)plan.ops.size();
-  const std::vector<Op> merged = compose_stage(ops, idx);
-  for (const Op& op : merged) {
-    Pass p = classify(op);
-    TileOp t;
-    std::memset(&t, 0, sizeof(t));
-    t.kind = p.kind;
-    t.nb = 2 * op.k;
-    for (int j = 0; j < op.k; j++) {
-      t.lbit[j] = local[op.q[j]];
-      t.lbit[j + op.k] = local[op.q[j] + n];
+  for (const Op& o : comp) {
+    TileBlock tb;
+    std::memset(&tb, 0, sizeof(tb));
+    tb.nq = o.k;
+    for (int j = 0; j < tb.nq; j++) {
+      tb.lbit[j] = local[o.q[j]];
+      tb.lbit[j + tb.nq] = local[o.q[j] + n];
     }
-    for (int j = 0; j < t.nb; j++)
-      if (t.lbit[j] < 0) throw Error(VQD_EINVAL, "internal: operator outside its stage tile");
-    for (int j = 0; j < t.nb; j++) t.lsorted[j] = t.lbit[j];
-    std::sort(t.lsorted, t.lsorted + t.nb);
-    t.coef = (int)plan.coef.size();
-    t.ncoef = (int)p.coef.size();
-    t.real = 1;
-    for (const cd& c : p.coef)
-      if (c.imag() != 0.0) t.real = 0;
-    plan.coef.insert(plan.coef.end(), p.coef.begin(), p.coef.end());
-    plan.ops.push_back(t);
-    sd.weight += op.weight;
+    const int nb = 2 * tb.nq;
+    for (int j = 0; j < nb; j++)
+      if (tb.lbit[j] < 0) throw Error(VQD_EINVAL, "internal: operator outside its stage tile");
+    for (int j = 0; j < nb; j++) tb.lsorted[j] = tb.lbit[j];
+    std::sort(tb.lsorted, tb.lsorted + nb);
+    tb.op_begin = (int)plan.ops.size();
+    BlockOp bo;
+    bo.coef = (int)plan.coef.size() - sd.coef_begin;
+    bo.kind = member_coefs(o, o.k, o.q, plan.coef);
+    plan.ops.push_back(bo);
+    sd.weight += o.weight;
+    tb.op_end = (int)plan.ops.size();
+    plan.blocks.push_back(tb);
   }
+  sd.block_end = (int)plan.blocks.size();
+  sd.coef_end = (int)plan.coef.size();
   sd.op_end = (int)plan.ops.size();
+  if (sd.coef_end - sd.coef_begin > kCoefCap || sd.op_end - sd.op_begin > kOpCap)
+    throw Error(VQD_EINVAL, "internal: stage coefficients exceed budget");
   plan.max_bits = std::max(plan.max_bits, sd.nbits);
   plan.stages.push_back(sd);
 }
@@ -234,14 +283,13 @@ FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubit
   const size_t kWindow = 1024;
   std::vector<int> remaining(ops.size());
   for (size_t i = 0; i < ops.size(); i++) remaining[i] = (int)i;
-  size_t head = 0;  // remaining[head..] is the unplanned suffix
   std::vector<int> stage, deferred;
-  while (head < remaining.size()) {
+  while (!remaining.empty()) {
     stage.clear();
     deferred.clear();
     uint32_t q = 0, dmask = 0;
-    size_t i = head;
-    for (; i < remaining.size() && i - head < kWindow; i++) {
+    size_t i = 0;
+    for (; i < remaining.size() && i < kWindow; i++) {
       const Op& op = ops[remaining[i]];
       uint32_t m = 0;
       for (int j = 0; j < op.k; j++) m |= 1u << op.q[j];
@@ -258,20 +306,17 @@ FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubit
           dmask |= m;
         }
       }
-      if ((dmask | q) == full && dmask == full) {
+      if (dmask == full) {
         i++;
         break;
       }
     }
     build_stage(plan, ops, stage, q, n, prec, false);
-    // new suffix: deferred operators (in order) followed by the unscanned rest
-    size_t rest = remaining.size() - i;
     std::vector<int> next;
-    next.reserve(deferred.size() + rest);
+    next.reserve(deferred.size() + remaining.size() - i);
     next.insert(next.end(), deferred.begin(), deferred.end());
     next.insert(next.end(), remaining.begin() + i, remaining.end());
     remaining.swap(next);
-    head = 0;
   }
   return plan;
 }
@@ -287,16 +332,22 @@ BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vecto
     bi.offset_amps = byte_offsets[i] / esz;
     bi.n = n[i];
     bi.stage_begin = (int)bp.all.stages.size();
-    const int op0 = (int)bp.all.ops.size(), c0 = (int)bp.all.coef.size();
+    const int b0 = (int)bp.all.blocks.size(), o0 = (int)bp.all.ops.size(), c0 = (int)bp.all.coef.size();
     for (StageDesc sd : p.stages) {
-      sd.op_begin += op0;
-      sd.op_end += op0;
+      sd.block_begin += b0;
+      sd.block_end += b0;
+      sd.op_begin += o0;
+      sd.op_end += o0;
+      sd.coef_begin += c0;
+      sd.coef_end += c0;
       bp.all.stages.push_back(sd);
     }
-    for (TileOp t : p.ops) {
-      t.coef += c0;
-      bp.all.ops.push_back(t);
+    for (TileBlock t : p.blocks) {
+      t.op_begin += o0;
+      t.op_end += o0;
+      bp.all.blocks.push_back(t);
     }
+    bp.all.ops.insert(bp.all.ops.end(), p.ops.begin(), p.ops.end());
     bp.all.coef.insert(bp.all.coef.end(), p.coef.begin(), p.coef.end());
     bp.all.max_bits = std::max(bp.all.max_bits, p.max_bits);
     bi.stage_end = (int)bp.all.stages.size();
@@ -342,8 +393,8 @@ __device__ __forceinline__ uint32_t insert_zeros32(uint32_t g, const int* pos) {
 }
 
 // Shared-memory position of tile element l: the low bits (one 128-byte row) are XORed with the
-// row number, so that the strided member accesses of an operator on a low tile bit spread over
-// all banks.  A permutation within each row; identity for tiles of one row.
+// row number, so that the strided member accesses of a block on a low tile bit spread over all
+// banks.  A permutation within each row; identity for tiles of one row.
 template <class T>
 __device__ __forceinline__ uint32_t sw(uint32_t l) {
   return sizeof(T) == 4 ? l ^ ((l >> 4) & 15u) : l ^ ((l >> 3) & 7u);
@@ -356,9 +407,10 @@ __device__ __forceinline__ uint64_t deposit(uint64_t t, const int* pos, int cnt)
   return r;
 }
 
-// Move one tile between HBM and shared memory.  Local index l = tid + it * blockDim; its global
-// offset is deposit(l, bits) = deposit(tid) + deposit(it * blockDim), the second advanced with
-// the masked-increment identity next = ((x | ~M) + 1) & M.
+// Move one tile between HBM and shared memory.  Local index l = tid + it * 256; its global offset
+// is deposit(l, bits) = deposit(tid) + deposit(it * 256), the second advanced with the
+// masked-increment identity next = ((x | ~M) + 1) & M.  Each thread moves its amplitudes in
+// batches of 16 independent accesses, so that 16 loads per thread are in flight at once.
 template <class T, bool LOAD>
 __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base, const int* bits,
                                         int nbits) {
@@ -369,165 +421,206 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
   for (int j = 0; j < lowbits; j++) lo |= (uint64_t)((threadIdx.x >> j) & 1u) << bits[j];
   uint64_t M = 0;
   for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
+  const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
   uint64_t hi = 0;
-  for (uint32_t l = threadIdx.x; l < size; l += 256) {
-    if (LOAD) sm[sw<T>(l)] = st[base + lo + hi];
-    else st[base + lo + hi] = sm[sw<T>(l)];
-    hi = ((hi | ~M) + 1ull) & M;
+  constexpr int K = 8;
+  for (int it0 = 0; it0 < iters; it0 += K) {
+    cx<T> v[K];
+    uint64_t h = hi;
+    if (LOAD) {
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (it0 + k < iters) v[k] = st[base + lo + h];
+        h = ((h | ~M) + 1ull) & M;
+      }
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (it0 + k < iters) sm[sw<T>(threadIdx.x + 256u * (uint32_t)(it0 + k))] = v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (it0 + k < iters) v[k] = sm[sw<T>(threadIdx.x + 256u * (uint32_t)(it0 + k))];
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (it0 + k < iters) st[base + lo + h] = v[k];
+        h = ((h | ~M) + 1ull) & M;
+      }
+    }
+    hi = h;
   }
 }
 
-// Apply one operator to the tile in shared memory; csm holds its coefficients.
-template <class T>
-__device__ __forceinline__ void tile_apply(cx<T>* __restrict__ sm, int nbits, const TileOp& op,
-                                           const cx<T>* __restrict__ csm) {
-  if (op.nb == 2) {
-    uint32_t moff[4];
+// ---- one operator, one sweep over the tile.  Each kind has its own loop with the operator's
+// coefficients in registers (loaded once per sweep from shared memory); member s of a group is
+// r | c << k over the operator's tile bits.  The XOR swizzle is linear: sw(base | off) =
+// sw(base) ^ sw(off), so a member address costs one XOR.
+template <class T, bool DIAG>
+__device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
+                                       const cx<T>* __restrict__ c) {
+  const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
+  const uint32_t ng = 1u << (nbits - 2);
+  cx<T> S[DIAG ? 4 : 16];
 #pragma unroll
-    for (int s = 0; s < 4; s++) moff[s] = ((s & 1) ? 1u << op.lbit[0] : 0u) | ((s & 2) ? 1u << op.lbit[1] : 0u);
-    const uint32_t ng = 1u << (nbits - 2);
-    if (op.kind == KK_ELEM) {
-      cx<T> f[4];
+  for (int i = 0; i < (DIAG ? 4 : 16); i++) S[i] = c[i];
+  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+    const uint32_t b = sw<T>(insert_zeros32<2>(g, B.lsorted));
+    const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
+    cx<T> x[4];
 #pragma unroll
-      for (int s = 0; s < 4; s++) f[s] = csm[s];
-      for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-        const uint32_t b = insert_zeros32<2>(g, op.lsorted);
+    for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
+    if (DIAG) {
 #pragma unroll
-        for (int s = 0; s < 4; s++) sm[sw<T>(b | moff[s])] = cmul<T>(sm[sw<T>(b | moff[s])], f[s]);
-      }
-    } else {  // KK_SUP1
-      cx<T> a[16];
+      for (int t = 0; t < 4; t++) sm[a[t]] = cmul<T>(x[t], S[t]);
+    } else {
 #pragma unroll
-      for (int i = 0; i < 16; i++) a[i] = csm[i];
-      for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-        const uint32_t b = insert_zeros32<2>(g, op.lsorted);
-        cx<T> x[4];
+      for (int t = 0; t < 4; t++) {
+        cx<T> y;
+        y.x = 0; y.y = 0;
 #pragma unroll
-        for (int s = 0; s < 4; s++) x[s] = sm[sw<T>(b | moff[s])];
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          cx<T> y;
-          y.x = 0; y.y = 0;
-#pragma unroll
-          for (int j = 0; j < 4; j++) cmac<T>(y, a[i * 4 + j], x[j]);
-          sm[sw<T>(b | moff[i])] = y;
-        }
+        for (int u = 0; u < 4; u++) cmac<T>(y, S[t * 4 + u], x[u]);
+        sm[a[t]] = y;
       }
     }
-    return;
   }
-  // two-qubit operators: 16-member groups, member s = r | c << 2
-  uint32_t moff[16];
+}
+
+// kind: BK_DIAG2, BK_UNI2 (U A U^dagger on the 4x4 block A[r][c] = member r | c << 2) or BK_SUP2
+template <class T, int KIND>
+__device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
+                                       const cx<T>* __restrict__ c) {
+  uint32_t soff[16];
 #pragma unroll
   for (int s = 0; s < 16; s++) {
     uint32_t o = 0;
 #pragma unroll
     for (int j = 0; j < 4; j++)
-      if (s >> j & 1) o |= 1u << op.lbit[j];
-    moff[s] = o;
+      if (s >> j & 1) o |= 1u << B.lbit[j];
+    soff[s] = sw<T>(o);
   }
   const uint32_t ng = 1u << (nbits - 4);
-  if (op.kind == KK_ELEM) {
-    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-      const uint32_t b = insert_zeros32<4>(g, op.lsorted);
+  cx<T> u[KIND == BK_SUP2 ? 1 : 16];
+  if (KIND != BK_SUP2) {
 #pragma unroll
-      for (int s = 0; s < 16; s++) sm[sw<T>(b | moff[s])] = cmul<T>(sm[sw<T>(b | moff[s])], csm[s]);
-    }
-  } else if (op.kind == KK_UNI2) {
-    cx<T> u[16];
+    for (int i = 0; i < 16; i++) u[i] = c[i];
+  }
+  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+    const uint32_t b = sw<T>(insert_zeros32<4>(g, B.lsorted));
+    cx<T> x[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) u[i] = csm[i];
-    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-      const uint32_t b = insert_zeros32<4>(g, op.lsorted);
-      cx<T> A[16], B[16];
+    for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
+    if (KIND == BK_DIAG2) {
 #pragma unroll
-      for (int s = 0; s < 16; s++) A[s] = sm[sw<T>(b | moff[s])];
+      for (int s = 0; s < 16; s++) sm[b ^ soff[s]] = cmul<T>(x[s], u[s]);
+    } else if (KIND == BK_UNI2) {
 #pragma unroll
-      for (int r = 0; r < 4; r++)
+      for (int cc = 0; cc < 4; cc++) {  // columns: A[:,c] <- U A[:,c]
+        cx<T> t[4];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-          cx<T> acc;
-          acc.x = 0; acc.y = 0;
+        for (int r = 0; r < 4; r++) {
+          t[r].x = 0; t[r].y = 0;
 #pragma unroll
-          for (int m = 0; m < 4; m++) cmac<T>(acc, u[r * 4 + m], A[m | (c << 2)]);
-          B[r | (c << 2)] = acc;
+          for (int m = 0; m < 4; m++) cmac<T>(t[r], u[r * 4 + m], x[m | (cc << 2)]);
         }
 #pragma unroll
-      for (int r = 0; r < 4; r++)
+        for (int r = 0; r < 4; r++) x[r | (cc << 2)] = t[r];
+      }
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-          cx<T> acc;
-          acc.x = 0; acc.y = 0;
+      for (int r = 0; r < 4; r++) {  // rows: A[r,:] <- A[r,:] U^dagger
+        cx<T> t[4];
+#pragma unroll
+        for (int cc = 0; cc < 4; cc++) {
+          t[cc].x = 0; t[cc].y = 0;
 #pragma unroll
           for (int m = 0; m < 4; m++) {
-            cx<T> uc = u[c * 4 + m];
+            cx<T> uc = u[cc * 4 + m];
             uc.y = -uc.y;
-            cmac<T>(acc, uc, B[r | (m << 2)]);
+            cmac<T>(t[cc], uc, x[r | (m << 2)]);
           }
-          sm[sw<T>(b | moff[r | (c << 2)])] = acc;
         }
-    }
-  } else {  // KK_SUP2: coefficients read from shared memory (broadcast), one output row at a time
-    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-      const uint32_t b = insert_zeros32<4>(g, op.lsorted);
-      cx<T> x[16];
 #pragma unroll
-      for (int s = 0; s < 16; s++) x[s] = sm[sw<T>(b | moff[s])];
+        for (int cc = 0; cc < 4; cc++) sm[b ^ soff[r | (cc << 2)]] = t[cc];
+      }
+    } else {
 #pragma unroll 1
       for (int i = 0; i < 16; i++) {
         cx<T> y;
         y.x = 0; y.y = 0;
 #pragma unroll
-        for (int j = 0; j < 16; j++) cmac<T>(y, csm[i * 16 + j], x[j]);
+        for (int j = 0; j < 16; j++) cmac<T>(y, c[i * 16 + j], x[j]);
         uint32_t o = 0;
 #pragma unroll
         for (int j = 0; j < 4; j++)
-          if (i >> j & 1) o |= 1u << op.lbit[j];
-        sm[sw<T>(b | o)] = y;
+          if (i >> j & 1) o |= 1u << B.lbit[j];
+        sm[b ^ sw<T>(o)] = y;
       }
     }
   }
 }
 
-// Run ops [ob, oe) on the tile.  Coefficients are staged in csm (256 entries) per operator.
+// Apply the stage's operators (one block each) to the tile, one sweep per operator.
 template <class T>
-__device__ __forceinline__ void tile_ops(cx<T>* __restrict__ sm, cx<T>* __restrict__ csm, int nbits,
-                                         const TileOp* __restrict__ ops, int ob, int oe,
-                                         const cx<T>* __restrict__ coef) {
-  for (int o = ob; o < oe; o++) {
-    const TileOp op = ops[o];
-    for (int i = threadIdx.x; i < op.ncoef; i += blockDim.x) csm[i] = coef[op.coef + i];
-    __syncthreads();
-    tile_apply<T>(sm, nbits, op, csm);
+__device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm, int nbits,
+                                            const TileBlock* __restrict__ blocks, int bb, int be,
+                                            const BlockOp* __restrict__ sops, int op0) {
+  for (int b = bb; b < be; b++) {
+    const TileBlock B = blocks[b];
+    const BlockOp bo = sops[B.op_begin - op0];
+    const cx<T>* c = csm + bo.coef;
+    switch (bo.kind) {
+      case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c); break;
+      case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c); break;
+      case BK_DIAG2: sweep2<T, BK_DIAG2>(sm, nbits, B, c); break;
+      case BK_UNI2: sweep2<T, BK_UNI2>(sm, nbits, B, c); break;
+      default: sweep2<T, BK_SUP2>(sm, nbits, B, c); break;
+    }
     __syncthreads();
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_stage(cx<T>* __restrict__ st, const StageDesc S,
-                                               const TileOp* __restrict__ ops, const cx<T>* __restrict__ coef) {
+__device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>* __restrict__ coef, int cb, int ce,
+                                            BlockOp* __restrict__ sops, const BlockOp* __restrict__ bops, int ob,
+                                            int oe) {
+  for (int i = threadIdx.x; i < ce - cb; i += blockDim.x) csm[i] = coef[cb + i];
+  for (int i = threadIdx.x; i < oe - ob; i += blockDim.x) sops[i] = bops[ob + i];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __restrict__ st, const StageDesc S,
+                                                                       const TileBlock* __restrict__ blocks,
+                                                                       const BlockOp* __restrict__ bops,
+                                                                       const cx<T>* __restrict__ coef) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
-  cx<T>* csm = sm + (1u << S.nbits);
-  const uint64_t ntiles = 1ull << S.nrest;
+  cx<T>* csm = reinterpret_cast<cx<T>*>(smraw);
+  cx<T>* sm = csm + kCoefCap;
+  __shared__ int s_bits[kMaxTileBits];
+  __shared__ int s_rest[2 * VQD_MAX_QUBITS];
+  if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = S.bits[threadIdx.x];
+  if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
+  const int nbits = S.nbits, nrest = S.nrest, bb = S.block_begin, be = S.block_end;
+  BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << nbits));
+  stage_coefs<T>(csm, coef, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
+  __syncthreads();
+  const uint64_t ntiles = 1ull << nrest;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = deposit(t, S.rest, S.nrest);
-    tile_io<T, true>(st, sm, base, S.bits, S.nbits);
+    const uint64_t base = deposit(t, s_rest, nrest);
+    tile_io<T, true>(st, sm, base, s_bits, nbits);
     __syncthreads();
-    tile_ops<T>(sm, csm, S.nbits, ops, S.op_begin, S.op_end, coef);
-    tile_io<T, false>(st, sm, base, S.bits, S.nbits);
+    tile_blocks<T>(sm, csm, nbits, blocks, bb, be, sops, S.op_begin);
+    tile_io<T, false>(st, sm, base, s_bits, nbits);
     __syncthreads();
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_batch(cx<T>* __restrict__ all, const BatchInst* __restrict__ inst, int ninst,
-                                               const StageDesc* __restrict__ stages, const TileOp* __restrict__ ops,
-                                               const cx<T>* __restrict__ coef, int* __restrict__ counter,
-                                               int max_bits) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch(cx<T>* __restrict__ all, const BatchInst* __restrict__ inst,
+                                                  int ninst, const StageDesc* __restrict__ stages,
+                                                  const TileBlock* __restrict__ blocks,
+                                                  const BlockOp* __restrict__ bops, const cx<T>* __restrict__ coef,
+                                                  int* __restrict__ counter, int max_bits) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
-  cx<T>* csm = sm + (1u << max_bits);
+  cx<T>* csm = reinterpret_cast<cx<T>*>(smraw);
+  cx<T>* sm = csm + kCoefCap;
   __shared__ int item;
   __shared__ int s_bits[kMaxTileBits];
   __shared__ int s_rest[2 * VQD_MAX_QUBITS];
@@ -541,16 +634,18 @@ __global__ void __launch_bounds__(256) k_batch(cx<T>* __restrict__ all, const Ba
     cx<T>* st = all + I.offset_amps;
     for (int s = I.stage_begin; s < I.stage_end; s++) {
       const int nbits = stages[s].nbits, nrest = stages[s].nrest;
-      const int ob = stages[s].op_begin, oe = stages[s].op_end;
       if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = stages[s].bits[threadIdx.x];
       if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = stages[s].rest[threadIdx.x];
+      BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << max_bits));
+      const int op0 = stages[s].op_begin;
+      stage_coefs<T>(csm, coef, stages[s].coef_begin, stages[s].coef_end, sops, bops, op0, stages[s].op_end);
       __syncthreads();
       const uint64_t ntiles = 1ull << nrest;
       for (uint64_t t = 0; t < ntiles; t++) {
         const uint64_t base = deposit(t, s_rest, nrest);
         tile_io<T, true>(st, sm, base, s_bits, nbits);
         __syncthreads();
-        tile_ops<T>(sm, csm, nbits, ops, ob, oe, coef);
+        tile_blocks<T>(sm, csm, nbits, blocks, stages[s].block_begin, stages[s].block_end, sops, op0);
         tile_io<T, false>(st, sm, base, s_bits, nbits);
         __syncthreads();
       }
@@ -584,11 +679,8 @@ static void check(cudaError_t e, const char* what) {
 }
 
 void fused_cache_free(FusedCache& c) {
-  if (c.d_ops) cudaFree(c.d_ops);
-  if (c.d_coef) cudaFree(c.d_coef);
-  if (c.d_stages) cudaFree(c.d_stages);
-  if (c.d_inst) cudaFree(c.d_inst);
-  if (c.d_counter) cudaFree(c.d_counter);
+  for (void* p : {c.d_blocks, c.d_ops, c.d_coef, c.d_stages, c.d_inst, (void*)c.d_counter})
+    if (p) cudaFree(p);
   c = FusedCache();
 }
 
@@ -601,11 +693,15 @@ static void upload_common(FusedCache& c, const FusedPlan& p, cudaStream_t s) {
     cf[i].x = (T)p.coef[i].real();
     cf[i].y = (T)p.coef[i].imag();
   }
-  grow(&c.d_ops, &c.ops_cap, std::max<size_t>(1, p.ops.size()) * sizeof(TileOp));
+  grow(&c.d_blocks, &c.blocks_cap, std::max<size_t>(1, p.blocks.size()) * sizeof(TileBlock));
+  grow(&c.d_ops, &c.ops_cap, std::max<size_t>(1, p.ops.size()) * sizeof(BlockOp));
   grow(&c.d_coef, &c.coef_cap, std::max<size_t>(1, cf.size()) * sizeof(cx<T>));
   grow(&c.d_stages, &c.stages_cap, std::max<size_t>(1, p.stages.size()) * sizeof(StageDesc));
+  if (!p.blocks.empty())
+    check(cudaMemcpyAsync(c.d_blocks, p.blocks.data(), p.blocks.size() * sizeof(TileBlock), cudaMemcpyHostToDevice, s),
+          "upload blocks");
   if (!p.ops.empty())
-    check(cudaMemcpyAsync(c.d_ops, p.ops.data(), p.ops.size() * sizeof(TileOp), cudaMemcpyHostToDevice, s), "upload ops");
+    check(cudaMemcpyAsync(c.d_ops, p.ops.data(), p.ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice, s), "upload ops");
   if (!cf.empty())
     check(cudaMemcpyAsync(c.d_coef, cf.data(), cf.size() * sizeof(cx<T>), cudaMemcpyHostToDevice, s), "upload coefficients");
   if (!p.stages.empty())
@@ -628,13 +724,19 @@ static unsigned persistent_grid(K kernel, size_t smem, uint64_t work) {
 }
 
 template <class T>
+static size_t stage_smem(int nbits) {
+  return ((size_t)kCoefCap + ((size_t)1 << nbits)) * sizeof(cx<T>) + (size_t)kOpCap * sizeof(BlockOp);
+}
+
+template <class T>
 static cudaError_t stage_t(FusedCache& c, const FusedPlan& p, int stage, void* state, cudaStream_t s) {
   const StageDesc& S = p.stages[stage];
-  const size_t smem = ((size_t)1 << S.nbits) * sizeof(cx<T>) + 256 * sizeof(cx<T>);
+  const size_t smem = stage_smem<T>(S.nbits);
   cudaError_t e = cudaFuncSetAttribute(k_stage<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   unsigned grid = persistent_grid(k_stage<T>, smem, 1ull << S.nrest);
-  k_stage<T><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileOp*)c.d_ops, (const cx<T>*)c.d_coef);
+  k_stage<T><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops,
+                                     (const cx<T>*)c.d_coef);
   return cudaGetLastError();
 }
 
@@ -651,34 +753,26 @@ void upload_batch(FusedCache& c, const BatchPlan& p, int prec, cudaStream_t s) {
         "upload instances");
   if (!c.d_counter) check(cudaMalloc(&c.d_counter, sizeof(int)), "queue counter");
   check(cudaStreamSynchronize(s), "upload batch");
-  c.n_inst = (int)p.inst.size();
-  c.max_bits = p.all.max_bits;
 }
 
 template <class T>
 static cudaError_t batch_t(FusedCache& c, const BatchPlan& p, void* base, cudaStream_t s) {
   const int mb = std::max(1, p.all.max_bits);
-  const size_t smem = ((size_t)1 << mb) * sizeof(cx<T>) + 256 * sizeof(cx<T>);
+  const size_t smem = stage_smem<T>(mb);
   cudaError_t e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c.d_counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   unsigned grid = persistent_grid(k_batch<T>, smem, p.inst.size());
   k_batch<T><<<grid, 256, smem, s>>>((cx<T>*)base, (const BatchInst*)c.d_inst, (int)p.inst.size(),
-                                     (const StageDesc*)c.d_stages, (const TileOp*)c.d_ops, (const cx<T>*)c.d_coef,
-                                     c.d_counter, mb);
+                                     (const StageDesc*)c.d_stages, (const TileBlock*)c.d_blocks,
+                                     (const BlockOp*)c.d_ops, (const cx<T>*)c.d_coef, c.d_counter, mb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base, cudaStream_t s) {
   if (prec == VQD_F32) return batch_t<float>(c, p, base, s);
   return batch_t<double>(c, p, base, s);
-}
-
-cudaError_t batch_status(FusedCache& c, cudaStream_t s) {
-  (void)c;
-  (void)s;
-  return cudaGetLastError();
 }
 
 }  // namespace vqd

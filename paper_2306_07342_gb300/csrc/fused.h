@@ -10,32 +10,42 @@
 namespace vqd {
 
 constexpr int kMaxTileBits = 16;
+constexpr int kCoefCap = 2048;  // complex coefficients of one stage, staged in shared memory
+constexpr int kOpCap = 512;     // operator descriptors of one stage, staged in shared memory
 
-// One operator inside a stage, addressed by tile-local bit positions (device record).
-struct TileOp {
-  int kind;        // KK_ELEM / KK_SUP1 / KK_UNI2 / KK_SUP2
-  int nb;          // 2k member bits
-  int lbit[4];     // tile-local bit of member bit j (row bits of q0, q1, then column bits)
-  int lsorted[4];  // the same bits ascending (zero insertion)
-  int coef;        // offset of the coefficients in the plan's coefficient array
-  int ncoef;
-  int real;        // ELEM: every factor real
-  int pad;
+// Operator kinds inside a block on qubits (a, b); member index s = ra | rb << 1 | ca << 2 | cb << 3.
+enum BlockOpKind { BK_DIAG_A = 0, BK_SUP1_A, BK_DIAG_B, BK_SUP1_B, BK_DIAG2, BK_UNI2, BK_SUP2 };
+
+struct BlockOp {
+  int kind;
+  int coef;  // offset within the stage's coefficients
 };
 
-// One stage: a set of index bits held in a shared-memory tile and the operators applied to it.
+// A block: operators acting within one qubit (nq = 1) or one pair (nq = 2), applied back to back
+// to amplitudes held in registers (one shared-memory sweep per block).
+struct TileBlock {
+  int nq;
+  int lbit[4];     // tile-local bits: a_row, b_row, a_col, b_col (nq = 2) or a_row, a_col (nq = 1)
+  int lsorted[4];  // the same bits ascending (zero insertion)
+  int op_begin, op_end;
+};
+
+// One stage: a set of index bits held in a shared-memory tile and the blocks applied to it.
 struct StageDesc {
   int nbits;                 // tile-local bits (ascending global positions in bits[])
   int bits[kMaxTileBits];
   int nrest;                 // remaining global bit positions (ascending), deposited from the tile index
   int rest[2 * VQD_MAX_QUBITS];
-  int op_begin, op_end;      // range in the plan's TileOp array
+  int block_begin, block_end;
+  int coef_begin, coef_end;  // this stage's coefficients in the plan's array (<= kCoefCap of them)
+  int op_begin, op_end;      // this stage's operator descriptors (<= kOpCap of them)
   double weight;             // original operations applied by this stage
 };
 
 struct FusedPlan {
   std::vector<StageDesc> stages;
-  std::vector<TileOp> ops;
+  std::vector<TileBlock> blocks;
+  std::vector<BlockOp> ops;
   std::vector<cd> coef;
   int max_bits = 0;
 };
@@ -52,7 +62,7 @@ struct BatchInst {
   double cost;           // 4^n x stages, for largest-first ordering
 };
 struct BatchPlan {
-  FusedPlan all;                 // stages of every instance, concatenated (op/coef offsets global)
+  FusedPlan all;                 // stages of every instance, concatenated (offsets global)
   std::vector<BatchInst> inst;   // in queue order (largest first)
   std::vector<int> passes;       // passes over the state per instance (indexed by instance id)
 };
@@ -61,6 +71,8 @@ BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vecto
 
 // Device buffers reused across calls (grown on demand; freed with the context).
 struct FusedCache {
+  void* d_blocks = nullptr;
+  size_t blocks_cap = 0;
   void* d_ops = nullptr;
   size_t ops_cap = 0;
   void* d_coef = nullptr;
@@ -70,15 +82,12 @@ struct FusedCache {
   void* d_inst = nullptr;
   size_t inst_cap = 0;
   int* d_counter = nullptr;
-  int n_inst = 0;
-  int max_bits = 0;
 };
 void fused_cache_free(FusedCache& c);
 void upload_plan(FusedCache& c, const FusedPlan& p, int prec, cudaStream_t s);
 cudaError_t launch_stage(FusedCache& c, const FusedPlan& p, int stage, int prec, void* state, int n, cudaStream_t s);
 void upload_batch(FusedCache& c, const BatchPlan& p, int prec, cudaStream_t s);
 cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base, cudaStream_t s);
-cudaError_t batch_status(FusedCache& c, cudaStream_t s);
 
 // Shared-memory tile budget (index bits) for a precision.
 int tile_bits_budget(int prec);

@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "vqd_profile_reset": (I, [P]),
             "vqd_profile_read": (I, [P, I, P, P]),
             "vqd_prob_static": (I, [P, I, I, I, P, P, P]),
+            "vqd_plan_info": (I, [I, I, I, P, I, U, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +231,15 @@ def vqd_compile_op(op, flags: int = 0):
     if isu.value:
         return "U", tuple(t[:kk]), m[: 4 ** kk].reshape(2 ** kk, 2 ** kk)
     return "S", tuple(t[:kk]), m[: 16 ** kk].reshape(4 ** kk, 4 ** kk)
+
+
+def vqd_plan_info(n: int, prec: int, ops, fuse_qubits: int = 0, flags: int = 0) -> dict:
+    """Fused-path plan statistics for a program (host only, no GPU needed)."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib().vqd_plan_info(n, prec, len(a), _ptr(a), fuse_qubits, flags, _ptr(info)))
+    keys = ["stages", "blocks", "diag", "sup1", "uni2", "sup2", "max_tile_bits", "native_ops"]
+    return dict(zip(keys, (int(x) for x in info)))
 
 
 def vqd_stderr_params(nq: int, fbar: float, x: float):
