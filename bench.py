@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--rows", type=int, default=2, help="grid rows (profiling cases only; the benchmark is 2x7)")
     ap.add_argument("--cols", type=int, default=7)
     ap.add_argument("--depth", type=int, default=60)
+    ap.add_argument("--batch-count", type=int, default=1024, help="instances of the batched neutral-atom workload")
     ap.add_argument("--path", default="plain", choices=["plain", "fused"],
                     help="path of the headline measurement (profiling cases; the benchmark is plain)")
     return ap.parse_args()
@@ -160,6 +161,62 @@ def load_traffic(kernel_class: str):
     src = os.path.join(ROOT, "paper_2306_07342_gb300", "csrc", rec["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return rec["bytes_per_launch"] if h == rec["source_sha256_16"] else None
+
+
+def measure_batch(vqd, torch, stream_handle, count):
+    """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of
+    persistent kernels), against one launch sequence per instance (fused and plain) on a sample."""
+    import numpy as np
+    from workloads import config4_neutral_batch
+    progs = config4_neutral_batch(count=count)
+    arrays = [vqd.native_ops(p.ops) for p in progs]
+    ns = [p.n for p in progs]
+    units = sum(len(p.ops) * 4.0 ** p.n for p in progs)
+    ctx = vqd.vqd_create_batch(ns, vqd.VQD_F32, stream_handle)
+    try:
+        vqd.vqd_run_batch(ctx, arrays)                       # warm-up (also compiles and plans)
+        torch.cuda.synchronize()
+        vqd.vqd_profile(ctx, 2)
+        vqd.vqd_profile_reset(ctx)
+        t0 = time.perf_counter()
+        vqd.vqd_run_batch(ctx, arrays)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = vqd.vqd_profile_read(ctx)["batch"]
+        vqd.vqd_profile(ctx, 0)
+        kern_s = st["total_ms"] * 1e-3
+        # one launch sequence per instance, on every 16th instance (all sizes represented)
+        sample = list(range(0, count, 16))
+        sunits = sum(len(progs[i].ops) * 4.0 ** progs[i].n for i in sample)
+        res = {}
+        for path in ("fused", "plain"):
+            for i in sample[:2]:
+                (vqd.vqd_run_program if path == "fused" else vqd.vqd_apply_native)(ctx, i, arrays[i])
+            torch.cuda.synchronize()
+            vqd.vqd_profile(ctx, 2)
+            vqd.vqd_profile_reset(ctx)
+            t0 = time.perf_counter()
+            for i in sample:
+                if path == "fused":
+                    vqd.vqd_run_program(ctx, i, arrays[i])
+                else:
+                    vqd.vqd_apply_native(ctx, i, arrays[i])
+            torch.cuda.synchronize()
+            w = time.perf_counter() - t0
+            ps = vqd.vqd_profile_read(ctx)
+            vqd.vqd_profile(ctx, 0)
+            kms = sum(v["total_ms"] for k, v in ps.items() if k not in ("reduce", "init"))
+            res[path] = {"value": sunits / w, "kernel_value": sunits / (kms * 1e-3),
+                         "launches": int(sum(v["launches"] for v in ps.values()))}
+        return {"value": units / wall, "unit": "amp-updates/s", "kernel_value": units / kern_s,
+                "instances": count, "native_ops": int(sum(len(a) for a in arrays)), "amp_updates": units,
+                "kernel_s": kern_s, "wall_s": wall, "host_compile_plan_s": wall - kern_s,
+                "state_bytes": int(sum(vqd.vqd_state_bytes(n, vqd.VQD_F32) for n in ns)),
+                "per_instance_sample": {"instances": len(sample), **res},
+                "note": "value = wall clock of one vqd_run_batch (host compile + fusion planning + all stage "
+                        "waves); kernel_value = CUDA-event time of the waves only"}
+    finally:
+        vqd.vqd_destroy(ctx)
 
 
 def main():
@@ -302,6 +359,9 @@ def main():
                                      "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
                                                    for k, v in dstats.items()}}
         vqd.vqd_destroy(ctx64)
+
+    if not args.no_extra and args.batch_count > 0:
+        extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)
 
     cpu = None
     if rank == 0 and not args.no_extra:

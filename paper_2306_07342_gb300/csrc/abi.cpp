@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <memory>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -386,21 +388,47 @@ int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int f
 int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags) {
   API_BEGIN
   need_ctx(c);
-  if (!offsets) throw Error(VQD_EINVAL, "NULL offsets");
+  if (!offsets || (offsets[c->n.size()] > 0 && !ops)) throw Error(VQD_EINVAL, "NULL offsets or ops");
   const int count = (int)c->n.size();
-  std::vector<std::vector<Op>> lists(count);
-  for (int i = 0; i < count; i++) {
-    if (offsets[i + 1] < offsets[i]) throw Error(VQD_EINVAL, "offsets must be non-decreasing");
-    lists[i] = compile_list(c, i, (int)(offsets[i + 1] - offsets[i]), ops + offsets[i], flags);
-  }
-  BatchPlan plan = plan_batch(lists, c->n, c->off, c->prec, fuse_qubits);
+  for (int i = 0; i < count; i++)
+    if (offsets[i] < 0 || offsets[i + 1] < offsets[i]) throw Error(VQD_EINVAL, "offsets must be non-decreasing");
+  // Instances are compiled and planned independently, on several host threads.
+  std::vector<FusedPlan> plans(count);
+  std::vector<size_t> nops(count);
+  std::vector<std::string> errs(count);
+  std::vector<int> codes(count, VQD_OK);
+  const int nt = std::max(1, std::min<int>(count, (int)std::thread::hardware_concurrency()));
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (int i = next++; i < count; i = next++) {
+      try {
+        std::vector<Op> list = compile_list(c, i, (int)(offsets[i + 1] - offsets[i]), ops + offsets[i], flags);
+        nops[i] = list.size();
+        plans[i] = plan_fused(list, c->n[i], c->prec, fuse_qubits);
+      } catch (const Error& e) {
+        codes[i] = e.code;
+        errs[i] = e.what();
+      } catch (const std::exception& e) {
+        codes[i] = VQD_EINVAL;
+        errs[i] = e.what();
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; t++) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < count; i++)
+    if (codes[i] != VQD_OK) throw Error(codes[i], "instance " + std::to_string(i) + ": " + errs[i]);
+  BatchPlan plan = merge_batch(plans, c->n, c->off, c->prec);
   upload_batch(c->fused, plan, c->prec, c->stream);
   double bytes = 0, upd = 0;
   for (int i = 0; i < count; i++) {
     bytes += 2.0 * c->bytes(i) * plan.passes[i];
-    upd += (double)lists[i].size() * std::ldexp(1.0, 2 * c->n[i]);
+    upd += (double)nops[i] * std::ldexp(1.0, 2 * c->n[i]);
   }
-  timed(c, SC_BATCH, bytes, upd, 1, [&] { return launch_batch(c->fused, plan, c->prec, c->base, c->stream); });
+  timed(c, SC_BATCH, bytes, upd, (int64_t)plan.wave_begin.size() - 1,
+        [&] { return launch_batch(c->fused, plan, c->prec, c->base, c->stream); });
   API_END(c)
 }
 

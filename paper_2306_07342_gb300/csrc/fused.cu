@@ -323,11 +323,19 @@ FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubit
 
 BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vector<int>& n,
                      const std::vector<size_t>& byte_offsets, int prec, int fuse_qubits) {
+  std::vector<FusedPlan> plans;
+  for (size_t i = 0; i < lists.size(); i++) plans.push_back(plan_fused(lists[i], n[i], prec, fuse_qubits));
+  return merge_batch(plans, n, byte_offsets, prec);
+}
+
+BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int>& n,
+                      const std::vector<size_t>& byte_offsets, int prec) {
   BatchPlan bp;
   const size_t esz = prec == VQD_F32 ? 8 : 16;
-  bp.passes.assign(lists.size(), 0);
-  for (size_t i = 0; i < lists.size(); i++) {
-    FusedPlan p = plan_fused(lists[i], n[i], prec, fuse_qubits);
+  bp.passes.assign(plans.size(), 0);
+  size_t max_stages = 0;
+  for (size_t i = 0; i < plans.size(); i++) {
+    const FusedPlan& p = plans[i];
     BatchInst bi;
     bi.offset_amps = byte_offsets[i] / esz;
     bi.n = n[i];
@@ -353,9 +361,26 @@ BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vecto
     bi.stage_end = (int)bp.all.stages.size();
     bi.cost = std::ldexp(1.0, 2 * n[i]) * std::max<size_t>(1, p.stages.size());
     bp.passes[i] = (int)p.stages.size();
+    max_stages = std::max(max_stages, p.stages.size());
     bp.inst.push_back(bi);
   }
-  std::stable_sort(bp.inst.begin(), bp.inst.end(), [](const BatchInst& a, const BatchInst& b) { return a.cost > b.cost; });
+  // Wave w: stage w of every instance that has one, split into chunks of at most kChunk tiles,
+  // largest states first so that the long items start early.
+  const uint32_t kChunk = 16;
+  std::vector<int> order(plans.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  for (size_t w = 0; w < max_stages; w++) {
+    bp.wave_begin.push_back((int)bp.items.size());
+    for (int i : order) {
+      const BatchInst& bi = bp.inst[i];
+      if ((int)w >= bi.stage_end - bi.stage_begin) continue;
+      const int s = bi.stage_begin + (int)w;
+      const uint32_t ntiles = 1u << bp.all.stages[s].nrest;
+      for (uint32_t t = 0; t < ntiles; t += kChunk) bp.items.push_back({i, s, t, std::min(kChunk, ntiles - t)});
+    }
+  }
+  bp.wave_begin.push_back((int)bp.items.size());
   return bp;
 }
 
@@ -382,15 +407,22 @@ __device__ __forceinline__ cx<T> cmul(const cx<T>& a, const cx<T>& b) {
   return r;
 }
 
+// Zero-bit insertion with precomputed masks: inserting a zero at bit p maps g to
+// (g & low) | ((g & ~low) << 1) = g + (g & ~low), low = 2^p - 1.  hi[i] = ~(2^pos[i] - 1) for
+// ascending positions, applied lowest first.
 template <int NB>
-__device__ __forceinline__ uint32_t insert_zeros32(uint32_t g, const int* pos) {
+struct Inserter {
+  uint32_t hi[NB];
+  __device__ __forceinline__ explicit Inserter(const int* pos) {
 #pragma unroll
-  for (int i = 0; i < NB; i++) {
-    const uint32_t lo = g & ((1u << pos[i]) - 1u);
-    g = ((g >> pos[i]) << (pos[i] + 1)) | lo;
+    for (int i = 0; i < NB; i++) hi[i] = ~((1u << pos[i]) - 1u);
   }
-  return g;
-}
+  __device__ __forceinline__ uint32_t operator()(uint32_t g) const {
+#pragma unroll
+    for (int i = 0; i < NB; i++) g += g & hi[i];
+    return g;
+  }
+};
 
 // Shared-memory position of tile element l: the low bits (one 128-byte row) are XORed with the
 // row number, so that the strided member accesses of a block on a low tile bit spread over all
@@ -462,8 +494,9 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
   cx<T> S[DIAG ? 4 : 16];
 #pragma unroll
   for (int i = 0; i < (DIAG ? 4 : 16); i++) S[i] = c[i];
+  const Inserter<2> ins(B.lsorted);
   for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-    const uint32_t b = sw<T>(insert_zeros32<2>(g, B.lsorted));
+    const uint32_t b = sw<T>(ins(g));
     const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
     cx<T> x[4];
 #pragma unroll
@@ -503,8 +536,9 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
 #pragma unroll
     for (int i = 0; i < 16; i++) u[i] = c[i];
   }
+  const Inserter<4> ins(B.lsorted);
   for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
-    const uint32_t b = sw<T>(insert_zeros32<4>(g, B.lsorted));
+    const uint32_t b = sw<T>(ins(g));
     cx<T> x[16];
 #pragma unroll
     for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
@@ -612,43 +646,50 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __
   }
 }
 
+// One wave of the batched path: CTAs take (instance, stage, tile chunk) items from an atomic
+// queue; a CTA restages coefficients and operator descriptors only when its next item belongs to
+// another stage.  Items of one wave never depend on each other, so no CTA waits for another.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch(cx<T>* __restrict__ all, const BatchInst* __restrict__ inst,
-                                                  int ninst, const StageDesc* __restrict__ stages,
-                                                  const TileBlock* __restrict__ blocks,
-                                                  const BlockOp* __restrict__ bops, const cx<T>* __restrict__ coef,
-                                                  int* __restrict__ counter, int max_bits) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __restrict__ all,
+                                                                      const BatchInst* __restrict__ inst,
+                                                                      const StageDesc* __restrict__ stages,
+                                                                      const TileBlock* __restrict__ blocks,
+                                                                      const BlockOp* __restrict__ bops,
+                                                                      const cx<T>* __restrict__ coef,
+                                                                      const WaveItem* __restrict__ items, int nitems,
+                                                                      int* __restrict__ counter, int max_bits) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* csm = reinterpret_cast<cx<T>*>(smraw);
   cx<T>* sm = csm + kCoefCap;
+  BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << max_bits));
   __shared__ int item;
   __shared__ int s_bits[kMaxTileBits];
   __shared__ int s_rest[2 * VQD_MAX_QUBITS];
+  int cur = -1;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1);
     __syncthreads();
     const int i = item;
     __syncthreads();  // every thread has read `item` before thread 0 may overwrite it
-    if (i >= ninst) break;
-    const BatchInst I = inst[i];
-    cx<T>* st = all + I.offset_amps;
-    for (int s = I.stage_begin; s < I.stage_end; s++) {
-      const int nbits = stages[s].nbits, nrest = stages[s].nrest;
-      if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = stages[s].bits[threadIdx.x];
-      if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = stages[s].rest[threadIdx.x];
-      BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << max_bits));
-      const int op0 = stages[s].op_begin;
-      stage_coefs<T>(csm, coef, stages[s].coef_begin, stages[s].coef_end, sops, bops, op0, stages[s].op_end);
+    if (i >= nitems) break;
+    const WaveItem W = items[i];
+    const StageDesc& S = stages[W.stage];
+    if (W.stage != cur) {
+      if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = S.bits[threadIdx.x];
+      if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
+      stage_coefs<T>(csm, coef, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
       __syncthreads();
-      const uint64_t ntiles = 1ull << nrest;
-      for (uint64_t t = 0; t < ntiles; t++) {
-        const uint64_t base = deposit(t, s_rest, nrest);
-        tile_io<T, true>(st, sm, base, s_bits, nbits);
-        __syncthreads();
-        tile_blocks<T>(sm, csm, nbits, blocks, stages[s].block_begin, stages[s].block_end, sops, op0);
-        tile_io<T, false>(st, sm, base, s_bits, nbits);
-        __syncthreads();
-      }
+      cur = W.stage;
+    }
+    cx<T>* st = all + inst[W.inst].offset_amps;
+    const int nbits = S.nbits, nrest = S.nrest, op0 = S.op_begin;
+    for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++) {
+      const uint64_t base = deposit(t, s_rest, nrest);
+      tile_io<T, true>(st, sm, base, s_bits, nbits);
+      __syncthreads();
+      tile_blocks<T>(sm, csm, nbits, blocks, S.block_begin, S.block_end, sops, op0);
+      tile_io<T, false>(st, sm, base, s_bits, nbits);
+      __syncthreads();
     }
   }
 }
@@ -679,7 +720,7 @@ static void check(cudaError_t e, const char* what) {
 }
 
 void fused_cache_free(FusedCache& c) {
-  for (void* p : {c.d_blocks, c.d_ops, c.d_coef, c.d_stages, c.d_inst, (void*)c.d_counter})
+  for (void* p : {c.d_blocks, c.d_ops, c.d_coef, c.d_stages, c.d_inst, c.d_items, (void*)c.d_counter})
     if (p) cudaFree(p);
   c = FusedCache();
 }
@@ -749,9 +790,13 @@ cudaError_t launch_stage(FusedCache& c, const FusedPlan& p, int stage, int prec,
 void upload_batch(FusedCache& c, const BatchPlan& p, int prec, cudaStream_t s) {
   upload_plan(c, p.all, prec, s);
   grow(&c.d_inst, &c.inst_cap, std::max<size_t>(1, p.inst.size()) * sizeof(BatchInst));
+  grow(&c.d_items, &c.items_cap, std::max<size_t>(1, p.items.size()) * sizeof(WaveItem));
+  grow((void**)&c.d_counter, &c.counter_cap, std::max<size_t>(1, p.wave_begin.size()) * sizeof(int));
   check(cudaMemcpyAsync(c.d_inst, p.inst.data(), p.inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s),
         "upload instances");
-  if (!c.d_counter) check(cudaMalloc(&c.d_counter, sizeof(int)), "queue counter");
+  if (!p.items.empty())
+    check(cudaMemcpyAsync(c.d_items, p.items.data(), p.items.size() * sizeof(WaveItem), cudaMemcpyHostToDevice, s),
+          "upload wave items");
   check(cudaStreamSynchronize(s), "upload batch");
 }
 
@@ -759,15 +804,22 @@ template <class T>
 static cudaError_t batch_t(FusedCache& c, const BatchPlan& p, void* base, cudaStream_t s) {
   const int mb = std::max(1, p.all.max_bits);
   const size_t smem = stage_smem<T>(mb);
-  cudaError_t e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_wave<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(c.d_counter, 0, sizeof(int), s);
+  const int nw = (int)p.wave_begin.size() - 1;
+  if (nw <= 0) return cudaSuccess;
+  e = cudaMemsetAsync(c.d_counter, 0, sizeof(int) * nw, s);
   if (e != cudaSuccess) return e;
-  unsigned grid = persistent_grid(k_batch<T>, smem, p.inst.size());
-  k_batch<T><<<grid, 256, smem, s>>>((cx<T>*)base, (const BatchInst*)c.d_inst, (int)p.inst.size(),
-                                     (const StageDesc*)c.d_stages, (const TileBlock*)c.d_blocks,
-                                     (const BlockOp*)c.d_ops, (const cx<T>*)c.d_coef, c.d_counter, mb);
-  return cudaGetLastError();
+  for (int w = 0; w < nw; w++) {
+    const int b = p.wave_begin[w], cnt = p.wave_begin[w + 1] - b;
+    unsigned grid = persistent_grid(k_wave<T>, smem, (uint64_t)cnt);
+    k_wave<T><<<grid, 256, smem, s>>>((cx<T>*)base, (const BatchInst*)c.d_inst, (const StageDesc*)c.d_stages,
+                                      (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops, (const cx<T>*)c.d_coef,
+                                      (const WaveItem*)c.d_items + b, cnt, c.d_counter + w, mb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base, cudaStream_t s) {

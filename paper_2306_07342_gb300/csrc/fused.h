@@ -59,16 +59,26 @@ struct BatchInst {
   uint64_t offset_amps;  // first amplitude of the instance in the batch allocation
   int n;
   int stage_begin, stage_end;
-  double cost;           // 4^n x stages, for largest-first ordering
+  double cost;
+};
+// One work item of a wave: a chunk of tiles of one stage of one instance.
+struct WaveItem {
+  int inst;
+  int stage;
+  uint32_t tile_begin, tile_count;
 };
 struct BatchPlan {
   FusedPlan all;                 // stages of every instance, concatenated (offsets global)
-  std::vector<BatchInst> inst;   // in queue order (largest first)
-  std::vector<int> passes;       // passes over the state per instance (indexed by instance id)
+  std::vector<BatchInst> inst;   // indexed by instance id
+  std::vector<int> passes;       // passes over the state per instance
+  std::vector<WaveItem> items;   // wave w holds items [wave_begin[w], wave_begin[w+1]), largest first
+  std::vector<int> wave_begin;
 };
 BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vector<int>& n,
                      const std::vector<size_t>& byte_offsets, int prec, int fuse_qubits);
-
+// Concatenate per-instance plans (planned independently, e.g. on several host threads).
+BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int>& n,
+                      const std::vector<size_t>& byte_offsets, int prec);
 // Device buffers reused across calls (grown on demand; freed with the context).
 struct FusedCache {
   void* d_blocks = nullptr;
@@ -81,7 +91,10 @@ struct FusedCache {
   size_t stages_cap = 0;
   void* d_inst = nullptr;
   size_t inst_cap = 0;
-  int* d_counter = nullptr;
+  void* d_items = nullptr;
+  size_t items_cap = 0;
+  int* d_counter = nullptr;  // one work counter per wave
+  size_t counter_cap = 0;
 };
 void fused_cache_free(FusedCache& c);
 void upload_plan(FusedCache& c, const FusedPlan& p, int prec, cudaStream_t s);

@@ -120,11 +120,12 @@ def native_ops(ops: Iterable) -> np.ndarray:
     """Marshal NativeOp(name, qubits, params) records into the C struct array."""
     ops = list(ops)
     arr = np.zeros(len(ops), dtype=NATIVE_OP_DTYPE)
-    for i, o in enumerate(ops):
-        arr[i]["code"] = OP_CODE[o.name]
-        arr[i]["nq"] = len(o.qubits)
-        arr[i]["q"][: len(o.qubits)] = o.qubits
-        arr[i]["par"][: len(o.params)] = o.params
+    if not ops:
+        return arr
+    arr["code"] = [OP_CODE[o.name] for o in ops]
+    arr["nq"] = [len(o.qubits) for o in ops]
+    arr["q"] = [(o.qubits + (0,))[:2] if len(o.qubits) == 1 else o.qubits for o in ops]
+    arr["par"] = [tuple(o.params) + (0.0,) * (4 - len(o.params)) for o in ops]
     return arr
 
 

@@ -205,13 +205,16 @@ def test_reductions(vqd, p):
 
 
 # ---------------------------------------------------------------- batched persistent path
-@pytest.mark.parametrize("p", PRECS)
-def test_batch_matches_per_instance_oracle(vqd, p):
+@pytest.mark.parametrize("p,fuse", [("f64", 0), ("f32", 0), ("f32", 3)])
+def test_batch_matches_per_instance_oracle(vqd, p, fuse):
+    """Uneven instances in one batched run: single-tile instances, and (n = 9, 10) multi-stage ones
+    whose stages span several waves and tile chunks."""
     from workloads import config4_neutral_batch
     progs = config4_neutral_batch(seed=8, count=10, n_lo=3, n_hi=8, depth=3)
+    progs += config4_neutral_batch(seed=9, count=2, n_lo=9, n_hi=10, depth=2)
     ctx = vqd.vqd_create_batch([q.n for q in progs], prec_code(vqd, p))
     try:
-        vqd.vqd_run_batch(ctx, [q.ops for q in progs])
+        vqd.vqd_run_batch(ctx, [q.ops for q in progs], fuse)
         for i, prog in enumerate(progs):
             want = evolve.run_program(prog)
             got = gpu_state(vqd, ctx, i)
