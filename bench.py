@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--cols", type=int, default=7)
     ap.add_argument("--depth", type=int, default=60)
     ap.add_argument("--batch-count", type=int, default=1024, help="instances of the batched neutral-atom workload")
+    ap.add_argument("--precision", default=None, choices=["sc_grid14", "ion15", "spin16"],
+                    help="instead of timing: error of the complex64 paths against the FP64 path on one workload")
+    ap.add_argument("--prefix", type=int, default=0, help="--precision: only the first N native ops (0 = all)")
     ap.add_argument("--path", default="plain", choices=["plain", "fused"],
                     help="path of the headline measurement (profiling cases; the benchmark is plain)")
     return ap.parse_args()
@@ -219,8 +222,83 @@ def measure_batch(vqd, torch, stream_handle, count):
         vqd.vqd_destroy(ctx)
 
 
+def device_view(torch, ptr: int, count: int, prec_f32: bool):
+    """Zero-copy complex torch view of `count` amplitudes at a library device address (measurement only)."""
+    class _A:
+        pass
+    a = _A()
+    a.__cuda_array_interface__ = {"shape": (2 * count,), "typestr": "<f4" if prec_f32 else "<f8",
+                                  "data": (ptr, False), "version": 3}
+    t = torch.as_tensor(a, device="cuda")
+    return torch.view_as_complex(t.view(-1, 2))
+
+
+def run_precision(args):
+    """Error of the complex64 plain and fused paths against the FP64 plain path on one workload."""
+    import numpy as np
+    import torch
+    from paper_2306_07342_gb300 import build as _b
+    _b.build()
+    from paper_2306_07342_gb300 import vqd
+    from workloads import config2_sc_grid, config3_ion_alltoall, config5_spin_chain
+    prog = {"sc_grid14": config2_sc_grid, "ion15": config3_ion_alltoall, "spin16": config5_spin_chain}[args.precision]()
+    ops = prog.ops[: args.prefix] if args.prefix else prog.ops
+    native = vqd.native_ops(ops)
+    n = prog.n
+    N = 4 ** n
+    sh = torch.cuda.current_stream().cuda_stream
+    out = {"workload": args.precision, "n": n, "native_ops": len(ops)}
+
+    def run(prec, path, fuse=0):
+        ctx = vqd.vqd_create(n, prec, sh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if path == "plain":
+            vqd.vqd_apply_native(ctx, 0, native)
+        else:
+            vqd.vqd_run_program(ctx, 0, native, fuse)
+        torch.cuda.synchronize()
+        return ctx, time.perf_counter() - t0
+
+    ref, t64 = run(vqd.VQD_F64, "plain")
+    r = device_view(torch, vqd.vqd_state_ptr(ref, 0), N, False)
+    p_ref = vqd.vqd_prob(ref, 0, list(range(n)))
+    pur_ref = vqd.vqd_purity(ref, 0)
+    out["f64_plain_s"] = t64
+    out["f64_trace"] = vqd.vqd_trace(ref, 0).real
+    out["f64_purity"] = pur_ref
+    for path, fuse in [("plain", 0), ("fused", 4), ("fused", 5), ("fused", 6)]:
+        ctx, t = run(vqd.VQD_F32, path, fuse)
+        x = device_view(torch, vqd.vqd_state_ptr(ctx, 0), N, True)
+        maxabs, fro2, tr_rs = 0.0, 0.0, 0.0
+        chunk = 1 << 26
+        for i in range(0, N, chunk):
+            a = r[i:i + chunk]
+            b = x[i:i + chunk].to(torch.complex128)
+            d = b - a
+            maxabs = max(maxabs, float(d.abs().max()))
+            fro2 += float((d.real ** 2 + d.imag ** 2).sum())
+            tr_rs += float((a.conj() * b).real.sum())      # tr(rho sigma) for Hermitian rho, sigma
+        p = vqd.vqd_prob(ctx, 0, list(range(n)))
+        pur = vqd.vqd_purity(ctx, 0)
+        sup_fid = tr_rs + np.sqrt(max(0.0, (1 - pur_ref) * (1 - pur)))
+        key = "c64_plain" if path == "plain" else f"c64_fused_f{fuse}"
+        out[key] = {"seconds": t, "max_abs": maxabs, "frobenius": fro2 ** 0.5,
+                    "trace_distance_bound": 0.5 * 2 ** (n / 2) * fro2 ** 0.5,
+                    "prob_tv_distance": 0.5 * float(np.abs(p - p_ref).sum()),
+                    "trace_err": abs(vqd.vqd_trace(ctx, 0).real - out["f64_trace"]),
+                    "purity_err": abs(pur - pur_ref), "super_fidelity": sup_fid}
+        vqd.vqd_destroy(ctx)
+        torch.cuda.empty_cache()
+    vqd.vqd_destroy(ref)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.precision:
+        run_precision(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -253,17 +331,13 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    from paper_2306_07342_gb300 import replicas
+
     def sync_all():
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = replicas.max_over_ranks
 
     def make_step(ctx, path, ops=native):
         def step():

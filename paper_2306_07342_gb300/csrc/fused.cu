@@ -432,6 +432,8 @@ __device__ __forceinline__ uint32_t sw(uint32_t l) {
   return sizeof(T) == 4 ? l ^ ((l >> 4) & 15u) : l ^ ((l >> 3) & 7u);
 }
 
+constexpr uint32_t kThreads = 256;  // threads per CTA of the stage and wave kernels
+
 // Deposit the low bits of t at the positions pos[0..cnt) (ascending).
 __device__ __forceinline__ uint64_t deposit(uint64_t t, const int* pos, int cnt) {
   uint64_t r = 0;
@@ -495,7 +497,8 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
 #pragma unroll
   for (int i = 0; i < (DIAG ? 4 : 16); i++) S[i] = c[i];
   const Inserter<2> ins(B.lsorted);
-  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+  #pragma unroll 2
+  for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
     cx<T> x[4];
@@ -537,7 +540,8 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
     for (int i = 0; i < 16; i++) u[i] = c[i];
   }
   const Inserter<4> ins(B.lsorted);
-  for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+  #pragma unroll 2
+  for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     cx<T> x[16];
 #pragma unroll
@@ -615,8 +619,8 @@ template <class T>
 __device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>* __restrict__ coef, int cb, int ce,
                                             BlockOp* __restrict__ sops, const BlockOp* __restrict__ bops, int ob,
                                             int oe) {
-  for (int i = threadIdx.x; i < ce - cb; i += blockDim.x) csm[i] = coef[cb + i];
-  for (int i = threadIdx.x; i < oe - ob; i += blockDim.x) sops[i] = bops[ob + i];
+  for (int i = threadIdx.x; i < ce - cb; i += kThreads) csm[i] = coef[cb + i];
+  for (int i = threadIdx.x; i < oe - ob; i += kThreads) sops[i] = bops[ob + i];
 }
 
 template <class T>

@@ -102,10 +102,68 @@ __global__ void __launch_bounds__(256) k_sup1(cx<T>* __restrict__ st, uint64_t n
 }
 
 // ---- two-qubit unitary: A <- U A U^dagger on the 4x4 block A[r][c] = amplitude r | c << 2.
-// Column c of B = U A needs only column c of A, so A is consumed one column at a time and only B
-// (16 amplitudes) stays live; then row r of U A U^dagger needs only row r of B.
+// k_uni2_pair (FP32): two neighbouring threads share a group; thread h holds columns 2h and 2h+1
+// (8 amplitudes), so all of its loads are in flight at once with few registers.  B = U A needs only a
+// thread's own columns; U A U^dagger needs every column of B, so the partner's half of B comes over
+// one warp shuffle per value.  Member offsets and coefficients that depend on h are chosen between
+// two static parameter entries, never indexed by h.  The grid-stride step is even, so partners run
+// the same iterations.
+// k_uni2_whole (FP64): one thread per group, with the zero/real/imaginary coefficient flags, since
+// FP64 is bound by its FMA rate rather than by memory.
+template <class T>
+__global__ void __launch_bounds__(256) k_uni2_pair(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
+  GRID_STRIDE_LOOP(t, 2 * ngroups) {
+    const unsigned mask = __activemask();
+    const uint64_t g = t >> 1;
+    const bool h = (t & 1) != 0;
+    const uint64_t base = insert_zeros<4>(g, P.g.pos);
+    cx<T> B[2][4];  // B[j][r] = (U A)[r][2h + j]
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const uint64_t cofs = h ? P.g.off[(2 + j) << 2] : P.g.off[j << 2];
+      cx<T> a[4];
+#pragma unroll
+      for (int m = 0; m < 4; m++) a[m] = st[base + P.g.off[m] + cofs];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        cx<T> acc; acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) cmac<T>(acc, P.u[r * 4 + m], a[m]);
+        B[j][r] = acc;
+      }
+    }
+    cx<T> O[2][4];  // the partner's columns 2(1-h) + j
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        O[j][r].x = __shfl_xor_sync(mask, B[j][r].x, 1);
+        O[j][r].y = __shfl_xor_sync(mask, B[j][r].y, 1);
+      }
+    // A'[r][c] = sum_m B[r][m] conj(U[c][m]) for this thread's columns c = 2h + j; B[r][m] is the
+    // thread's own value when m's half equals h
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const uint64_t cofs = h ? P.g.off[(2 + j) << 2] : P.g.off[j << 2];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        cx<T> acc; acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+          const cx<T> bm = (((m >> 1) != 0) == h) ? B[m & 1][r] : O[m & 1][r];
+          cx<T> uc;
+          uc.x = h ? P.uc[(2 + j) * 4 + m].x : P.uc[j * 4 + m].x;
+          uc.y = h ? P.uc[(2 + j) * 4 + m].y : P.uc[j * 4 + m].y;
+          cmac<T>(acc, uc, bm);
+        }
+        st[base + P.g.off[r] + cofs] = acc;
+      }
+    }
+  }
+}
+
 template <class T, bool SPARSE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_uni2(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
+__global__ void __launch_bounds__(256) k_uni2_whole(cx<T>* __restrict__ st, uint64_t ngroups, const Uni2P<T> P) {
   GRID_STRIDE_LOOP(g, ngroups) {
     const uint64_t base = insert_zeros<4>(g, P.g.pos);
     cx<T> B[16];
@@ -419,8 +477,9 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
     }
     // conj keeps the flag class except ONE stays ONE; an entry equal to 1 has conj 1 as well.
     const uint64_t ng = N / 16;
-    if (use_sparse(p.coef, fp64)) k_uni2<T, true><<<grid_for(k_uni2<T, true>, ng), 256, 0, s>>>(st, ng, P);
-    else k_uni2<T, false><<<grid_for(k_uni2<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    if (!fp64) k_uni2_pair<T><<<grid_for(k_uni2_pair<T>, 2 * ng), 256, 0, s>>>(st, ng, P);
+    else if (use_sparse(p.coef, fp64)) k_uni2_whole<T, true><<<grid_for(k_uni2_whole<T, true>, ng), 256, 0, s>>>(st, ng, P);
+    else k_uni2_whole<T, false><<<grid_for(k_uni2_whole<T, false>, ng), 256, 0, s>>>(st, ng, P);
     return cudaGetLastError();
   }
   if (p.kind == KK_SUP2) {
