@@ -456,6 +456,8 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
   uint64_t M = 0;
   for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
   const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
+  // sw() only mixes bits 0..7 of the local index, so sw(tid + 256 it) = sw(tid) + 256 it
+  const uint32_t swt = sw<T>(threadIdx.x);
   uint64_t hi = 0;
   constexpr int K = 8;
   for (int it0 = 0; it0 < iters; it0 += K) {
@@ -469,11 +471,11 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
       }
 #pragma unroll
       for (int k = 0; k < K; k++)
-        if (it0 + k < iters) sm[sw<T>(threadIdx.x + 256u * (uint32_t)(it0 + k))] = v[k];
+        if (it0 + k < iters) sm[swt + 256u * (uint32_t)(it0 + k)] = v[k];
     } else {
 #pragma unroll
       for (int k = 0; k < K; k++)
-        if (it0 + k < iters) v[k] = sm[sw<T>(threadIdx.x + 256u * (uint32_t)(it0 + k))];
+        if (it0 + k < iters) v[k] = sm[swt + 256u * (uint32_t)(it0 + k)];
 #pragma unroll
       for (int k = 0; k < K; k++) {
         if (it0 + k < iters) st[base + lo + h] = v[k];

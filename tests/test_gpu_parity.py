@@ -311,3 +311,57 @@ def test_config2_full_size_sample_and_invariants(vqd, path, config2_full_sample)
         assert np.abs(flat[r + (c << 14)] - np.conj(flat[c + (r << 14)])).max() < 1e-6
     finally:
         vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- the largest workloads (15 and 16 qubits)
+def test_ion15_full_size_sample_vs_oracle(vqd):
+    """15 qubits (complex64 8.6 GB, complex128 17.2 GB): the first gates of the ion-trap program, both precisions,
+    element by element against the oracle (compared in the library's flat layout)."""
+    prog = config3_ion_alltoall()
+    ops = list(prog.ops[:3])
+    want = evolve.to_device_layout(evolve.run_program(Program(prog.n, ops)))
+    for p in PRECS:
+        for path in ("plain", "fused"):
+            ctx = vqd.vqd_create(prog.n, prec_code(vqd, p))
+            try:
+                if path == "plain":
+                    vqd.vqd_apply_native(ctx, 0, ops)
+                else:
+                    vqd.vqd_run_program(ctx, 0, ops)
+                got = vqd.vqd_get_state(ctx, 0)
+                assert np.abs(got - want).max() < tol(p, 3), (p, path)
+                assert abs(vqd.vqd_trace(ctx, 0) - 1) < tol(p, 3)
+                del got
+            finally:
+                vqd.vqd_destroy(ctx)
+
+
+def test_spin16_max_size_invariants_and_paths_agree(vqd):
+    """16 qubits, the largest supported size (complex64 34.4 GB): the first 240 native ops of the spin-chain program
+    through the plain and the fused path; CPTP invariants and agreement of the two paths on sampled amplitudes."""
+    prog = config5_spin_chain()
+    ops = prog.ops[:240]
+    n = prog.n
+    rng = np.random.default_rng(16)
+    r, c = rng.integers(0, 2 ** n, 8192), rng.integers(0, 2 ** n, 8192)
+    idx = r + (c << n)
+    samples, reds = {}, {}
+    for path in ("plain", "fused"):
+        ctx = vqd.vqd_create(n, vqd.VQD_F32)
+        try:
+            if path == "plain":
+                vqd.vqd_apply_native(ctx, 0, ops)
+            else:
+                vqd.vqd_run_program(ctx, 0, ops)
+            reds[path] = (vqd.vqd_trace(ctx, 0), vqd.vqd_purity(ctx, 0), vqd.vqd_prob(ctx, 0, [0, 7, 15]))
+            flat = vqd.vqd_get_state(ctx, 0)
+            samples[path] = flat[idx]
+            herm = np.abs(flat[idx] - np.conj(flat[c + (r << n)])).max()
+            del flat
+        finally:
+            vqd.vqd_destroy(ctx)
+        tr, pur, pr = reds[path]
+        assert abs(tr - 1) < 1e-4 and pur <= 1 + 1e-5 and herm < 1e-6
+        assert abs(pr.sum() - tr.real) < 1e-9 and pr.min() > -1e-7
+    assert np.abs(samples["plain"] - samples["fused"]).max() < tol_f32(len(ops))
+    assert abs(reds["plain"][1] - reds["fused"][1]) < 1e-5
