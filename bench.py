@@ -409,12 +409,26 @@ def main():
 
     extra = {}
     if not args.no_extra:
-        # ---- fused path, complex64
-        fms, fstats, _ = timed(make_step(ctx, "fused"), args.steps, 1, ctx)
+        # ---- fused path, complex64, with the autotuned fusion width and tile shape (tuned on the first
+        # 10 layers, outside the timed region)
+        from paper_2306_07342_gb300 import autotune
+        layer_ops = len(prog.ops) // prog.meta["depth"]
+        choice = autotune.tune(n, vqd.VQD_F32, native, sh, prefix=10 * layer_ops)
+        fuse = autotune.apply(ctx, choice)
+
+        def fused_step():
+            vqd.vqd_init_zero(ctx, 0)
+            vqd.vqd_run_program(ctx, 0, native, fuse)
+            vqd.vqd_prob(ctx, 0, list(range(n)))
+            vqd.vqd_trace(ctx, 0)
+            vqd.vqd_purity(ctx, 0)
+
+        fms, fstats, _ = timed(fused_step, args.steps, 1, ctx)
         fdom, froof = roofline(fstats, args.steps)
         extra["fused_c64"] = {"value": world * args.steps * units_per_step / (fms * 1e-3), "unit": UNIT,
                               "ms_per_step": fms / args.steps, "speedup_vs_plain": ms / fms,
                               "stages_per_step": fstats.get("fused_stage", {}).get("launches", 0) // args.steps,
+                              "autotuned": {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")},
                               "roofline": froof}
     vqd.vqd_destroy(ctx)
     if not args.no_extra:

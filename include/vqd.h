@@ -195,11 +195,20 @@ int vqd_run_batch(vqd_t ctx, const int64_t* offsets, const vqd_native_op* ops, i
 int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int* k, int* targets,
                    vqd_c128* mat);
 
-/* Plan of the fused path for an n-qubit program, without running it (host only).  info[0..7] =
+/* Tile shape of the fused and batched paths of a context: tile_bits index bits per shared-memory tile
+ * (<= 13 for VQD_F32, <= 12 for VQD_F64: a 64 KB tile; 0 = that maximum) of which passenger_bits
+ * (0..3; -1 = default 3 for VQD_F32, 2 for VQD_F64) are the lowest row bits, carried along so that
+ * every tile is made of contiguous DRAM runs.  Needs 4 + passenger_bits <= tile_bits.  Results do
+ * not depend on the shape; speed does (the autotuner in the Python package picks it). */
+int vqd_set_tile_shape(vqd_t ctx, int tile_bits, int passenger_bits);
+
+/* Plan of the fused path for an n-qubit program, without running it (host only); tile_bits and
+ * passenger_bits as in vqd_set_tile_shape.  info[0..7] =
  * {stages (one pass over the state each), blocks (one shared-memory sweep each), operators after
  * composition that are diagonal / 1-qubit superoperators / 2-qubit unitaries / 2-qubit
  * superoperators, largest tile (index bits), original operators}. */
-int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags, int64_t* info);
+int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, int tile_bits,
+                  int passenger_bits, unsigned flags, int64_t* info);
 
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */

@@ -1,0 +1,74 @@
+"""Autotuner of the fused path: fusion width and tile shape, picked by timing candidates.
+
+A candidate is (fuse_qubits, tile_bits, passenger_bits). The tuner runs a prefix of the program
+through ``vqd_run_program`` on a scratch state of the same size, for every candidate. It times the
+stage kernels with the library's CUDA-event launch accounting and returns the fastest candidate.
+Results can be cached in a JSON file, keyed by the qubit count, the precision and the program's gate
+structure (op codes and qubits, not angles).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import Iterable, Optional
+
+import numpy as np
+
+from . import vqd
+
+CANDIDATES = {
+    vqd.VQD_F32: [(f, tb, p) for f in (4, 5, 6) for (tb, p) in ((13, 3), (13, 2), (12, 2))],
+    vqd.VQD_F64: [(f, tb, p) for f in (4, 5, 6) for (tb, p) in ((12, 2), (12, 1), (11, 1))],
+}
+
+
+def structure_key(n: int, prec: int, native: np.ndarray) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(native["code"]).tobytes())
+    h.update(np.ascontiguousarray(native["q"]).tobytes())
+    return f"n{n}-p{prec}-{len(native)}-{h.hexdigest()[:16]}"
+
+
+def tune(n: int, prec: int, ops, stream: int = 0, prefix: int = 0, candidates: Optional[Iterable] = None,
+         cache_path: Optional[str] = None) -> dict:
+    """Fastest (fuse_qubits, tile_bits, passenger_bits) for this program; runs on a scratch state."""
+    native = ops if isinstance(ops, np.ndarray) else vqd.native_ops(ops)
+    sample = native[:prefix] if prefix else native
+    key = structure_key(n, prec, sample)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return cache[key]
+    cands = list(candidates) if candidates is not None else CANDIDATES[prec]
+    ctx = vqd.vqd_create(n, prec, stream)
+    trials = []
+    try:
+        for f, tb, p in cands:
+            vqd.vqd_set_tile_shape(ctx, tb, p)
+            vqd.vqd_run_program(ctx, 0, sample, f)          # warm-up (and plan)
+            vqd.vqd_sync(ctx)
+            vqd.vqd_profile(ctx, 2)
+            vqd.vqd_profile_reset(ctx)
+            vqd.vqd_run_program(ctx, 0, sample, f)
+            st = vqd.vqd_profile_read(ctx).get("fused_stage", {"total_ms": 0.0, "launches": 0})
+            vqd.vqd_profile(ctx, 0)
+            trials.append({"fuse_qubits": f, "tile_bits": tb, "passenger_bits": p, "ms": st["total_ms"],
+                           "stages": st["launches"]})
+    finally:
+        vqd.vqd_destroy(ctx)
+    best = min(trials, key=lambda t: t["ms"])
+    result = dict(best, trials=trials, sample_ops=int(len(sample)))
+    if cache_path:
+        cache[key] = result
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return result
+
+
+def apply(ctx, choice: dict) -> int:
+    """Set the tuned tile shape on a context; returns the fuse width to pass to vqd_run_program."""
+    vqd.vqd_set_tile_shape(ctx, choice["tile_bits"], choice["passenger_bits"])
+    return int(choice["fuse_qubits"])

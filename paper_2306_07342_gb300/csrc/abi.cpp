@@ -60,6 +60,7 @@ struct vqd_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpool;
   std::vector<int> pending;  // class of the launch timed by evpool[i]
   FusedCache fused;          // device buffers reused by the fused and batched paths
+  TileShape shape;           // tile shape of the fused and batched paths (defaults per precision)
 
   char* ptr(int inst) { return base + off[inst]; }
   size_t bytes(int inst) const { return vqd_state_bytes(n[inst], prec); }
@@ -270,6 +271,19 @@ int vqd_sync(vqd_t c) {
 
 const char* vqd_last_error(vqd_t c) { return c ? c->err.c_str() : g_err.c_str(); }
 
+int vqd_set_tile_shape(vqd_t c, int tile_bits, int passenger_bits) {
+  API_BEGIN
+  need_ctx(c);
+  const int maxb = tile_bits_budget(c->prec);
+  const int tb = tile_bits > 0 ? tile_bits : maxb;
+  const int L = passenger_bits >= 0 ? passenger_bits : default_passengers(c->prec);
+  if (tb > maxb || L > 3 || tb < 4 + L)
+    throw Error(VQD_EINVAL, "tile shape: need 4 + passengers <= tile bits <= " + std::to_string(maxb) + ", passengers <= 3");
+  c->shape.tile_bits = tile_bits;
+  c->shape.passengers = passenger_bits;
+  API_END(c)
+}
+
 int vqd_set_flags(vqd_t c, unsigned flags) {
   API_BEGIN
   need_ctx(c)->flags = flags;
@@ -376,7 +390,7 @@ int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int f
   need_inst(c, inst);
   std::vector<Op> list = compile_list(c, inst, nops, ops, flags);
   const int n = c->n[inst];
-  FusedPlan plan = plan_fused(list, n, c->prec, fuse_qubits);
+  FusedPlan plan = plan_fused(list, n, c->prec, fuse_qubits, c->shape);
   upload_plan(c->fused, plan, c->prec, c->stream);
   for (size_t s = 0; s < plan.stages.size(); s++) {
     timed(c, SC_FUSED, 2.0 * c->bytes(inst), plan.stages[s].weight * std::ldexp(1.0, 2 * n), 1,
@@ -404,7 +418,7 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
       try {
         std::vector<Op> list = compile_list(c, i, (int)(offsets[i + 1] - offsets[i]), ops + offsets[i], flags);
         nops[i] = list.size();
-        plans[i] = plan_fused(list, c->n[i], c->prec, fuse_qubits);
+        plans[i] = plan_fused(list, c->n[i], c->prec, fuse_qubits, c->shape);
       } catch (const Error& e) {
         codes[i] = e.code;
         errs[i] = e.what();
@@ -443,8 +457,8 @@ int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int
   API_END(nullptr)
 }
 
-int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags,
-                  int64_t* info) {
+int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, int tile_bits,
+                  int passenger_bits, unsigned flags, int64_t* info) {
   API_BEGIN
   if (!info || n < 1 || n > VQD_MAX_QUBITS || nops < 0 || (nops > 0 && !ops)) throw Error(VQD_EINVAL, "bad argument");
   if (prec != VQD_F64 && prec != VQD_F32) throw Error(VQD_EINVAL, "bad precision");
@@ -458,7 +472,10 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
         throw Error(VQD_EINVAL, "bad target qubit");
     list.push_back(compile_native(ops[i], flags));
   }
-  FusedPlan plan = plan_fused(list, n, prec, fuse_qubits);
+  TileShape shape;
+  shape.tile_bits = tile_bits;
+  shape.passengers = passenger_bits;
+  FusedPlan plan = plan_fused(list, n, prec, fuse_qubits, shape);
   for (int i = 0; i < 8; i++) info[i] = 0;
   info[0] = (int64_t)plan.stages.size();
   info[1] = (int64_t)plan.blocks.size();

@@ -28,7 +28,7 @@
 namespace vqd {
 
 int tile_bits_budget(int prec) { return prec == VQD_F32 ? 13 : 12; }  // 64 KB tiles
-static int passenger_bits(int prec) { return prec == VQD_F32 ? 3 : 2; }  // 64-byte runs
+int default_passengers(int prec) { return prec == VQD_F32 ? 3 : 2; }    // 64-byte runs
 static int default_fuse(int prec) { (void)prec; return 6; }
 
 static int popc(uint32_t x) { return __builtin_popcount(x); }
@@ -199,7 +199,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
 }
 
 static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::vector<int>& idx, uint32_t qmask,
-                        int n, int prec, bool whole) {
+                        int n, int L, bool whole) {
   // Blocks, members and their coefficients first: a stage whose coefficients overflow the shared
   // memory budget is split in two (each half is a valid stage on the same tile).
   const std::vector<Op> comp = compose_stage(ops, idx);
@@ -207,8 +207,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   for (const Op& o : comp) ncoef += is_diag(o) ? (o.k == 1 ? 4 : 16) : (o.k == 1 ? 16 : (o.unitary ? 16 : 256));
   if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap) && idx.size() > 1) {
     std::vector<int> a(idx.begin(), idx.begin() + idx.size() / 2), b(idx.begin() + idx.size() / 2, idx.end());
-    build_stage(plan, ops, a, qmask, n, prec, whole);
-    build_stage(plan, ops, b, qmask, n, prec, whole);
+    build_stage(plan, ops, a, qmask, n, L, whole);
+    build_stage(plan, ops, b, qmask, n, L, whole);
     return;
   }
   StageDesc sd;
@@ -217,8 +217,7 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   if (whole) {
     for (int b = 0; b < 2 * n; b++) in_tile[b] = true;
   } else {
-    const int L = std::min(passenger_bits(prec), n);
-    for (int b = 0; b < L; b++) in_tile[b] = true;
+    for (int b = 0; b < std::min(L, n); b++) in_tile[b] = true;
     for (int q = 0; q < n; q++)
       if (qmask >> q & 1) in_tile[q] = in_tile[q + n] = true;
   }
@@ -266,17 +265,20 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   plan.stages.push_back(sd);
 }
 
-FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits) {
+FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits, TileShape shape) {
   FusedPlan plan;
-  const int budget = tile_bits_budget(prec);
-  const int L = std::min(passenger_bits(prec), n);
+  const int budget = shape.tile_bits > 0 ? shape.tile_bits : tile_bits_budget(prec);
+  const int Lset = shape.passengers >= 0 ? shape.passengers : default_passengers(prec);
+  if (budget > tile_bits_budget(prec) || Lset > 3 || budget < 4 + Lset)
+    throw Error(VQD_EINVAL, "tile shape: need 4 + passengers <= tile bits <= the precision's maximum, passengers <= 3");
+  const int L = std::min(Lset, n);
   int f = fuse_qubits <= 0 ? default_fuse(prec) : fuse_qubits;
   if (f < 2 || f > VQD_MAX_FUSE) throw Error(VQD_EINVAL, "fuse_qubits must be in 2..6");
   if (ops.empty()) return plan;
   if (2 * n <= budget) {  // the whole state is one tile: one stage holds every operator
     std::vector<int> all(ops.size());
     for (size_t i = 0; i < ops.size(); i++) all[i] = (int)i;
-    build_stage(plan, ops, all, (1u << n) - 1, n, prec, true);
+    build_stage(plan, ops, all, (1u << n) - 1, n, L, true);
     return plan;
   }
   const uint32_t full = (1u << n) - 1;
@@ -311,7 +313,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubit
         break;
       }
     }
-    build_stage(plan, ops, stage, q, n, prec, false);
+    build_stage(plan, ops, stage, q, n, L, false);
     std::vector<int> next;
     next.reserve(deferred.size() + remaining.size() - i);
     next.insert(next.end(), deferred.begin(), deferred.end());
@@ -319,13 +321,6 @@ FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubit
     remaining.swap(next);
   }
   return plan;
-}
-
-BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vector<int>& n,
-                     const std::vector<size_t>& byte_offsets, int prec, int fuse_qubits) {
-  std::vector<FusedPlan> plans;
-  for (size_t i = 0; i < lists.size(); i++) plans.push_back(plan_fused(lists[i], n[i], prec, fuse_qubits));
-  return merge_batch(plans, n, byte_offsets, prec);
 }
 
 BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int>& n,
@@ -486,6 +481,35 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
   }
 }
 
+// Asynchronous tile load (cp.async): each thread issues all of its copies straight into shared memory
+// (no register staging, so every copy of the tile is in flight at once), then waits for them.
+template <class T>
+__device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base,
+                                                const int* bits, int nbits) {
+  const uint32_t size = 1u << nbits;
+  const int lowbits = min(nbits, 8);
+  if (threadIdx.x >= size) return;
+  uint64_t lo = 0;
+  for (int j = 0; j < lowbits; j++) lo |= (uint64_t)((threadIdx.x >> j) & 1u) << bits[j];
+  uint64_t M = 0;
+  for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
+  const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
+  const uint32_t swt = sw<T>(threadIdx.x);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+  uint64_t hi = 0;
+  for (int it = 0; it < iters; it++) {
+    const uint32_t dst = sbase + (swt + 256u * (uint32_t)it) * (uint32_t)sizeof(cx<T>);
+    const cx<T>* src = st + base + lo + hi;
+    if (sizeof(T) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+    else
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    hi = ((hi | ~M) + 1ull) & M;
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ---- one operator, one sweep over the tile.  Each kind has its own loop with the operator's
 // coefficients in registers (loaded once per sweep from shared memory); member s of a group is
 // r | c << k over the operator's tile bits.  The XOR swizzle is linear: sw(base | off) =
@@ -644,7 +668,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __
   const uint64_t ntiles = 1ull << nrest;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = deposit(t, s_rest, nrest);
-    tile_io<T, true>(st, sm, base, s_bits, nbits);
+    tile_load_async<T>(st, sm, base, s_bits, nbits);
     __syncthreads();
     tile_blocks<T>(sm, csm, nbits, blocks, bb, be, sops, S.op_begin);
     tile_io<T, false>(st, sm, base, s_bits, nbits);
@@ -691,7 +715,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __r
     const int nbits = S.nbits, nrest = S.nrest, op0 = S.op_begin;
     for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++) {
       const uint64_t base = deposit(t, s_rest, nrest);
-      tile_io<T, true>(st, sm, base, s_bits, nbits);
+      tile_load_async<T>(st, sm, base, s_bits, nbits);
       __syncthreads();
       tile_blocks<T>(sm, csm, nbits, blocks, S.block_begin, S.block_end, sops, op0);
       tile_io<T, false>(st, sm, base, s_bits, nbits);

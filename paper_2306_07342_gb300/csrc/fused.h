@@ -50,9 +50,16 @@ struct FusedPlan {
   int max_bits = 0;
 };
 
+// Tile shape of the fused path: index bits held in a tile (0 = default for the precision) and
+// low row bits carried along in every tile for contiguous DRAM runs (-1 = default).
+struct TileShape {
+  int tile_bits = 0;
+  int passengers = -1;
+};
+
 // Group the compiled operators of one n-qubit instance into stages of at most `fuse_qubits`
-// qubits (0 = default) whose tiles fit the shared-memory budget of precision `prec`.
-FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits);
+// qubits (0 = default) whose tiles have the given shape.
+FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits, TileShape shape = TileShape());
 
 // Per-instance description used by the batched kernel.
 struct BatchInst {
@@ -74,8 +81,6 @@ struct BatchPlan {
   std::vector<WaveItem> items;   // wave w holds items [wave_begin[w], wave_begin[w+1]), largest first
   std::vector<int> wave_begin;
 };
-BatchPlan plan_batch(const std::vector<std::vector<Op>>& lists, const std::vector<int>& n,
-                     const std::vector<size_t>& byte_offsets, int prec, int fuse_qubits);
 // Concatenate per-instance plans (planned independently, e.g. on several host threads).
 BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int>& n,
                       const std::vector<size_t>& byte_offsets, int prec);
@@ -102,7 +107,8 @@ cudaError_t launch_stage(FusedCache& c, const FusedPlan& p, int stage, int prec,
 void upload_batch(FusedCache& c, const BatchPlan& p, int prec, cudaStream_t s);
 cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base, cudaStream_t s);
 
-// Shared-memory tile budget (index bits) for a precision.
+// Largest tile (index bits) the shared-memory budget allows for a precision, and the defaults.
 int tile_bits_budget(int prec);
+int default_passengers(int prec);
 
 }  // namespace vqd

@@ -88,7 +88,8 @@ def lib() -> ctypes.CDLL:
             "vqd_profile_reset": (I, [P]),
             "vqd_profile_read": (I, [P, I, P, P]),
             "vqd_prob_static": (I, [P, I, I, I, P, P, P]),
-            "vqd_plan_info": (I, [I, I, I, P, I, U, P]),
+            "vqd_plan_info": (I, [I, I, I, P, I, I, I, U, P]),
+            "vqd_set_tile_shape": (I, [P, I, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -169,6 +170,10 @@ def vqd_sync(ctx):
     _check(lib().vqd_sync(ctx), ctx)
 
 
+def vqd_set_tile_shape(ctx, tile_bits: int = 0, passenger_bits: int = -1):
+    _check(lib().vqd_set_tile_shape(ctx, tile_bits, passenger_bits), ctx)
+
+
 def vqd_set_flags(ctx, flags: int):
     _check(lib().vqd_set_flags(ctx, flags), ctx)
 
@@ -234,11 +239,12 @@ def vqd_compile_op(op, flags: int = 0):
     return "S", tuple(t[:kk]), m[: 16 ** kk].reshape(4 ** kk, 4 ** kk)
 
 
-def vqd_plan_info(n: int, prec: int, ops, fuse_qubits: int = 0, flags: int = 0) -> dict:
+def vqd_plan_info(n: int, prec: int, ops, fuse_qubits: int = 0, flags: int = 0, tile_bits: int = 0,
+                  passenger_bits: int = -1) -> dict:
     """Fused-path plan statistics for a program (host only, no GPU needed)."""
     a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
     info = np.zeros(8, dtype=np.int64)
-    _check(lib().vqd_plan_info(n, prec, len(a), _ptr(a), fuse_qubits, flags, _ptr(info)))
+    _check(lib().vqd_plan_info(n, prec, len(a), _ptr(a), fuse_qubits, tile_bits, passenger_bits, flags, _ptr(info)))
     keys = ["stages", "blocks", "diag", "sup1", "uni2", "sup2", "max_tile_bits", "native_ops"]
     return dict(zip(keys, (int(x) for x in info)))
 

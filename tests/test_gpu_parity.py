@@ -365,3 +365,47 @@ def test_spin16_max_size_invariants_and_paths_agree(vqd):
         assert abs(pr.sum() - tr.real) < 1e-9 and pr.min() > -1e-7
     assert np.abs(samples["plain"] - samples["fused"]).max() < tol_f32(len(ops))
     assert abs(reds["plain"][1] - reds["fused"][1]) < 1e-5
+
+
+# ---------------------------------------------------------------- tile shapes and the autotuner
+@pytest.mark.parametrize("p", PRECS)
+def test_tile_shapes_give_the_same_result(vqd, p):
+    prog = random_program(303, 8, 120)
+    want = evolve.run_program(prog)
+    shapes = [(13, 3), (13, 2), (12, 2), (11, 1), (8, 0)] if p == "f32" else [(12, 2), (11, 1), (8, 0)]
+    for tb, L in shapes:
+        ctx = vqd.vqd_create(prog.n, prec_code(vqd, p))
+        try:
+            vqd.vqd_set_tile_shape(ctx, tb, L)
+            vqd.vqd_run_program(ctx, 0, prog.ops, 4)
+            got = gpu_state(vqd, ctx)
+        finally:
+            vqd.vqd_destroy(ctx)
+        assert np.abs(got - want).max() < tol(p, len(prog.ops)), (tb, L)
+    ctx = vqd.vqd_create(4, prec_code(vqd, p))
+    try:
+        with pytest.raises(vqd.VQDError):
+            vqd.vqd_set_tile_shape(ctx, 14, 3)                # above the 64 KB tile
+        with pytest.raises(vqd.VQDError):
+            vqd.vqd_set_tile_shape(ctx, 5, 2)                 # a 2-qubit operator needs 4 bits + passengers
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results(vqd, tmp_path):
+    from paper_2306_07342_gb300 import autotune
+    prog = config2_sc_grid(seed=11, rows=2, cols=5, depth=6)
+    cache = str(tmp_path / "tune.json")
+    choice = autotune.tune(prog.n, vqd.VQD_F32, prog.ops, cache_path=cache)
+    assert (choice["fuse_qubits"], choice["tile_bits"], choice["passenger_bits"]) in autotune.CANDIDATES[vqd.VQD_F32]
+    assert len(choice["trials"]) == len(autotune.CANDIDATES[vqd.VQD_F32])
+    assert autotune.tune(prog.n, vqd.VQD_F32, prog.ops, cache_path=cache) == choice    # cached
+    want = evolve.run_program(prog)
+    ctx = vqd.vqd_create(prog.n, vqd.VQD_F32)
+    try:
+        f = autotune.apply(ctx, choice)
+        vqd.vqd_run_program(ctx, 0, prog.ops, f)
+        got = gpu_state(vqd, ctx)
+    finally:
+        vqd.vqd_destroy(ctx)
+    assert np.abs(got - want).max() < tol_f32(len(prog.ops))
