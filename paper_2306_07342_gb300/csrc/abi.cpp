@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <atomic>
+#include <functional>
 #include <memory>
 #include <thread>
 #include <string>
@@ -59,7 +60,15 @@ struct vqd_ctx {
   Stat stats[SC_COUNT];
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpool;
   std::vector<int> pending;  // class of the launch timed by evpool[i]
-  FusedCache fused;          // device buffers reused by the fused and batched paths
+  FusedCache fused;          // device buffers of the fused path
+  // Batched path: its own device buffers, and the CUDA graph of the last batch (replayed when the
+  // same program runs again on a capturable stream).
+  FusedCache batch;
+  uint64_t batch_key = 0;
+  cudaGraphExec_t batch_graph = nullptr;
+  std::vector<int> batch_passes;
+  std::vector<size_t> batch_nops;
+  int64_t batch_waves = 0;
   TileShape shape;           // tile shape of the fused and batched paths (defaults per precision)
 
   char* ptr(int inst) { return base + off[inst]; }
@@ -171,6 +180,8 @@ static void free_ctx(vqd_ctx* c) {
     cudaEventDestroy(e.second);
   }
   fused_cache_free(c->fused);
+  if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
+  fused_cache_free(c->batch);
   if (c->owns && c->base) cudaFree(c->base);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_out) cudaFree(c->d_out);
@@ -212,6 +223,8 @@ int report_static_error(int code, const char* msg) {
   return code;
 }
 }  // namespace vqd
+
+using F_LAUNCH = std::function<cudaError_t()>;
 
 // ================================================================== exported API
 extern "C" {
@@ -399,6 +412,16 @@ int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int f
   API_END(c)
 }
 
+// FNV-1a over the bytes of the batch description: identical programs give identical keys.
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; i++) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
 int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags) {
   API_BEGIN
   need_ctx(c);
@@ -406,6 +429,23 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
   const int count = (int)c->n.size();
   for (int i = 0; i < count; i++)
     if (offsets[i] < 0 || offsets[i + 1] < offsets[i]) throw Error(VQD_EINVAL, "offsets must be non-decreasing");
+  uint64_t key = 1469598103934665603ull;
+  key = fnv1a(key, offsets, sizeof(int64_t) * (count + 1));
+  key = fnv1a(key, ops, sizeof(vqd_native_op) * (size_t)offsets[count]);
+  const int params[4] = {fuse_qubits, (int)flags, c->shape.tile_bits, c->shape.passengers};
+  key = fnv1a(key, params, sizeof(params));
+  auto account = [&](int64_t launches, F_LAUNCH launch) {
+    double bytes = 0, upd = 0;
+    for (int i = 0; i < count; i++) {
+      bytes += 2.0 * c->bytes(i) * c->batch_passes[i];
+      upd += (double)c->batch_nops[i] * std::ldexp(1.0, 2 * c->n[i]);
+    }
+    timed(c, SC_BATCH, bytes, upd, launches, launch);
+  };
+  if (c->batch_graph && key == c->batch_key) {  // same batch as last time: replay its graph
+    account(1, [&] { return cudaGraphLaunch(c->batch_graph, c->stream); });
+    return VQD_OK;
+  }
   // Instances are compiled and planned independently, on several host threads.
   std::vector<FusedPlan> plans(count);
   std::vector<size_t> nops(count);
@@ -435,14 +475,31 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
   for (int i = 0; i < count; i++)
     if (codes[i] != VQD_OK) throw Error(codes[i], "instance " + std::to_string(i) + ": " + errs[i]);
   BatchPlan plan = merge_batch(plans, c->n, c->off, c->prec);
-  upload_batch(c->fused, plan, c->prec, c->stream);
-  double bytes = 0, upd = 0;
-  for (int i = 0; i < count; i++) {
-    bytes += 2.0 * c->bytes(i) * plan.passes[i];
-    upd += (double)nops[i] * std::ldexp(1.0, 2 * c->n[i]);
+  if (c->batch_graph) {
+    cudaGraphExecDestroy(c->batch_graph);
+    c->batch_graph = nullptr;
   }
-  timed(c, SC_BATCH, bytes, upd, (int64_t)plan.wave_begin.size() - 1,
-        [&] { return launch_batch(c->fused, plan, c->prec, c->base, c->stream); });
+  upload_batch(c->batch, plan, c->prec, c->stream);
+  c->batch_passes = plan.passes;
+  c->batch_nops = nops;
+  c->batch_waves = (int64_t)plan.wave_begin.size() - 1;
+  // On a stream that can be captured (not the legacy default stream), the waves are captured into
+  // one CUDA graph, launched now and replayed by later calls with the same batch.
+  if (c->stream != nullptr) {
+    cudaGraph_t g = nullptr;
+    cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+    cudaError_t le = launch_batch(c->batch, plan, c->prec, c->base, c->stream);
+    cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+    cuda_check(le, "batched waves (capture)");
+    cuda_check(ce, "end graph capture");
+    cudaError_t ie = cudaGraphInstantiate(&c->batch_graph, g, 0);
+    cudaGraphDestroy(g);
+    cuda_check(ie, "instantiate batch graph");
+    c->batch_key = key;
+    account(1, [&] { return cudaGraphLaunch(c->batch_graph, c->stream); });
+  } else {
+    account(c->batch_waves, [&] { return launch_batch(c->batch, plan, c->prec, c->base, c->stream); });
+  }
   API_END(c)
 }
 

@@ -409,3 +409,33 @@ def test_autotuner_picks_a_candidate_and_keeps_results(vqd, tmp_path):
     finally:
         vqd.vqd_destroy(ctx)
     assert np.abs(got - want).max() < tol_f32(len(prog.ops))
+
+
+def test_batch_graph_capture_and_replay(vqd):
+    """On a non-default stream the batch is captured into a CUDA graph; running the same batch again replays
+    it (after re-initialising the states) and a different batch rebuilds it.  Results match the oracle each time."""
+    torch = pytest.importorskip("torch")
+    from workloads import config4_neutral_batch
+    progs = config4_neutral_batch(seed=12, count=6, n_lo=3, n_hi=9, depth=2)
+    stream = torch.cuda.Stream()
+    ctx = vqd.vqd_create_batch([q.n for q in progs], vqd.VQD_F32, stream.cuda_stream)
+    try:
+        for round_ in range(3):
+            if round_ == 2:     # a different batch: new angles for every instance
+                progs = config4_neutral_batch(seed=13, count=6, n_lo=3, n_hi=9, depth=2)
+                ctx2 = vqd.vqd_create_batch([q.n for q in progs], vqd.VQD_F32, stream.cuda_stream)
+                vqd.vqd_destroy(ctx)
+                ctx = ctx2
+            for i in range(len(progs)):
+                vqd.vqd_init_zero(ctx, i)
+            vqd.vqd_profile(ctx, 1)
+            vqd.vqd_profile_reset(ctx)
+            vqd.vqd_run_batch(ctx, [q.ops for q in progs])
+            launches = vqd.vqd_profile_read(ctx)["batch"]["launches"]
+            assert launches == 1                          # one graph launch
+            vqd.vqd_sync(ctx)
+            for i, prog in enumerate(progs):
+                want = evolve.run_program(prog)
+                assert np.abs(gpu_state(vqd, ctx, i) - want).max() < tol_f32(len(prog.ops)), (round_, i)
+    finally:
+        vqd.vqd_destroy(ctx)
