@@ -449,6 +449,12 @@ def main():
         kern_ms = sum(v["total_ms"] for k, v in dstats.items() if k not in ("reduce", "init"))
         fp64_rate = len(sample) * 4.0 ** n / (kern_ms * 1e-3)
         droof["bound"] = "alu" if ddom in ("sup1", "uni2", "sup2") else "hbm"
+        # the same sample through the fused path in FP64
+        fms64, fst64, _ = timed(make_step(ctx64, "fused", sample), 1, 1, ctx64)
+        fk64 = sum(v["total_ms"] for k, v in fst64.items() if k not in ("reduce", "init"))
+        extra["fused_f64_sample"] = {"value": world * len(sample) * 4.0 ** n / (fk64 * 1e-3), "unit": UNIT,
+                                     "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
+                                     "stages": fst64.get("fused_stage", {}).get("launches", 0)}
         extra["plain_f64_sample"] = {"value": world * fp64_rate, "unit": UNIT,
                                      "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
                                      "roofline_hbm": droof,
