@@ -166,6 +166,30 @@ def load_traffic(kernel_class: str):
     return rec["bytes_per_launch"] if h == rec["source_sha256_16"] else None
 
 
+def measure_trajectories(vqd, torch, prog, native, stream_handle, ntraj=1024):
+    """The same program as Monte-Carlo statevector trajectories (one CTA per trajectory, statevector in shared
+    memory): <sum_q Z_q> estimated from `ntraj` trajectories against the density-matrix value."""
+    import numpy as np
+    n = prog.n
+    codes = np.zeros((n, n), np.uint8)
+    for q in range(n):
+        codes[q, q] = 3
+    coeffs = np.ones(n)
+    t0 = time.perf_counter()
+    vals, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F32, native, ntraj, 2024, codes, coeffs, 0, stream_handle)
+    wall = time.perf_counter() - t0
+    ctx = vqd.vqd_create(n, vqd.VQD_F32, stream_handle)
+    try:
+        vqd.vqd_run_program(ctx, 0, native)
+        exact = vqd.vqd_expect(ctx, 0, codes, coeffs)
+    finally:
+        vqd.vqd_destroy(ctx)
+    return {"trajectories": ntraj, "seconds": wall, "trajectories_per_s": ntraj / wall,
+            "statevector_amp_updates_per_s": ntraj * len(native) * 2.0 ** n / wall,
+            "observable": "sum_q Z_q", "mean": mean, "stderr": se, "density_matrix_value": exact,
+            "z_score": (mean - exact) / se if se > 0 else None}
+
+
 def measure_batch(vqd, torch, stream_handle, count):
     """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of
     persistent kernels), against one launch sequence per instance (fused and plain) on a sample."""
@@ -461,6 +485,9 @@ def main():
                                      "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
                                                    for k, v in dstats.items()}}
         vqd.vqd_destroy(ctx64)
+
+    if not args.no_extra:
+        extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
 
     if not args.no_extra and args.batch_count > 0:
         extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)

@@ -238,6 +238,29 @@ int vqd_get_state(vqd_t ctx, int inst, vqd_c128* host_out);
 int vqd_set_state(vqd_t ctx, int inst, const vqd_c128* host_in);
 
 /* ------------------------------------------------------------------------------------------
+ * Monte-Carlo trajectories (Sec. 2: the statevector alternative to the density matrix)
+ *
+ * Estimates Re sum_t coeffs[t] tr(P_t rho) for the state rho that the native program `ops` makes
+ * from |0..0>, by ntraj statevector trajectories.  In every trajectory each channel is replaced by
+ * one of its Kraus operators K_k, chosen with probability ||K_k psi||^2 (psi <- K_k psi / norm);
+ * a trace-decreasing channel's missing probability ends the trajectory, which then contributes 0.
+ * Kraus operators are enumerated in a fixed order: a composite process (step A then step B) has
+ * operators B_j A_i with A's index i outer; Pauli channels list I, X, Y, Z (two-qubit: the first
+ * qubit's Pauli outer).  The draw for native op o in trajectory t is the first two 32-bit words of
+ * Philox4x32-10 (Salmon et al., SC 2011) at counter (o, t, 0, 0) with key (seed low, seed high),
+ * as a 53-bit uniform u = (w0 >> 5) 2^-27 + (w1 >> 6) 2^-53; operator k is chosen when
+ * sum_{j<k} p_j <= u < sum_{j<=k} p_j.
+ *
+ * n <= 14 (VQD_F32) or 13 (VQD_F64): every trajectory keeps its statevector in shared memory.
+ * paulis is nterms x n codes (0=I,1=X,2=Y,3=Z) as in vqd_expect.  out (host, ntraj) receives each
+ * trajectory's value; mean and stderr_out (either may be NULL) the sample mean and its standard
+ * error.  Synchronous on `stream`.  Returns VQD_ENOTSUP for n above the limit or more than 16
+ * state-dependent Kraus operators in one channel; messages via vqd_last_error(NULL). */
+int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* ops, unsigned flags, int ntraj, uint64_t seed,
+                    int nterms, const uint8_t* paulis, const double* coeffs, void* stream, double* out,
+                    double* mean, double* stderr_out);
+
+/* ------------------------------------------------------------------------------------------
  * Allocation-free reduction (the paper has no counterpart: this serves callers of the library)
  *
  * vqd_prob_static computes the same marginal Z-basis probabilities as vqd_prob, for callers that

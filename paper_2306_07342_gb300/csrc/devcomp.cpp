@@ -404,4 +404,135 @@ Pass classify(const Op& op) {
   return p;
 }
 
+// ================================================================== Kraus forms (trajectory path)
+namespace {
+
+Mat scaled(const Mat& m, double a) {
+  Mat r(m);
+  for (cd& x : r) x *= a;
+  return r;
+}
+std::vector<Mat> kraus_pauli1(const double* w) {  // order I, X, Y, Z; zero weights dropped
+  std::vector<Mat> ks;
+  for (int s = 0; s < 4; s++)
+    if (w[s] > 0) ks.push_back(scaled(pauli(s), std::sqrt(w[s])));
+  return ks;
+}
+Mat two(const Mat& lo, const Mat& hi) { return kron(hi, 2, lo, 2); }
+std::vector<Mat> kraus_depol2(double p) {  // low qubit's Pauli outer, high qubit's inner
+  std::vector<Mat> ks;
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < 4; b++) {
+      double w = (a == 0 && b == 0) ? 1 - p : p / 15;
+      if (w > 0) ks.push_back(scaled(two(pauli(a), pauli(b)), std::sqrt(w)));
+    }
+  return ks;
+}
+std::vector<Mat> kraus_three2(double p, int s) {  // (1-p) I + p/3 (S (x) I, I (x) S, S (x) S), S = pauli(s)
+  std::vector<Mat> ks = {scaled(eye(4), std::sqrt(1 - p))};
+  if (p > 0) {
+    ks.push_back(scaled(two(pauli(s), pauli(0)), std::sqrt(p / 3)));
+    ks.push_back(scaled(two(pauli(0), pauli(s)), std::sqrt(p / 3)));
+    ks.push_back(scaled(two(pauli(s), pauli(s)), std::sqrt(p / 3)));
+  }
+  return ks;
+}
+std::vector<Mat> kraus_amp(double p) { return {{1.0, 0.0, 0.0, std::sqrt(1 - p)}, {0.0, std::sqrt(p), 0.0, 0.0}}; }
+std::vector<Mat> kraus_then(const std::vector<Mat>& first, const std::vector<Mat>& second, int d) {
+  std::vector<Mat> ks;
+  for (const Mat& A : first)
+    for (const Mat& B : second) ks.push_back(mul(B, A, d));
+  return ks;
+}
+
+}  // namespace
+
+KrausForm compile_kraus_form(const vqd_native_op& o, unsigned flags) {
+  Op op = compile_native(o, flags);  // validates the op; gives U for unitaries
+  KrausForm f;
+  f.k = op.k;
+  f.q[0] = op.q[0];
+  f.q[1] = op.q[1];
+  if (op.unitary) {
+    f.unitary = true;
+    f.K = {op.m};
+    return f;
+  }
+  f.unitary = false;
+  const double* P = o.par;
+  switch (o.code) {
+    case VQD_OP_DEPOL1: { double w[4] = {1 - P[0], P[0] / 3, P[0] / 3, P[0] / 3}; f.K = kraus_pauli1(w); break; }
+    case VQD_OP_DEPH1: { double w[4] = {1 - P[0], 0, 0, P[0]}; f.K = kraus_pauli1(w); break; }
+    case VQD_OP_BITFLIP: { double w[4] = {1 - P[0], P[0], 0, 0}; f.K = kraus_pauli1(w); break; }
+    case VQD_OP_DEPOL2: f.K = kraus_depol2(P[0]); break;
+    case VQD_OP_DEPH2: f.K = kraus_three2(P[0], 3); break;
+    case VQD_OP_BITFLIP2: f.K = kraus_three2(P[0], 1); break;
+    case VQD_OP_AMP: f.K = kraus_amp(P[0]); break;
+    case VQD_OP_GAMP: {
+      double g = 1 - std::exp(-P[0] / P[1]), a = std::sqrt(P[2]), b = std::sqrt(1 - P[2]);
+      f.K = {{a, 0.0, 0.0, a * std::sqrt(1 - g)}, {0.0, a * std::sqrt(g), 0.0, 0.0},
+             {b * std::sqrt(1 - g), 0.0, 0.0, b}, {0.0, 0.0, b * std::sqrt(g), 0.0}};
+      break;
+    }
+    case VQD_OP_IDLE:
+    case VQD_OP_IDLE_DEPOL:
+    case VQD_OP_AMPDEPH2: {
+      double tphi = dephasing_time(P[1], P[2], flags);
+      double pd = t2_deph_p(P[0], tphi);
+      double wd[4] = {1 - pd, 0, 0, pd};
+      std::vector<Mat> first;
+      if (o.code == VQD_OP_IDLE_DEPOL) {
+        double q = t1_depol_p(P[0], P[1]);
+        double w[4] = {1 - q, q / 3, q / 3, q / 3};
+        first = kraus_pauli1(w);
+      } else {
+        first = kraus_amp(t1_amp_p(P[0], P[1]));
+      }
+      std::vector<Mat> one = kraus_then(first, kraus_pauli1(wd), 2);
+      if (o.code == VQD_OP_AMPDEPH2) {
+        for (const Mat& A : one)
+          for (const Mat& B : one) f.K.push_back(two(A, B));
+      } else {
+        f.K = one;
+      }
+      break;
+    }
+    case VQD_OP_STDERR1:
+    case VQD_OP_STDERR2: {
+      double p, q;
+      stderr_params(op.k, P[0], P[1], &p, &q);
+      if (op.k == 1) {
+        double wq[4] = {1 - q, q / 3, q / 3, q / 3}, wp[4] = {1 - p, 0, 0, p};
+        f.K = kraus_then(kraus_pauli1(wq), kraus_pauli1(wp), 2);
+      } else {
+        f.K = kraus_then(kraus_depol2(q), kraus_three2(p, 3), 4);
+      }
+      break;
+    }
+    case VQD_OP_LEAK_INIT: f.K = {{std::sqrt(1 - P[0]), 0.0, 0.0, 1.0}}; break;
+    case VQD_OP_LEAK_CZ: f.K = {diag4(1.0, std::sqrt(1 - P[0]), std::sqrt(1 - P[0]), std::sqrt(1 - P[1]))}; break;
+    default: throw Error(VQD_EINVAL, "no Kraus form for this op");
+  }
+  // state-independent branch probabilities: K_k^dagger K_k = w_k I for every k
+  const int d = 1 << op.k;
+  f.mixture = true;
+  for (const Mat& K : f.K) {
+    double w = 0;
+    for (int i = 0; i < d * d; i++) w += std::norm(K[i]);
+    w /= d;
+    for (int a = 0; a < d && f.mixture; a++)
+      for (int b = 0; b < d; b++) {
+        cd s = 0;
+        for (int l = 0; l < d; l++) s += std::conj(K[l * d + a]) * K[l * d + b];
+        if (std::abs(s - (a == b ? w : 0.0)) > 1e-12) {
+          f.mixture = false;
+          break;
+        }
+      }
+    f.w.push_back(w);
+  }
+  if (!f.mixture) f.w.clear();
+  return f;
+}
+
 }  // namespace vqd

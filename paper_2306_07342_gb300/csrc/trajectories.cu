@@ -1,0 +1,423 @@
+// Monte-Carlo trajectory path of libvqd: Pauli-sum expectation values from statevector trajectories.
+//
+// Sec. 2 describes the unravelling that replaces the density matrix: every decoherence channel is
+// replaced, in each trajectory, by one of its Kraus operators chosen at random, the chosen operator
+// acts on a statevector, and the expectation value is averaged over trajectories.  Here operator k
+// of a channel {K_k} is chosen with probability p_k = ||K_k psi||^2 and psi <- K_k psi / sqrt(p_k).
+// When sum_k p_k < 1 (trace-decreasing leakage) the missing probability is a branch in which the
+// trajectory is lost and contributes 0, so the mean still estimates Re tr(H rho).
+//
+// One CTA runs one trajectory at a time with the whole statevector in shared memory (2^n
+// amplitudes: n <= 14 for complex64, n <= 13 for complex128).  The random number of channel o in
+// trajectory t is the first Philox4x32-10 output for counter (o, t, 0, 0) and key = the seed
+// (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011); the same
+// draws can therefore be reproduced anywhere.  Channels whose Kraus operators are all multiples
+// of unitaries have state-independent probabilities and skip the norm computation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "vqd_internal.h"
+
+namespace vqd {
+namespace dev {
+
+template <class T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+template <class T> using cx = typename V2<T>::t;
+
+enum { TJ_UNITARY = 0, TJ_MIXTURE = 1, TJ_KRAUS = 2 };
+constexpr int kTrajThreads = 256;
+constexpr int kMaxKraus = 16;  // state-dependent channels (mixtures may have more operators)
+
+struct TrajOp {
+  int kind;
+  int k;
+  int q[2];
+  int nK;
+  int coef;  // offset (complex) of operator 0; operator j at coef + j d^2
+  int wofs;  // mixtures: offset of the weights
+  int pad;
+};
+
+struct PauliTerm {
+  uint32_t xm, zy;
+  int ny;
+  int pad;
+  double c;
+};
+
+// Philox4x32 with 10 rounds: round (x0,x1,x2,x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
+// lo(M0 x0)), key bumped by the Weyl constants after each round.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; r++) {
+    const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Uniform double in [0, 1) with 53 random bits from the first two output words.
+__host__ __device__ inline double draw_uniform(uint64_t seed, uint32_t op, uint32_t traj) {
+  uint32_t c[4] = {op, traj, 0u, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> cmadd(cx<T> acc, const cx<T>& c, const cx<T>& x) {
+  acc.x = fma(c.x, x.x, acc.x);
+  acc.x = fma(-c.y, x.y, acc.x);
+  acc.y = fma(c.x, x.y, acc.y);
+  acc.y = fma(c.y, x.x, acc.y);
+  return acc;
+}
+
+__device__ __forceinline__ uint32_t ins0(uint32_t g, int p) { return g + (g & ~((1u << p) - 1u)); }
+
+// psi <- scale * K psi on the op's qubits (K is d x d, row-major, index little-endian over q)
+template <class T>
+__device__ void apply_op(cx<T>* __restrict__ psi, int n, const TrajOp& op, const cx<T>* __restrict__ K, T scale) {
+  if (op.k == 1) {
+    const uint32_t m = 1u << op.q[0];
+    const cx<T> a = K[0], b = K[1], c = K[2], d = K[3];
+    for (uint32_t g = threadIdx.x; g < (1u << (n - 1)); g += kTrajThreads) {
+      const uint32_t i0 = ins0(g, op.q[0]);
+      const cx<T> x0 = psi[i0], x1 = psi[i0 | m];
+      cx<T> y0, y1;
+      y0.x = 0; y0.y = 0; y1 = y0;
+      y0 = cmadd<T>(cmadd<T>(y0, a, x0), b, x1);
+      y1 = cmadd<T>(cmadd<T>(y1, c, x0), d, x1);
+      y0.x *= scale; y0.y *= scale; y1.x *= scale; y1.y *= scale;
+      psi[i0] = y0;
+      psi[i0 | m] = y1;
+    }
+  } else {
+    const int lo = min(op.q[0], op.q[1]), hi = max(op.q[0], op.q[1]);
+    const uint32_t m0 = 1u << op.q[0], m1 = 1u << op.q[1];
+    cx<T> U[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) U[i] = K[i];
+    for (uint32_t g = threadIdx.x; g < (1u << (n - 2)); g += kTrajThreads) {
+      const uint32_t b = ins0(ins0(g, lo), hi);
+      const uint32_t idx[4] = {b, b | m0, b | m1, b | m0 | m1};
+      cx<T> x[4];
+#pragma unroll
+      for (int s = 0; s < 4; s++) x[s] = psi[idx[s]];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        cx<T> y;
+        y.x = 0; y.y = 0;
+#pragma unroll
+        for (int s = 0; s < 4; s++) y = cmadd<T>(y, U[r * 4 + s], x[s]);
+        y.x *= scale;
+        y.y *= scale;
+        psi[idx[r]] = y;
+      }
+    }
+  }
+}
+
+// p[k] = ||K_k psi||^2 for k < nK (FP64 accumulation); result in red[0..nK)
+template <class T>
+__device__ void kraus_norms(const cx<T>* __restrict__ psi, int n, const TrajOp& op, const cx<T>* __restrict__ Ks,
+                            double* __restrict__ red) {
+  double acc[kMaxKraus];
+#pragma unroll
+  for (int j = 0; j < kMaxKraus; j++) acc[j] = 0.0;
+  if (op.k == 1) {
+    const uint32_t m = 1u << op.q[0];
+    for (uint32_t g = threadIdx.x; g < (1u << (n - 1)); g += kTrajThreads) {
+      const uint32_t i0 = ins0(g, op.q[0]);
+      const cx<T> x0 = psi[i0], x1 = psi[i0 | m];
+#pragma unroll
+      for (int j = 0; j < kMaxKraus; j++) {
+        if (j >= op.nK) break;
+        const cx<T>* K = Ks + 4 * j;
+        cx<T> y0, y1;
+        y0.x = 0; y0.y = 0; y1 = y0;
+        y0 = cmadd<T>(cmadd<T>(y0, K[0], x0), K[1], x1);
+        y1 = cmadd<T>(cmadd<T>(y1, K[2], x0), K[3], x1);
+        acc[j] += (double)y0.x * y0.x + (double)y0.y * y0.y + (double)y1.x * y1.x + (double)y1.y * y1.y;
+      }
+    }
+  } else {
+    const int lo = min(op.q[0], op.q[1]), hi = max(op.q[0], op.q[1]);
+    const uint32_t m0 = 1u << op.q[0], m1 = 1u << op.q[1];
+    for (uint32_t g = threadIdx.x; g < (1u << (n - 2)); g += kTrajThreads) {
+      const uint32_t b = ins0(ins0(g, lo), hi);
+      const cx<T> x[4] = {psi[b], psi[b | m0], psi[b | m1], psi[b | m0 | m1]};
+#pragma unroll
+      for (int j = 0; j < kMaxKraus; j++) {
+        if (j >= op.nK) break;
+        const cx<T>* K = Ks + 16 * j;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          cx<T> y;
+          y.x = 0; y.y = 0;
+#pragma unroll
+          for (int s = 0; s < 4; s++) y = cmadd<T>(y, K[r * 4 + s], x[s]);
+          acc[j] += (double)y.x * y.x + (double)y.y * y.y;
+        }
+      }
+    }
+  }
+  // block reduction of the nK sums in fixed order: warps, then over warps
+  __shared__ double wsum[kTrajThreads / 32][kMaxKraus];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kMaxKraus; j++) {
+    double v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (l == 0) wsum[w][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxKraus) {
+    double v = 0;
+    for (int i = 0; i < kTrajThreads / 32; i++) v += wsum[i][threadIdx.x];
+    red[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTrajThreads) k_traj(const TrajOp* __restrict__ ops, int nops,
+                                                      const cx<T>* __restrict__ coef, const double* __restrict__ wts,
+                                                      uint64_t seed, int ntraj, int n,
+                                                      const PauliTerm* __restrict__ terms, int nterms,
+                                                      double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<T>* psi = reinterpret_cast<cx<T>*>(smraw);
+  __shared__ double red[kMaxKraus];
+  __shared__ int s_choice;
+  __shared__ double s_scale;
+  __shared__ double s_part[kTrajThreads / 32][2];
+  const uint32_t dim = 1u << n;
+  for (int t = blockIdx.x; t < ntraj; t += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < dim; i += kTrajThreads) {
+      cx<T> z;
+      z.x = (i == 0) ? (T)1 : (T)0;
+      z.y = 0;
+      psi[i] = z;
+    }
+    __syncthreads();
+    bool alive = true;
+    for (int o = 0; o < nops && alive; o++) {
+      const TrajOp op = ops[o];
+      const int dd = op.k == 1 ? 4 : 16;
+      if (op.kind == TJ_UNITARY) {
+        apply_op<T>(psi, n, op, coef + op.coef, (T)1);
+        __syncthreads();
+        continue;
+      }
+      if (op.kind == TJ_KRAUS) kraus_norms<T>(psi, n, op, coef + op.coef, red);
+      if (threadIdx.x == 0) {
+        const double u = draw_uniform(seed, (uint32_t)o, (uint32_t)t);
+        double cum = 0.0;
+        int choice = -1;
+        double pk = 0.0;
+        for (int j = 0; j < op.nK; j++) {
+          const double p = op.kind == TJ_MIXTURE ? wts[op.wofs + j] : red[j];
+          cum += p;
+          if (u < cum) {
+            choice = j;
+            pk = p;
+            break;
+          }
+        }
+        s_choice = choice;
+        s_scale = (op.kind == TJ_KRAUS && choice >= 0) ? 1.0 / sqrt(pk) : 1.0;
+      }
+      __syncthreads();
+      const int choice = s_choice;
+      if (choice < 0) {  // the trajectory left the computational space (trace-decreasing branch)
+        alive = false;
+        break;
+      }
+      apply_op<T>(psi, n, op, coef + op.coef + dd * choice, (T)s_scale);
+      __syncthreads();
+    }
+    // <psi|H|psi> = sum_t c_t i^{ny} sum_x (-1)^{popc(x & zy)} conj(psi[x ^ xm]) psi[x]
+    double total = 0.0;
+    if (alive) {
+      for (int j = 0; j < nterms; j++) {
+        const PauliTerm P = terms[j];
+        double re = 0.0, im = 0.0;
+        for (uint32_t x = threadIdx.x; x < dim; x += kTrajThreads) {
+          const cx<T> a = psi[x ^ P.xm], b = psi[x];
+          const double sg = (__popc(x & P.zy) & 1) ? -1.0 : 1.0;
+          re += sg * ((double)a.x * b.x + (double)a.y * b.y);
+          im += sg * ((double)a.x * b.y - (double)a.y * b.x);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_down_sync(0xffffffffu, re, o);
+          im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          s_part[threadIdx.x >> 5][0] = re;
+          s_part[threadIdx.x >> 5][1] = im;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double sr = 0, si = 0;
+          for (int w = 0; w < kTrajThreads / 32; w++) {
+            sr += s_part[w][0];
+            si += s_part[w][1];
+          }
+          // times i^{ny}: real part of (sr + i si) i^ny
+          const int r = P.ny & 3;
+          const double v = r == 0 ? sr : r == 1 ? -si : r == 2 ? -sr : si;
+          total += P.c * v;
+        }
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) out[t] = alive ? total : 0.0;
+    __syncthreads();
+  }
+}
+
+}  // namespace dev
+
+static int max_traj_qubits(int prec) { return prec == VQD_F32 ? 14 : 13; }
+
+template <class T>
+static cudaError_t traj_run(const std::vector<dev::TrajOp>& ops, const std::vector<cd>& coef,
+                            const std::vector<double>& wts, uint64_t seed, int ntraj, int n,
+                            const std::vector<dev::PauliTerm>& terms, cudaStream_t s, double* host_out) {
+  using namespace dev;
+  std::vector<cx<T>> cf(coef.size());
+  for (size_t i = 0; i < coef.size(); i++) {
+    cf[i].x = (T)coef[i].real();
+    cf[i].y = (T)coef[i].imag();
+  }
+  void *d_ops = nullptr, *d_coef = nullptr, *d_w = nullptr, *d_terms = nullptr, *d_out = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b > 0 ? b : 16);
+  };
+  al(&d_ops, ops.size() * sizeof(TrajOp));
+  al(&d_coef, cf.size() * sizeof(cx<T>));
+  al(&d_w, wts.size() * sizeof(double));
+  al(&d_terms, terms.size() * sizeof(PauliTerm));
+  al(&d_out, (size_t)ntraj * sizeof(double));
+  if (e == cudaSuccess && !ops.empty())
+    e = cudaMemcpyAsync(d_ops, ops.data(), ops.size() * sizeof(TrajOp), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !cf.empty())
+    e = cudaMemcpyAsync(d_coef, cf.data(), cf.size() * sizeof(cx<T>), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !wts.empty())
+    e = cudaMemcpyAsync(d_w, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !terms.empty())
+    e = cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(PauliTerm), cudaMemcpyHostToDevice, s);
+  const size_t smem = ((size_t)1 << n) * sizeof(cx<T>);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_traj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traj<T>, kTrajThreads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    const int grid = std::max(1, std::min(ntraj, per_sm * num_sms()));
+    k_traj<T><<<grid, kTrajThreads, smem, s>>>((const TrajOp*)d_ops, (int)ops.size(), (const cx<T>*)d_coef,
+                                               (const double*)d_w, seed, ntraj, n, (const PauliTerm*)d_terms,
+                                               (int)terms.size(), (double*)d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d_out, (size_t)ntraj * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (void* p : {d_ops, d_coef, d_w, d_terms, d_out})
+    if (p) cudaFree(p);
+  return e;
+}
+
+}  // namespace vqd
+
+extern "C" int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* ops, unsigned flags, int ntraj,
+                               uint64_t seed, int nterms, const uint8_t* paulis, const double* coeffs, void* stream,
+                               double* out, double* mean, double* stderr_out) {
+  using namespace vqd;
+  try {
+    if (prec != VQD_F32 && prec != VQD_F64) throw Error(VQD_EINVAL, "bad precision");
+    if (n < 1 || n > max_traj_qubits(prec))
+      throw Error(VQD_ENOTSUP, "trajectories hold the statevector in shared memory: n <= " +
+                                   std::to_string(max_traj_qubits(prec)) + " for this precision");
+    if (ntraj < 1 || nops < 0 || (nops > 0 && !ops) || nterms < 1 || !paulis || !coeffs || !out)
+      throw Error(VQD_EINVAL, "bad argument");
+    std::vector<dev::TrajOp> top;
+    std::vector<cd> coef;
+    std::vector<double> wts;
+    for (int i = 0; i < nops; i++) {
+      const int ar = native_arity(ops[i].code);
+      if (ar < 1 || ops[i].nq != ar) throw Error(VQD_EINVAL, "bad native op at index " + std::to_string(i));
+      for (int j = 0; j < ar; j++)
+        if (ops[i].q[j] < 0 || ops[i].q[j] >= n || (j == 1 && ops[i].q[1] == ops[i].q[0]))
+          throw Error(VQD_EINVAL, "bad target qubit at index " + std::to_string(i));
+      KrausForm f = compile_kraus_form(ops[i], flags);
+      dev::TrajOp t;
+      std::memset(&t, 0, sizeof(t));
+      t.k = f.k;
+      t.q[0] = f.q[0];
+      t.q[1] = f.q[1];
+      t.nK = (int)f.K.size();
+      t.coef = (int)coef.size();
+      t.wofs = -1;
+      t.kind = f.unitary ? dev::TJ_UNITARY : f.mixture ? dev::TJ_MIXTURE : dev::TJ_KRAUS;
+      if (t.kind == dev::TJ_KRAUS && t.nK > dev::kMaxKraus)
+        throw Error(VQD_ENOTSUP, "more than 16 state-dependent Kraus operators");
+      for (size_t j = 0; j < f.K.size(); j++) {
+        const double inv = t.kind == dev::TJ_MIXTURE ? 1.0 / std::sqrt(f.w[j]) : 1.0;
+        for (const cd& x : f.K[j]) coef.push_back(x * inv);
+      }
+      if (t.kind == dev::TJ_MIXTURE) {
+        t.wofs = (int)wts.size();
+        wts.insert(wts.end(), f.w.begin(), f.w.end());
+      }
+      top.push_back(t);
+    }
+    std::vector<dev::PauliTerm> terms(nterms);
+    for (int t = 0; t < nterms; t++) {
+      uint32_t x = 0, z = 0;
+      int y = 0;
+      for (int q = 0; q < n; q++) {
+        const uint8_t s = paulis[(size_t)t * n + q];
+        if (s > 3) throw Error(VQD_EINVAL, "Pauli code must be 0..3");
+        if (s == 1 || s == 2) x |= 1u << q;
+        if (s == 2 || s == 3) z |= 1u << q;
+        if (s == 2) y++;
+      }
+      terms[t] = {x, z, y, 0, coeffs[t]};
+    }
+    cudaError_t e = prec == VQD_F32
+                        ? traj_run<float>(top, coef, wts, seed, ntraj, n, terms, (cudaStream_t)stream, out)
+                        : traj_run<double>(top, coef, wts, seed, ntraj, n, terms, (cudaStream_t)stream, out);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(e == cudaErrorMemoryAllocation ? VQD_ENOMEM : VQD_EDEVICE, cudaGetErrorString(e));
+    }
+    double s1 = 0, s2 = 0;
+    for (int t = 0; t < ntraj; t++) {
+      s1 += out[t];
+      s2 += out[t] * out[t];
+    }
+    const double m = s1 / ntraj;
+    if (mean) *mean = m;
+    if (stderr_out) *stderr_out = ntraj > 1 ? std::sqrt(std::max(0.0, (s2 / ntraj - m * m) / (ntraj - 1))) : 0.0;
+    return VQD_OK;
+  } catch (const Error& e) {
+    return report_static_error(e.code, e.what());
+  } catch (const std::exception& e) {
+    return report_static_error(VQD_EINVAL, e.what());
+  }
+}

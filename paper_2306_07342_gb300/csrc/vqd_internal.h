@@ -37,6 +37,20 @@ void check_unitary(int k, const cd* U);                           // throws VQD_
 void check_cptn(int k, int nK, const cd* K);                      // throws VQD_ENOTCP
 int native_arity(int code);
 
+// Kraus form of one native op for the trajectory path: a unitary (K = {U}) or the channel's Kraus
+// operators in a fixed order.  For a composite process (first step A, then step B) the operators
+// are B_j A_i with the first step's index i outer.  `mixture` marks channels whose operators are
+// all sqrt(w_k) times a unitary: their branch probabilities w_k do not depend on the state.
+struct KrausForm {
+  bool unitary = true;
+  int k = 1;
+  int q[2] = {0, 0};
+  std::vector<std::vector<cd>> K;
+  bool mixture = false;
+  std::vector<double> w;
+};
+KrausForm compile_kraus_form(const vqd_native_op& op, unsigned flags);
+
 // ---- kernel classes of the plain path
 enum KernelKind { KK_ELEM = 0, KK_SUP1 = 1, KK_UNI2 = 2, KK_SUP2 = 3, KK_COUNT_PLAIN = 4 };
 

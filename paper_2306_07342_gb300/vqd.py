@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "vqd_prob_static": (I, [P, I, I, I, P, P, P]),
             "vqd_plan_info": (I, [I, I, I, P, I, I, I, U, P]),
             "vqd_set_tile_shape": (I, [P, I, I]),
+            "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -268,6 +269,18 @@ def vqd_expect(ctx, inst: int, paulis, coeffs) -> float:
     out = ctypes.c_double()
     _check(lib().vqd_expect(ctx, inst, len(c), _ptr(p), _ptr(c), ctypes.byref(out)), ctx)
     return out.value
+
+
+def vqd_traj_expect(n: int, prec: int, ops, ntraj: int, seed: int, paulis, coeffs, flags: int = 0, stream: int = 0):
+    """Monte-Carlo trajectory estimate of Re sum_t c_t tr(P_t rho): (per-trajectory values, mean, standard error)."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    p = np.ascontiguousarray(np.asarray(paulis, dtype=np.uint8))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    out = np.zeros(ntraj, dtype=np.float64)
+    m, se = ctypes.c_double(), ctypes.c_double()
+    _check(lib().vqd_traj_expect(n, prec, len(a), _ptr(a), flags, ntraj, seed, len(c), _ptr(p), _ptr(c),
+                                 ctypes.c_void_p(stream), _ptr(out), ctypes.byref(m), ctypes.byref(se)))
+    return out, m.value, se.value
 
 
 def vqd_trace(ctx, inst: int = 0) -> complex:

@@ -1,0 +1,115 @@
+"""Monte-Carlo trajectories (Sec. 2): oracle pins on CPU, GPU parity (one by one and in the mean)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import evolve, measure
+from oracle import trajectories as otj
+from workloads import config1_chain6
+from workloads.circuits import OP_NAMES, NativeOp, Program, random_program
+
+from ._lib import get_lib
+
+UNITARIES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
+             "crz_xtalk", "exchange"]
+
+
+def hamiltonian(n, rng, nterms=6):
+    codes = rng.integers(0, 4, size=(nterms, n)).astype(np.uint8)
+    codes[0] = 0
+    codes[0][0] = 3                       # always include Z_0
+    return codes, rng.normal(size=nterms)
+
+
+# ---------------------------------------------------------------- CPU pins of the oracle
+def test_philox_uniform_draws_are_uniform_and_distinct():
+    u = np.array([otj.uniform(12345, op, t) for op in range(40) for t in range(250)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert len(np.unique(u)) == u.size
+    hist, _ = np.histogram(u, bins=20, range=(0, 1))
+    chi2 = float(((hist - u.size / 20) ** 2 / (u.size / 20)).sum())
+    assert chi2 < 50.0                    # 19 degrees of freedom: p ~ 1e-4
+    assert abs(u.mean() - 0.5) < 0.01
+    assert otj.uniform(1, 2, 3) != otj.uniform(1, 3, 2) and otj.uniform(1, 2, 3) != otj.uniform(2, 2, 3)
+
+
+def test_oracle_trajectory_mean_converges_to_density_matrix():
+    """The unravelling's mean estimates Re tr(H rho) (Sec. 2), including a trace-decreasing channel."""
+    rng = np.random.default_rng(5)
+    prog = random_program(17, 3, 30)
+    prog.ops.append(NativeOp("leak_init", (1,), (0.2,)))
+    codes, coeffs = hamiltonian(3, rng)
+    exact = measure.expect(evolve.run_program(prog), codes, coeffs)
+    vals = otj.trajectory_values(prog, 3000, 99, codes, coeffs)
+    se = vals.std(ddof=1) / math.sqrt(vals.size)
+    assert abs(vals.mean() - exact) < 5 * se + 1e-12
+
+
+def test_oracle_unitary_trajectories_are_exact():
+    rng = np.random.default_rng(6)
+    prog = random_program(18, 4, 40, names=UNITARIES)
+    codes, coeffs = hamiltonian(4, rng)
+    exact = measure.expect(evolve.run_program(prog), codes, coeffs)
+    vals = otj.trajectory_values(prog, 3, 1, codes, coeffs)
+    assert np.abs(vals - exact).max() < 1e-13
+
+
+# ---------------------------------------------------------------- GPU parity
+@pytest.fixture(scope="module")
+def vqd():
+    return get_lib()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_traj_unitary_program_is_exact_every_trajectory(vqd, p, tol):
+    rng = np.random.default_rng(7)
+    prog = random_program(19, 6, 80, names=UNITARIES)
+    codes, coeffs = hamiltonian(6, rng)
+    exact = measure.expect(evolve.run_program(prog), codes, coeffs)
+    vals, mean, se = vqd.vqd_traj_expect(6, vqd.VQD_F64 if p == "f64" else vqd.VQD_F32, prog.ops, 8, 3, codes, coeffs)
+    assert np.abs(vals - exact).max() < tol
+    assert se < tol
+
+
+@pytest.mark.gpu
+def test_traj_match_oracle_one_by_one_fp64(vqd):
+    """Same draws on both sides: every FP64 trajectory equals the oracle's (every native op kind, incl. leakage)."""
+    rng = np.random.default_rng(8)
+    prog = random_program(21, 4, 60)
+    codes, coeffs = hamiltonian(4, rng)
+    want = otj.trajectory_values(prog, 48, 2024, codes, coeffs)
+    got, mean, se = vqd.vqd_traj_expect(4, vqd.VQD_F64, prog.ops, 48, 2024, codes, coeffs)
+    assert np.abs(got - want).max() < 1e-10
+    assert abs(mean - want.mean()) < 1e-10
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p", ["f64", "f32"])
+def test_traj_mean_converges_to_density_matrix(vqd, p):
+    """The six-qubit chain (682 native ops): 4096 trajectories against the density-matrix oracle."""
+    rng = np.random.default_rng(9)
+    prog = config1_chain6()
+    codes, coeffs = hamiltonian(6, rng, nterms=8)
+    exact = measure.expect(evolve.run_program(prog), codes, coeffs)
+    vals, mean, se = vqd.vqd_traj_expect(6, vqd.VQD_F64 if p == "f64" else vqd.VQD_F32, prog.ops, 4096, 77,
+                                         codes, coeffs)
+    assert se > 0
+    assert abs(mean - exact) < 5 * se + 1e-6
+
+
+@pytest.mark.gpu
+def test_traj_largest_statevector_and_errors(vqd):
+    n = 14
+    prog = Program(n, [NativeOp("h", (q,)) for q in range(n)] + [NativeOp("depol1", (q,), (0.1,)) for q in range(n)])
+    codes = np.zeros((1, n), np.uint8)
+    codes[0, 3] = 1                                     # <X_3> = 1 - 4p/3 after H and depol1(p)
+    vals, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F32, prog.ops, 2048, 5, codes, [1.0])
+    assert abs(mean - (1 - 4 * 0.1 / 3)) < 5 * se + 1e-6
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_traj_expect(15, vqd.VQD_F32, [], 4, 1, np.zeros((1, 15), np.uint8), [1.0])
+    assert e.value.code == vqd.VQD_ENOTSUP
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_traj_expect(14, vqd.VQD_F64, [], 4, 1, np.zeros((1, 14), np.uint8), [1.0])
+    assert e.value.code == vqd.VQD_ENOTSUP
