@@ -210,6 +210,18 @@ int vqd_set_tile_shape(vqd_t ctx, int tile_bits, int passenger_bits);
 int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_qubits, int tile_bits,
                   int passenger_bits, unsigned flags, int64_t* info);
 
+/* Automatic scheduling (Sec. 2: idle qubits experience passive noise while waiting for the slowest
+ * operation of their automatically scheduled parallel batch).  Input: `nin` native ops in program
+ * order, where ops with dur[i] >= 0 are gates of that duration (us) and ops with dur[i] < 0 are the
+ * noise that follows the previous gate on the same qubits (kept right after it).  Each gate goes to the
+ * earliest layer after every earlier gate that shares a qubit; a layer lasts as long as its slowest
+ * gate.  Output, layer by layer: the layer's gates, each followed by its noise ops, then for every
+ * qubit j a passive-noise op of code idle_code (VQD_OP_IDLE or VQD_OP_IDLE_DEPOL) with parameters
+ * (dt, t1[j], t2[j]), dt = layer duration minus the time qubit j was busy in the layer (skipped when
+ * dt = 0).  out has room for cap ops; *nout receives the count (VQD_EINVAL if cap is too small). */
+int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int idle_code, const double* t1,
+                 const double* t2, int cap, vqd_native_op* out, int* nout);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);
@@ -226,6 +238,14 @@ int vqd_prob(vqd_t ctx, int inst, int m, const int* qubits, double* out);
 /* *out = Re sum_t coeffs[t] tr(P_t rho); paulis is nterms x n bytes, paulis[t*n + q] in
  * {0=I, 1=X, 2=Y, 3=Z} is the factor on qubit q. */
 int vqd_expect(vqd_t ctx, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out);
+
+/* Projective Z-basis measurement of qubit q with collapse (the readout of Sec. 3.6 / Sec. 6):
+ * p_m = tr(P_m rho) / tr(rho) for P_m = |m><m|_q.  With force = -1 the outcome is 0 when
+ * u tr(rho) < tr(P_0 rho), else 1 (u in [0,1) is the caller's uniform draw); force = 0 or 1
+ * post-selects that outcome.  The state becomes P_m rho P_m / tr(P_m rho).  Returns the outcome and
+ * its probability (either pointer may be NULL).  Synchronous.  EINVAL for a zero-probability
+ * forced outcome. */
+int vqd_measure(vqd_t ctx, int inst, int q, double u, int force, int* outcome, double* prob);
 
 /* tr rho (not renormalised: trace-decreasing leakage channels leave it below 1). */
 int vqd_trace(vqd_t ctx, int inst, double* re_out, double* im_out);

@@ -92,3 +92,18 @@ def uhlmann_fidelity(a: np.ndarray, b: np.ndarray) -> float:
     m = sa @ b @ sa
     ev = np.linalg.eigvalsh(0.5 * (m + m.conj().T))
     return float(np.sum(np.sqrt(np.clip(ev, 0, None))) ** 2)
+
+
+def measure_collapse(rho: np.ndarray, q: int, u: float = 0.0, force: int = -1):
+    """Projective Z measurement of qubit q (selective): outcome m with probability tr(P_m rho)/tr(rho),
+    drawn as m = 0 when u tr(rho) < tr(P_0 rho) (or forced), and the collapsed state
+    P_m rho P_m / tr(P_m rho).  Returns (m, probability, new rho)."""
+    n = int(round(np.log2(rho.shape[0])))
+    p = probs(rho, [q])
+    tot = p[0] + p[1]
+    m = force if force >= 0 else (0 if u * tot < p[0] else 1)
+    proj = np.zeros((2, 2), dtype=complex)
+    proj[m, m] = 1.0
+    from .evolve import apply_kraus
+    out = apply_kraus(rho, (q,), [proj]) / p[m]
+    return m, p[m] / tot, out

@@ -548,6 +548,70 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
   API_END(nullptr)
 }
 
+int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int idle_code, const double* t1,
+                 const double* t2, int cap, vqd_native_op* out, int* nout) {
+  API_BEGIN
+  if (n < 1 || n > 32 || nin < 0 || (nin > 0 && (!in || !dur)) || !t1 || !t2 || !out || !nout || cap < 0)
+    throw Error(VQD_EINVAL, "bad argument");
+  if (idle_code != VQD_OP_IDLE && idle_code != VQD_OP_IDLE_DEPOL) throw Error(VQD_EINVAL, "idle_code must be an idle op");
+  // gates with their trailing noise ops, each assigned to a layer
+  struct G {
+    int first, count;  // gate op and its noise ops: in[first .. first+count)
+    int layer;
+  };
+  std::vector<G> gates;
+  std::vector<int> ready(n, 0);  // first layer qubit j is free in
+  for (int i = 0; i < nin; i++) {
+    const int ar = native_arity(in[i].code);
+    if (ar < 1 || in[i].nq != ar) throw Error(VQD_EINVAL, "bad native op at index " + std::to_string(i));
+    for (int j = 0; j < ar; j++)
+      if (in[i].q[j] < 0 || in[i].q[j] >= n) throw Error(VQD_EINVAL, "qubit out of range at index " + std::to_string(i));
+    if (dur[i] < 0) {
+      if (gates.empty() || gates.back().first + gates.back().count != i)
+        throw Error(VQD_EINVAL, "noise op at index " + std::to_string(i) + " does not follow a gate");
+      gates.back().count++;
+      continue;
+    }
+    int layer = 0;
+    for (int j = 0; j < ar; j++) layer = std::max(layer, ready[in[i].q[j]]);
+    for (int j = 0; j < ar; j++) ready[in[i].q[j]] = layer + 1;
+    gates.push_back({i, 1, layer});
+  }
+  int nl = 0;
+  for (const G& g : gates) nl = std::max(nl, g.layer + 1);
+  int cnt = 0;
+  auto emit = [&](const vqd_native_op& o) {
+    if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+    out[cnt++] = o;
+  };
+  for (int l = 0; l < nl; l++) {
+    double len = 0;
+    std::vector<double> busy(n, 0.0);
+    for (const G& g : gates) {
+      if (g.layer != l) continue;
+      const double d = dur[g.first];
+      len = std::max(len, d);
+      for (int j = 0; j < in[g.first].nq; j++) busy[in[g.first].q[j]] = d;
+      for (int k = 0; k < g.count; k++) emit(in[g.first + k]);
+    }
+    for (int j = 0; j < n; j++) {
+      const double dt = len - busy[j];
+      if (dt <= 0) continue;
+      vqd_native_op o;
+      std::memset(&o, 0, sizeof(o));
+      o.code = idle_code;
+      o.nq = 1;
+      o.q[0] = j;
+      o.par[0] = dt;
+      o.par[1] = t1[j];
+      o.par[2] = t2[j];
+      emit(o);
+    }
+  }
+  *nout = cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");
@@ -575,6 +639,36 @@ int vqd_prob(vqd_t c, int inst, int m, const int* qubits, double* out) {
         [&] { return launch_prob(c->prec, c->ptr(inst), n, m, qubits, c->d_scratch, c->d_out, c->stream); });
   fetch(c, (size_t)1 << m);
   std::memcpy(out, c->h_out, sizeof(double) << m);
+  API_END(c)
+}
+
+int vqd_measure(vqd_t c, int inst, int q, double u, int force, int* outcome, double* prob) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  const int n = c->n[inst];
+  if (q < 0 || q >= n) throw Error(VQD_EINVAL, "measured qubit out of range");
+  if (force < -1 || force > 1) throw Error(VQD_EINVAL, "force must be -1 (draw), 0 or 1");
+  if (force == -1 && !(u >= 0 && u < 1)) throw Error(VQD_EINVAL, "u must be in [0, 1)");
+  timed(c, SC_REDUCE, std::ldexp(1.0, n) * c->esize, 0, 2,
+        [&] { return launch_prob(c->prec, c->ptr(inst), n, 1, &q, c->d_scratch, c->d_out, c->stream); });
+  fetch(c, 2);
+  const double p0 = c->h_out[0], p1 = c->h_out[1], tot = p0 + p1;
+  if (!(tot > 0)) throw Error(VQD_EINVAL, "state has zero trace");
+  const int m = force >= 0 ? force : (u * tot < p0 ? 0 : 1);
+  const double pm = m == 0 ? p0 : p1;
+  if (!(pm > 0)) throw Error(VQD_EINVAL, "forced outcome has probability zero");
+  // rho <- P_m rho P_m / tr(P_m rho): amplitudes whose row and column bit q both equal m are scaled,
+  // all others vanish (a real diagonal superoperator on qubit q, member index r | c << 1)
+  Pass p;
+  p.kind = KK_ELEM;
+  p.k = 1;
+  p.q[0] = q;
+  p.coef.assign(4, 0.0);
+  p.coef[m | (m << 1)] = 1.0 / pm;
+  timed(c, SC_ELEM, 2.0 * c->bytes(inst), 0, 1, [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
+  if (outcome) *outcome = m;
+  if (prob) *prob = pm / tot;
   API_END(c)
 }
 

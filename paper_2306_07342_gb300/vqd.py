@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
             "vqd_prob_static": (I, [P, I, I, I, P, P, P]),
             "vqd_plan_info": (I, [I, I, I, P, I, I, I, U, P]),
             "vqd_set_tile_shape": (I, [P, I, I]),
+            "vqd_measure": (I, [P, I, I, D, I, P, P]),
+            "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -250,6 +252,21 @@ def vqd_plan_info(n: int, prec: int, ops, fuse_qubits: int = 0, flags: int = 0, 
     return dict(zip(keys, (int(x) for x in info)))
 
 
+def vqd_schedule(n: int, ops, durations, t1, t2, idle: str = "idle") -> np.ndarray:
+    """Schedule gates (duration >= 0) and their trailing noise ops (duration < 0) into parallel layers with
+    passive idle noise (host only).  Returns the scheduled native-op array."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    d = np.ascontiguousarray(np.asarray(durations, dtype=np.float64))
+    t1a = np.ascontiguousarray(np.asarray(t1, dtype=np.float64))
+    t2a = np.ascontiguousarray(np.asarray(t2, dtype=np.float64))
+    cap = len(a) + n * max(1, len(a))
+    out = np.zeros(cap, dtype=NATIVE_OP_DTYPE)
+    cnt = ctypes.c_int()
+    _check(lib().vqd_schedule(n, len(a), _ptr(a), _ptr(d), OP_CODE[idle], _ptr(t1a), _ptr(t2a), cap, _ptr(out),
+                              ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
 def vqd_stderr_params(nq: int, fbar: float, x: float):
     p, q = ctypes.c_double(), ctypes.c_double()
     _check(lib().vqd_stderr_params(nq, fbar, x, ctypes.byref(p), ctypes.byref(q)))
@@ -281,6 +298,13 @@ def vqd_traj_expect(n: int, prec: int, ops, ntraj: int, seed: int, paulis, coeff
     _check(lib().vqd_traj_expect(n, prec, len(a), _ptr(a), flags, ntraj, seed, len(c), _ptr(p), _ptr(c),
                                  ctypes.c_void_p(stream), _ptr(out), ctypes.byref(m), ctypes.byref(se)))
     return out, m.value, se.value
+
+
+def vqd_measure(ctx, inst: int, q: int, u: float = 0.0, force: int = -1):
+    """Projective Z measurement of qubit q with collapse: (outcome, probability)."""
+    m, pr = ctypes.c_int(), ctypes.c_double()
+    _check(lib().vqd_measure(ctx, inst, q, u, force, ctypes.byref(m), ctypes.byref(pr)), ctx)
+    return m.value, pr.value
 
 
 def vqd_trace(ctx, inst: int = 0) -> complex:

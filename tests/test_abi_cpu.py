@@ -109,3 +109,52 @@ def test_state_bytes(vqd):
     assert vqd.vqd_state_bytes(14, vqd.VQD_F32) == 8 * 4 ** 14
     assert vqd.vqd_state_bytes(16, vqd.VQD_F64) == 16 * 4 ** 16
     assert vqd.vqd_state_bytes(17, vqd.VQD_F64) == 0
+
+
+def test_schedule_worked_example_and_oracle(vqd):
+    """Two layers by hand: rx(q0) 0.1 us and cz(q1,q2) 0.3 us run together (q0 waits 0.2, q3 idles 0.3);
+    then cz(q0,q1) 0.3 us (q2, q3 idle 0.3).  Gate noise stays right after its gate."""
+    from oracle.schedule import schedule
+    t1, t2 = [50.0, 60.0, 70.0, 80.0], [30.0, 40.0, 50.0, 60.0]
+    ops = [NativeOp("rx", (0,), (0.5,)), NativeOp("depol1", (0,), (1e-3,)),
+           NativeOp("cz", (1, 2)), NativeOp("depol2", (1, 2), (1e-2,)),
+           NativeOp("cz", (0, 1))]
+    dur = [0.1, -1, 0.3, -1, 0.3]
+    want = [("rx", (0,)), ("depol1", (0,)), ("cz", (1, 2)), ("depol2", (1, 2)),
+            ("idle", (0,), 0.2), ("idle", (3,), 0.3),
+            ("cz", (0, 1)), ("idle", (2,), 0.3), ("idle", (3,), 0.3)]
+    orc = schedule(4, ops, dur, t1, t2)
+    got = vqd.vqd_schedule(4, ops, dur, t1, t2)
+    assert len(orc) == len(want) == len(got)
+    for w, o, g in zip(want, orc, got):
+        assert o.name == w[0] and o.qubits == w[1]
+        assert vqd.OP_CODES[g["code"]] == w[0] and tuple(g["q"][: g["nq"]]) == w[1]
+        if len(w) == 3:
+            assert abs(o.params[0] - w[2]) < 1e-15 and abs(g["par"][0] - w[2]) < 1e-15
+            assert g["par"][1] == t1[w[1][0]] and g["par"][2] == t2[w[1][0]]
+
+
+def test_schedule_random_programs_match_oracle(vqd):
+    from oracle.schedule import schedule
+    r = _rng(77)
+    n = 5
+    prog = random_program(78, n, 60, names=["rx", "ry", "cz", "zx", "xx", "depol1", "depol2", "amp"])
+    dur = [(-1.0 if o.name in ("depol1", "depol2", "amp") else float(r.uniform(0.05, 0.5))) for o in prog.ops]
+    # a noise op must follow a gate on the same qubits: make every noise op act on its gate's qubits
+    ops, d2 = [], []
+    for o, d in zip(prog.ops, dur):
+        if d < 0:
+            if not ops or d2[-1] < 0:
+                continue
+            g = ops[-1]
+            name = "depol1" if len(g.qubits) == 1 else "depol2"
+            o = NativeOp(name, g.qubits, (1e-3,))
+        ops.append(o)
+        d2.append(d)
+    t1, t2 = list(r.uniform(20, 100, n)), list(r.uniform(10, 50, n))
+    orc = schedule(n, ops, d2, t1, t2, idle="idle_depol")
+    got = vqd.vqd_schedule(n, ops, d2, t1, t2, idle="idle_depol")
+    assert len(orc) == len(got)
+    for o, g in zip(orc, got):
+        assert vqd.OP_CODES[g["code"]] == o.name and tuple(g["q"][: g["nq"]]) == o.qubits
+        assert np.allclose(g["par"][: len(o.params)], o.params, rtol=0, atol=1e-15)

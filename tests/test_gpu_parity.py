@@ -439,3 +439,24 @@ def test_batch_graph_capture_and_replay(vqd):
                 assert np.abs(gpu_state(vqd, ctx, i) - want).max() < tol_f32(len(prog.ops)), (round_, i)
     finally:
         vqd.vqd_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", PRECS)
+def test_measure_collapse_matches_oracle(vqd, p):
+    from oracle.measure import measure_collapse
+    rng = np.random.default_rng(41)
+    n = 5
+    rho = rand_state(n, rng)
+    ctx = make_ctx(vqd, n, p, rho)
+    try:
+        rho = gpu_state(vqd, ctx)                    # the stored state (FP32-rounded in f32)
+        for q, u, force in ((2, 0.31, -1), (0, 0.93, -1), (4, 0.0, 1), (1, 0.5, 0)):
+            m, pm = vqd.vqd_measure(ctx, 0, q, u, force)
+            mw, pw, rho = measure_collapse(rho, q, u, force)
+            assert m == mw and abs(pm - pw) < (1e-13 if p == "f64" else 1e-6)
+            assert np.abs(gpu_state(vqd, ctx) - rho).max() < (1e-12 if p == "f64" else 1e-5)
+            assert abs(vqd.vqd_trace(ctx, 0) - 1) < (1e-13 if p == "f64" else 1e-5)
+        with pytest.raises(vqd.VQDError):
+            vqd.vqd_measure(ctx, 0, 4, 0.0, 0)       # qubit 4 was post-selected to 1: outcome 0 is impossible
+    finally:
+        vqd.vqd_destroy(ctx)

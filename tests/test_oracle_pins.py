@@ -412,3 +412,22 @@ def test_trace_distance_and_fidelity_helpers():
     rho = evolve.apply_kraus(np.outer(psi, psi.conj()), (0, 1), oc.depol2(0.2))
     # square roots of near-zero eigenvalues of a rank-deficient state limit this helper to ~1e-8
     assert abs(measure.uhlmann_fidelity(rho, np.outer(psi, psi.conj())) - (1 - 0.8 * 0.2)) < 1e-7
+
+
+def test_measure_collapse_bell_and_product_states():
+    """Measuring one qubit of |Phi+> gives each outcome with probability 1/2 and leaves |mm><mm|; on a
+    product state the other qubit's reduced state is untouched."""
+    psi = bell()
+    rho = np.outer(psi, psi.conj())
+    for u, m_want in ((0.2, 0), (0.7, 1)):
+        m, pm, out = measure.measure_collapse(rho, 0, u)
+        assert m == m_want and abs(pm - 0.5) < 1e-15
+        want = np.zeros((4, 4))
+        want[3 * m, 3 * m] = 1.0
+        assert np.abs(out - want).max() < 1e-15
+    a = np.array([[0.7, 0.2 + 0.1j], [0.2 - 0.1j, 0.3]])
+    b = np.array([[0.4, -0.3j], [0.3j, 0.6]])
+    rho = np.kron(b, a)                               # qubit 0 in a, qubit 1 in b
+    m, pm, out = measure.measure_collapse(rho, 1, force=1)
+    assert abs(pm - 0.6) < 1e-15
+    assert np.abs(out - np.kron(np.diag([0, 1]), a)).max() < 1e-15
