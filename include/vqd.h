@@ -101,7 +101,16 @@ typedef enum {
   VQD_OP_AMPDEPH2 = 29, /* q0,q1; dt, T1, T2: the T1/T2 decay of both qubits as one 2-qubit channel */
   VQD_OP_LEAK_INIT = 30,/* q0; gamma: CPTN L = diag(sqrt(1-gamma), 1), Sec. 6                 */
   VQD_OP_LEAK_CZ = 31,  /* q0,q1; alpha, beta: CPTN K of Eq. (czleak)                          */
-  VQD_OP_COUNT = 32
+  /* device-family crosstalk unitaries */
+  VQD_OP_OFFRES = 32,   /* q0; Omega, Delta, t: off-resonant Rabi drive on a passive qubit, Sec. 3.3
+                           Eq. (off_resonant) as printed: exp(i Omega_R t Z/2) exp(-i t (Omega X + Delta Z)/2),
+                           Omega_R = sqrt(Omega^2 + Delta^2); near the identity for Delta >> Omega;
+                           the identity when Omega = Delta = 0                                          */
+  VQD_OP_ZZ_STATIC = 33,/* q0 = control, q1 = target; J dt, Delta_ct dt, alpha_t dt, alpha_c dt:
+                           exp(-i beta Z Z), beta = J^2 (1/(Delta-alpha_t) - 1/(Delta+alpha_c)), Sec. 8;
+                           the parameters are frequencies times the idle duration, so beta is the
+                           accumulated phase; a zero denominator is VQD_EINVAL                       */
+  VQD_OP_COUNT = 34
 } vqd_op_code;
 
 typedef struct {
@@ -238,6 +247,12 @@ int vqd_prob(vqd_t ctx, int inst, int m, const int* qubits, double* out);
 /* *out = Re sum_t coeffs[t] tr(P_t rho); paulis is nterms x n bytes, paulis[t*n + q] in
  * {0=I, 1=X, 2=Y, 3=Z} is the factor on qubit q. */
 int vqd_expect(vqd_t ctx, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out);
+
+/* Reductions of every instance of a batch context in one batched launch (one CTA per chunk of 2^20
+ * amplitudes of an instance), copied back once.  probs (host, sum_i 2^{n_i} doubles, instances in order)
+ * receives each instance's full Z-basis distribution Re rho[x][x]; trace_re and purity (host, count
+ * doubles) receive Re tr rho and sum |rho_ij|^2 per instance.  Any output may be NULL.  Synchronous. */
+int vqd_batch_reduce(vqd_t ctx, double* probs, double* trace_re, double* purity);
 
 /* Projective Z-basis measurement of qubit q with collapse (the readout of Sec. 3.6 / Sec. 6):
  * p_m = tr(P_m rho) / tr(rho) for P_m = |m><m|_q.  With force = -1 the outcome is 0 when

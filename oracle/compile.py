@@ -115,6 +115,43 @@ def zz_idle(dt, xi):
     return zzphase(math.pi * xi * dt / 2)
 
 
+def off_resonant(omega, delta, t):
+    """Off-resonant Rabi drive on a passive qubit, Sec. 3.3 Eq. (off_resonant), as printed.
+
+    With Omega_R = sqrt(Omega^2 + Delta^2) and h = Omega_R t / 2: the top row is
+    ((cos h - i Delta/Omega_R sin h) e^{ih}, -i Omega/Omega_R sin h e^{ih}) and the bottom row
+    (-i Omega/Omega_R sin h e^{-ih}, (cos h + i Delta/Omega_R sin h) e^{-ih}).  It tends to the identity
+    for Delta >> Omega; for Delta < 0 the printed frame phase leaves a Z rotation by Omega_R t.
+    Omega_R = 0 is the limit of the formula, the identity.
+    """
+    om_r = math.sqrt(omega * omega + delta * delta)
+    if om_r == 0.0:
+        return np.eye(2, dtype=complex)
+    h = om_r * t / 2
+    c, s = math.cos(h), math.sin(h)
+    ph = np.exp(1j * h)
+    return np.array([[(c - 1j * delta / om_r * s) * ph, -1j * omega / om_r * s * ph],
+                     [-1j * omega / om_r * s / ph, (c + 1j * delta / om_r * s) / ph]])
+
+
+def static_zz_beta(j, delta_ct, alpha_t, alpha_c):
+    """Static ZZ strength of two capacitively coupled transmons, Sec. 8:
+    beta = J^2 (1/(Delta_ct - alpha_t) - 1/(Delta_ct + alpha_c))."""
+    d1, d2 = delta_ct - alpha_t, delta_ct + alpha_c
+    if d1 == 0.0 or d2 == 0.0:
+        raise ValueError("zz_static: Delta_ct - alpha_t or Delta_ct + alpha_c is zero")
+    return j * j * (1.0 / d1 - 1.0 / d2)
+
+
+def zz_static(j, delta_ct, alpha_t, alpha_c):
+    """Static ZZ crosstalk exp(-i beta Z_c Z_t) of Sec. 8 with beta from static_zz_beta.
+
+    Reading: the four parameters are the frequencies times the idle duration (J dt, Delta dt,
+    alpha dt), so beta, homogeneous of degree one in them, is the accumulated phase beta dt.
+    """
+    return zzphase(static_zz_beta(j, delta_ct, alpha_t, alpha_c))
+
+
 def crz_xtalk(alpha):
     """Conditional-Rz crosstalk |0><0|_p (x) I_q + |1><1|_p (x) Rz(alpha)_q, Eq. (weak_dephasing); p = first."""
     p0 = np.diag([1, 0]).astype(complex)
@@ -271,7 +308,7 @@ def compile_op(name: str, qubits: Sequence[int], params: Sequence[float], t2_is_
         "u": lambda: raman_u(*P), "r": lambda: ion_r(*P), "cz": cz, "cph": lambda: cph(*P),
         "czphi": lambda: czphi(*P), "zx": lambda: zx(*P), "zz": lambda: zz(*P), "xx": lambda: xx(*P),
         "zzphase": lambda: zzphase(*P), "zz_idle": lambda: zz_idle(*P), "crz_xtalk": lambda: crz_xtalk(*P),
-        "exchange": lambda: exchange(*P),
+        "exchange": lambda: exchange(*P), "offres": lambda: off_resonant(*P), "zz_static": lambda: zz_static(*P),
     }
     if name in unitary:
         return [("U", q, unitary[name]())]

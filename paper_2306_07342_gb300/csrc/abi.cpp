@@ -642,6 +642,51 @@ int vqd_prob(vqd_t c, int inst, int m, const int* qubits, double* out) {
   API_END(c)
 }
 
+int vqd_batch_reduce(vqd_t c, double* probs, double* trace_re, double* purity) {
+  API_BEGIN
+  need_ctx(c);
+  std::vector<unsigned char> items;
+  std::vector<int> item_inst;
+  batch_reduce_items(c->n, c->off, c->esize, items, item_inst);
+  const size_t nitems = item_inst.size();
+  size_t nprob = 0;
+  for (int n : c->n) nprob += (size_t)1 << n;
+  void *d_items = nullptr, *d_probs = nullptr, *d_part = nullptr;
+  struct Free {
+    void** p[3];
+    ~Free() {
+      for (void** q : p)
+        if (*q) cudaFree(*q);
+    }
+  } guard{{&d_items, &d_probs, &d_part}};
+  cuda_check(cudaMalloc(&d_items, items.size()), "batch reduce items");
+  cuda_check(cudaMalloc(&d_probs, sizeof(double) * nprob), "batch reduce probabilities");
+  cuda_check(cudaMalloc(&d_part, sizeof(double) * 3 * nitems), "batch reduce partials");
+  cuda_check(cudaMemcpyAsync(d_items, items.data(), items.size(), cudaMemcpyHostToDevice, c->stream), "upload items");
+  double bytes = 0;
+  for (size_t i = 0; i < c->n.size(); i++) bytes += (double)c->bytes((int)i);
+  timed(c, SC_REDUCE, bytes, 0, 1, [&] {
+    return launch_batch_reduce(c->prec, c->base, c->n, c->off, (double*)d_probs, (double*)d_part, d_items, nitems,
+                               c->stream);
+  });
+  std::vector<double> part(3 * nitems);
+  cuda_check(cudaMemcpyAsync(part.data(), d_part, sizeof(double) * 3 * nitems, cudaMemcpyDeviceToHost, c->stream), "D2H");
+  if (probs)
+    cuda_check(cudaMemcpyAsync(probs, d_probs, sizeof(double) * nprob, cudaMemcpyDeviceToHost, c->stream), "D2H probs");
+  cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  const size_t count = c->n.size();
+  std::vector<double> tr(count, 0.0), pu(count, 0.0);
+  for (size_t j = 0; j < nitems; j++) {  // chunks of one instance are summed in order
+    tr[item_inst[j]] += part[3 * j];
+    pu[item_inst[j]] += part[3 * j + 2];
+  }
+  for (size_t i = 0; i < count; i++) {
+    if (trace_re) trace_re[i] = tr[i];
+    if (purity) purity[i] = pu[i];
+  }
+  API_END(c)
+}
+
 int vqd_measure(vqd_t c, int inst, int q, double u, int force, int* outcome, double* prob) {
   API_BEGIN
   need_ctx(c);

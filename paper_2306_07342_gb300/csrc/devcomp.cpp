@@ -81,6 +81,17 @@ Mat raman(double phi, double om, double de, double t) {
           -I1 * (om / w * s) * std::exp(-I1 * phi), cd(c, de / w * s)};
 }
 
+// Off-resonant Rabi drive seen by a passive qubit, Sec. 3.3 Eq. (off_resonant), as printed: the detuned
+// Rabi rotation exp(-i t (Omega X + Delta Z)/2) followed by the frame phase diag(e^{ih}, e^{-ih}),
+// h = Omega_R t / 2, Omega_R = sqrt(Omega^2 + Delta^2).  Omega_R = 0 gives the identity.
+Mat off_resonant(double om, double de, double t) {
+  const double w = std::hypot(om, de);
+  if (w == 0.0) return {1.0, 0.0, 0.0, 1.0};
+  const double h = w * t / 2, c = std::cos(h), s = std::sin(h);
+  const cd e = std::exp(I1 * h), a(c, -de / w * s), b(0.0, -om / w * s);
+  return {a * e, b * e, b / e, std::conj(a) / e};
+}
+
 Mat diag4(cd a, cd b, cd c, cd d) {
   Mat m(16, 0.0);
   m[0] = a; m[5] = b; m[10] = c; m[15] = d;
@@ -176,7 +187,7 @@ void require(bool ok, const char* msg) {
 
 int native_arity(int code) {
   static const int ar[VQD_OP_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2,
-                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2};
+                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2};
   if (code < 0 || code >= VQD_OP_COUNT) return -1;
   return ar[code];
 }
@@ -240,6 +251,15 @@ Op compile_native(const vqd_native_op& o, unsigned flags) {
     case VQD_OP_EXCHANGE: {
       Mat u = mul(mul(pauli_exp2(1, 1, P[0] / 4), pauli_exp2(2, 2, P[0] / 4), 4), pauli_exp2(3, 3, P[0] / 4), 4);
       U1(u);
+      break;
+    }
+    case VQD_OP_OFFRES: U1(off_resonant(P[0], P[1], P[2])); break;
+    case VQD_OP_ZZ_STATIC: {  // Sec. 8 static ZZ of a transmon pair; control = first qubit
+      const double d1 = P[1] - P[2], d2 = P[1] + P[3];
+      require(d1 != 0.0 && d2 != 0.0, "zz_static: Delta_ct - alpha_t or Delta_ct + alpha_c is zero");
+      const double beta = P[0] * P[0] * (1.0 / d1 - 1.0 / d2);
+      require(std::isfinite(beta), "zz_static: beta is not finite");
+      U1(pauli_exp2(3, 3, beta));
       break;
     }
     case VQD_OP_DEPOL1: require(P[0] >= 0 && P[0] <= 0.75 + 1e-12, "depol1: p outside [0,3/4]"); S(sup_depol1(P[0])); break;

@@ -612,6 +612,85 @@ cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const 
   return expect_t<double>((const cx<double>*)state, n, nterms, xmask, zymask, scratch, out, s);
 }
 
+// ================================================================== batched reductions
+namespace dev {
+// One CTA per (instance, chunk of its amplitudes): diagonal -> probabilities (written directly),
+// and FP64 partial sums of Re tr, Im tr and sum |rho_ij|^2 for the chunk.
+struct BatchRedItem {
+  uint64_t offset_amps;  // instance start in the batch allocation
+  uint64_t begin, end;   // amplitude range of this chunk
+  uint64_t prob_offset;  // where the instance's 2^n probabilities go
+  int n;
+  int inst;
+};
+template <class T>
+__global__ void __launch_bounds__(256) k_batch_reduce(const cx<T>* __restrict__ all, const BatchRedItem* __restrict__ items,
+                                                      double* __restrict__ probs, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const BatchRedItem it = items[blockIdx.x];
+  const cx<T>* st = all + it.offset_amps;
+  const uint64_t dim = 1ull << it.n;
+  double tr_re = 0, tr_im = 0, pur = 0;
+  for (uint64_t i = it.begin + threadIdx.x; i < it.end; i += blockDim.x) {
+    const cx<T> v = st[i];
+    pur = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, pur));
+    const uint64_t r = i & (dim - 1), c = i >> it.n;
+    if (r == c) {
+      tr_re += (double)v.x;
+      tr_im += (double)v.y;
+      probs[it.prob_offset + r] = (double)v.x;
+    }
+  }
+  tr_re = block_sum(tr_re, sh);
+  tr_im = block_sum(tr_im, sh);
+  pur = block_sum(pur, sh);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = tr_re;
+    part[3 * blockIdx.x + 1] = tr_im;
+    part[3 * blockIdx.x + 2] = pur;
+  }
+}
+}  // namespace dev
+
+cudaError_t launch_batch_reduce(int prec, const void* base, const std::vector<int>& n, const std::vector<size_t>& off_bytes,
+                                double* d_probs, double* d_part, void* d_items, size_t nitems, cudaStream_t s) {
+  if (prec == VQD_F32)
+    dev::k_batch_reduce<float><<<(unsigned)nitems, 256, 0, s>>>((const cx<float>*)base, (const dev::BatchRedItem*)d_items,
+                                                                d_probs, d_part);
+  else
+    dev::k_batch_reduce<double><<<(unsigned)nitems, 256, 0, s>>>((const cx<double>*)base, (const dev::BatchRedItem*)d_items,
+                                                                 d_probs, d_part);
+  (void)n;
+  (void)off_bytes;
+  return cudaGetLastError();
+}
+
+size_t batch_reduce_item_bytes() { return sizeof(dev::BatchRedItem); }
+
+void batch_reduce_items(const std::vector<int>& n, const std::vector<size_t>& off_bytes, size_t esize,
+                        std::vector<unsigned char>& items, std::vector<int>& item_inst) {
+  const uint64_t chunk = 1ull << 20;  // amplitudes per CTA
+  uint64_t prob_off = 0;
+  items.clear();
+  item_inst.clear();
+  for (size_t i = 0; i < n.size(); i++) {
+    const uint64_t N = 1ull << (2 * n[i]);
+    for (uint64_t b = 0; b < N; b += chunk) {
+      dev::BatchRedItem it;
+      it.offset_amps = off_bytes[i] / esize;
+      it.begin = b;
+      it.end = std::min(N, b + chunk);
+      it.prob_offset = prob_off;
+      it.n = n[i];
+      it.inst = (int)i;
+      const unsigned char* p = (const unsigned char*)&it;
+      items.insert(items.end(), p, p + sizeof(it));
+      item_inst.push_back((int)i);
+    }
+    prob_off += 1ull << n[i];
+  }
+}
+
 // ================================================================== allocation-free probabilities
 // vqd_prob_static: the marginal-probability reduction with its partial sums in a file-scope device
 // array instead of memory from cudaMalloc.  Every GPU that loads the library holds this array

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "vqd_internal.h"
 
@@ -31,6 +32,13 @@ cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const 
                           const uint32_t* zymask, double* scratch, double* out, cudaStream_t s);
 
 int num_sms();
+
+// Batched reductions of a batch context: per-CTA items over (instance, chunk of amplitudes).
+size_t batch_reduce_item_bytes();
+void batch_reduce_items(const std::vector<int>& n, const std::vector<size_t>& off_bytes, size_t esize,
+                        std::vector<unsigned char>& items, std::vector<int>& item_inst);
+cudaError_t launch_batch_reduce(int prec, const void* base, const std::vector<int>& n, const std::vector<size_t>& off_bytes,
+                                double* d_probs, double* d_part, void* d_items, size_t nitems, cudaStream_t s);
 
 // Records the message of a failed vqd_prob_static call for vqd_last_error(NULL); returns code.
 int report_static_error(int code, const char* msg);

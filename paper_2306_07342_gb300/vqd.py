@@ -23,7 +23,8 @@ VQD_MAX_FUSE = 6
 # Native op codes, in the order of the header's vqd_op_code enum.
 OP_CODES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
             "crz_xtalk", "exchange", "depol1", "depol2", "deph1", "deph2", "amp", "bitflip", "bitflip2", "gamp",
-            "idle", "idle_depol", "stderr1", "stderr2", "ampdeph2", "leak_init", "leak_cz"]
+            "idle", "idle_depol", "stderr1", "stderr2", "ampdeph2", "leak_init", "leak_cz",
+            "offres", "zz_static"]
 OP_CODE = {name: i for i, name in enumerate(OP_CODES)}
 
 NATIVE_OP_DTYPE = np.dtype([("code", "<i4"), ("nq", "<i4"), ("q", "<i4", (2,)), ("par", "<f8", (4,))])
@@ -91,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "vqd_plan_info": (I, [I, I, I, P, I, I, I, U, P]),
             "vqd_set_tile_shape": (I, [P, I, I]),
             "vqd_measure": (I, [P, I, I, D, I, P, P]),
+            "vqd_batch_reduce": (I, [P, P, P, P]),
             "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
@@ -298,6 +300,20 @@ def vqd_traj_expect(n: int, prec: int, ops, ntraj: int, seed: int, paulis, coeff
     _check(lib().vqd_traj_expect(n, prec, len(a), _ptr(a), flags, ntraj, seed, len(c), _ptr(p), _ptr(c),
                                  ctypes.c_void_p(stream), _ptr(out), ctypes.byref(m), ctypes.byref(se)))
     return out, m.value, se.value
+
+
+def vqd_batch_reduce(ctx, ns):
+    """Every instance's Z-basis probabilities (list of arrays), traces and purities in one batched reduction."""
+    total = int(sum(2 ** n for n in ns))
+    probs = np.zeros(total, dtype=np.float64)
+    tr = np.zeros(len(ns), dtype=np.float64)
+    pu = np.zeros(len(ns), dtype=np.float64)
+    _check(lib().vqd_batch_reduce(ctx, _ptr(probs), _ptr(tr), _ptr(pu)), ctx)
+    out, o = [], 0
+    for n in ns:
+        out.append(probs[o:o + 2 ** n])
+        o += 2 ** n
+    return out, tr, pu
 
 
 def vqd_measure(ctx, inst: int, q: int, u: float = 0.0, force: int = -1):

@@ -95,6 +95,9 @@ def test_compile_rejects_bad_ops(vqd):
     with pytest.raises(vqd.VQDError) as e:
         vqd.vqd_compile_op(NativeOp("depol1", (0,), (0.9,)))          # p > 3/4
     assert e.value.code == vqd.VQD_EINVAL
+    with pytest.raises(vqd.VQDError) as e:                            # Delta_ct - alpha_t = 0: no finite beta
+        vqd.vqd_compile_op(NativeOp("zz_static", (0, 1), (0.1, -2.5, -2.5, -2.0)))
+    assert e.value.code == vqd.VQD_EINVAL
     a = vqd.native_ops([NativeOp("rx", (0,), (0.1,))])
     a[0]["code"] = 99
     isu, k = ctypes.c_int(), ctypes.c_int()

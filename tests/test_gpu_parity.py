@@ -71,6 +71,26 @@ def test_one_qubit_operators(vqd, p, n):
         vqd.vqd_destroy(ctx)
 
 
+@pytest.mark.parametrize("name", list(OP_NAMES))
+def test_every_native_op_alone(vqd, name):
+    """Each native op of the device vocabulary, compiled by the library and applied by vqd_apply_native to a
+    random 5-qubit state in FP64, against the oracle's compiler and evolution (both qubit orders for pairs)."""
+    from workloads.circuits import _random_params, _rng
+    n = 5
+    r = _rng(4000 + list(OP_NAMES).index(name))
+    rho = rand_state(n, np.random.default_rng(4100 + list(OP_NAMES).index(name)))
+    nq = OP_NAMES[name][0]
+    ops = [NativeOp(name, (3,) if nq == 1 else (3, 1), _random_params(r, name)),
+           NativeOp(name, (0,) if nq == 1 else (0, 4), _random_params(r, name))]
+    ctx = make_ctx(vqd, n, "f64", rho)
+    try:
+        vqd.vqd_apply_native(ctx, 0, ops)
+        want = evolve.run_program(Program(n, ops), rho0=rho)
+        assert np.abs(gpu_state(vqd, ctx) - want).max() < TOL_F64
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
 @pytest.mark.parametrize("p", PRECS)
 @pytest.mark.parametrize("n,targets", [(2, (0, 1)), (2, (1, 0)), (5, (4, 1)), (7, (2, 6)), (7, (6, 5))])
 def test_two_qubit_operators(vqd, p, n, targets):
@@ -215,11 +235,15 @@ def test_batch_matches_per_instance_oracle(vqd, p, fuse):
     ctx = vqd.vqd_create_batch([q.n for q in progs], prec_code(vqd, p))
     try:
         vqd.vqd_run_batch(ctx, [q.ops for q in progs], fuse)
+        probs, trs, purs = vqd.vqd_batch_reduce(ctx, [q.n for q in progs])
         for i, prog in enumerate(progs):
             want = evolve.run_program(prog)
             got = gpu_state(vqd, ctx, i)
-            assert np.abs(got - want).max() < tol(p, len(prog.ops)), i
-            assert abs(vqd.vqd_trace(ctx, i) - 1) < tol(p, len(prog.ops))
+            t = tol(p, len(prog.ops))
+            assert np.abs(got - want).max() < t, i
+            assert abs(vqd.vqd_trace(ctx, i) - 1) < t
+            assert np.abs(probs[i] - measure.probs(want, range(prog.n))).max() < t
+            assert abs(trs[i] - measure.trace(want).real) < t and abs(purs[i] - measure.purity(want)) < t
     finally:
         vqd.vqd_destroy(ctx)
 

@@ -328,11 +328,73 @@ def test_stderr_inversion_round_trip(nq, fbar, x):
         assert p == 0.0
 
 
+# ---------------------------------------------------------------- device-family crosstalk (Secs. 3.3, 8)
+@pytest.mark.parametrize("omega,delta,t", [(1.0, 0.0, 0.7), (0.8, 1.3, 2.1), (2.0, -3.0, 1.1), (0.0, 0.9, 1.7),
+                                           (1.5, 40.0, 0.3), (0.0, -0.9, 1.7), (1.2, -25.0, 2.2)])
+def test_off_resonant_is_frame_phase_times_detuned_rotation(omega, delta, t):
+    """Eq. (off_resonant) as printed is exp(+i Omega_R t Z/2) exp(-i t (Omega X + Delta Z)/2): a detuned Rabi
+    rotation seen from a frame turning at Omega_R.  Both factors from the matrix exponential of their generators."""
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    om_r = math.hypot(omega, delta)
+    want = expm(0.5j * om_r * t * Z) @ expm(-0.5j * t * (omega * X + delta * Z))
+    U = oc.off_resonant(omega, delta, t)
+    assert np.abs(U - want).max() < 1e-14
+    assert np.abs(U.conj().T @ U - np.eye(2)).max() < 1e-14
+
+
+@pytest.mark.parametrize("delta", [1e2, 1e3, 1e4])
+def test_off_resonant_tends_to_identity_for_large_detuning(delta):
+    """Sec. 3.3: the passive qubit is left alone when Delta >> Omega; |U - I| <= Omega / Delta.  (As printed the
+    frame phase turns with +Omega_R, so the limit is the identity for a positive frequency difference.)"""
+    for omega, t in [(1.0, 0.9), (2.5, 3.0)]:
+        U = oc.off_resonant(omega, delta, t)
+        assert np.abs(U - np.eye(2)).max() <= omega / abs(delta) * 1.0001
+
+
+def test_off_resonant_special_cases():
+    """Omega = Delta = 0: identity (limit of the formula).  Omega = 0: no population transfer.
+    Resonance (Delta = 0): Rz(-Omega t) Rx(Omega t) with the textbook rotations."""
+    assert np.abs(oc.off_resonant(0.0, 0.0, 5.0) - np.eye(2)).max() == 0.0
+    U = oc.off_resonant(0.0, 1.7, 0.6)
+    assert abs(U[0, 1]) == 0.0 and abs(U[1, 0]) == 0.0
+    w = 1.3 * 0.8
+    rz = np.diag([np.exp(-0.5j * -w), np.exp(0.5j * -w)])
+    rx = np.array([[math.cos(w / 2), -1j * math.sin(w / 2)], [-1j * math.sin(w / 2), math.cos(w / 2)]])
+    assert np.abs(oc.off_resonant(1.3, 0.0, 0.8) - rz @ rx).max() < 1e-15
+
+
+def test_static_zz_beta_worked_value_and_matrix():
+    """J = 0.1, Delta = 0.5, alpha_t = -2.5, alpha_c = -2.0: beta = 0.01 (1/3 + 2/3) = 0.01 (Sec. 8 formula,
+    by hand); the op is the matrix exponential of -i beta Z Z."""
+    beta = oc.static_zz_beta(0.1, 0.5, -2.5, -2.0)
+    assert abs(beta - 0.01) < 1e-17
+    Z = np.diag([1.0, -1.0])
+    assert np.abs(oc.zz_static(0.1, 0.5, -2.5, -2.0) - expm(-1j * 0.01 * np.kron(Z, Z))).max() < 1e-15
+
+
+def test_static_zz_invariants():
+    """beta is symmetric in the two transmons (swap alpha_c, alpha_t and flip Delta_ct), homogeneous of degree
+    one in the frequencies, and zero when the anharmonicities cancel (alpha_c + alpha_t = 0)."""
+    r = np.random.default_rng(5)
+    for _ in range(20):
+        j, d = r.uniform(0.01, 0.3), r.uniform(0.1, 1.5)
+        at, ac = r.uniform(-3.5, -1.8), r.uniform(-3.5, -1.8)
+        b = oc.static_zz_beta(j, d, at, ac)
+        assert abs(oc.static_zz_beta(j, -d, ac, at) - b) < 1e-15
+        s = r.uniform(0.1, 10.0)
+        assert abs(oc.static_zz_beta(s * j, s * d, s * at, s * ac) - s * b) < 1e-14 * max(1.0, abs(s * b))
+        assert abs(oc.static_zz_beta(j, d, at, -at)) < 1e-16
+    with pytest.raises(ValueError):
+        oc.static_zz_beta(0.1, -2.5, -2.5, -2.0)
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4
     prog = random_program(21, n, 60, names=["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi",
-                                            "zx", "zz", "xx", "zzphase", "zz_idle", "crz_xtalk", "exchange"])
+                                            "zx", "zz", "xx", "zzphase", "zz_idle", "crz_xtalk", "exchange",
+                                            "offres", "zz_static"])
     psi = np.zeros(2 ** n, dtype=complex)
     psi[0] = 1
     for o in prog.ops:

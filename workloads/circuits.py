@@ -54,6 +54,9 @@ OP_NAMES = {
     "ampdeph2": (2, ("dt", "t1", "t2")),      # T1/T2 decay of both qubits of a pair as one 2-qubit channel
     "leak_init": (1, ("gamma",)),             # CPTN init leakage L
     "leak_cz": (2, ("alpha", "beta")),        # CPTN Rydberg decay K
+    # device-family crosstalk unitaries
+    "offres": (1, ("omega", "delta", "t")),    # off-resonant Rabi drive on a passive qubit, Eq. (off_resonant)
+    "zz_static": (2, ("j", "delta", "alpha_t", "alpha_c")),  # SC static ZZ exp(-i beta Z Z), beta from J, Delta, alpha
 }
 
 
@@ -347,5 +350,7 @@ def _random_params(r: np.random.Generator, name: str) -> Tuple[float, ...]:
         "stderr1": lambda: (u(0.95, 1.0), u(0, 1)), "stderr2": lambda: (u(0.9, 1.0), u(0, 1)),
         "ampdeph2": lambda: (u(0.01, 20), u(20, 200), u(10, 100)),
         "leak_init": lambda: (u(0, 0.1),), "leak_cz": lambda: (u(0, 0.1), u(0, 0.01)),
+        "offres": lambda: (u(0.5, 2.0), u(-8.0, 8.0), u(0.0, 3.0)),
+        "zz_static": lambda: (u(0.02, 0.2), u(0.2, 1.0), u(-3.0, -2.0), u(-3.0, -2.0)),
     }
     return table[name]()
