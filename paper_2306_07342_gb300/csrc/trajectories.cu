@@ -406,14 +406,14 @@ extern "C" int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* o
       cudaGetLastError();
       throw Error(e == cudaErrorMemoryAllocation ? VQD_ENOMEM : VQD_EDEVICE, cudaGetErrorString(e));
     }
+    // two passes (mean, then squared deviations): the one-pass E[x^2] - E[x]^2 loses the spread of
+    // nearly equal values to cancellation
     double s1 = 0, s2 = 0;
-    for (int t = 0; t < ntraj; t++) {
-      s1 += out[t];
-      s2 += out[t] * out[t];
-    }
+    for (int t = 0; t < ntraj; t++) s1 += out[t];
     const double m = s1 / ntraj;
+    for (int t = 0; t < ntraj; t++) s2 += (out[t] - m) * (out[t] - m);
     if (mean) *mean = m;
-    if (stderr_out) *stderr_out = ntraj > 1 ? std::sqrt(std::max(0.0, (s2 / ntraj - m * m) / (ntraj - 1))) : 0.0;
+    if (stderr_out) *stderr_out = ntraj > 1 ? std::sqrt(s2 / (ntraj - 1) / ntraj) : 0.0;
     return VQD_OK;
   } catch (const Error& e) {
     return report_static_error(e.code, e.what());

@@ -71,6 +71,7 @@ def test_traj_unitary_program_is_exact_every_trajectory(vqd, p, tol):
     vals, mean, se = vqd.vqd_traj_expect(6, vqd.VQD_F64 if p == "f64" else vqd.VQD_F32, prog.ops, 8, 3, codes, coeffs)
     assert np.abs(vals - exact).max() < tol
     assert se < tol
+    assert abs(mean - vals.mean()) < 1e-15 and abs(se - vals.std(ddof=1) / math.sqrt(vals.size)) < 1e-15
 
 
 @pytest.mark.gpu
