@@ -213,6 +213,7 @@ def measure_batch(vqd, torch, stream_handle, count):
         for i in range(count):
             vqd.vqd_init_zero(ctx, i)
         vqd.vqd_run_batch(ctx, arrays)                       # same batch again: one graph launch
+        bstream.synchronize()
         t1 = time.perf_counter()
         probs, trs, purs = vqd.vqd_batch_reduce(ctx, ns)     # every instance's results, one launch, one read-back
         wall = time.perf_counter() - t0
@@ -247,7 +248,7 @@ def measure_batch(vqd, torch, stream_handle, count):
         return {"value": units / wall, "unit": "amp-updates/s", "kernel_value": units / kern_s,
                 "first_run_value": units / first_wall, "first_run_s": first_wall,
                 "instances": count, "native_ops": int(sum(len(a) for a in arrays)), "amp_updates": units,
-                "kernel_s": kern_s, "wall_s": wall, "host_init_replay_s": wall - kern_s - reduce_wall,
+                "kernel_s": kern_s, "wall_s": wall, "host_init_replay_s": wall - reduce_wall - kern_s,
                 "batch_reduce_s": reduce_wall,
                 "state_bytes": int(sum(vqd.vqd_state_bytes(n, vqd.VQD_F32) for n in ns)),
                 "per_instance_sample": {"instances": len(sample), **res},

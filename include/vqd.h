@@ -231,6 +231,46 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
 int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int idle_code, const double* t1,
                  const double* t2, int cap, vqd_native_op* out, int* nout);
 
+/* ------------------------------------------------------------------------------------------
+ * Device-family compilers (host only): a logical circuit in a family's native gates -> the
+ * native op list with that family's noise, ready for vqd_apply_native / vqd_run_program.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Superconducting transmon device of Sec. 8 with the parameters of its App. C table.  All arrays
+ * are host arrays owned by the caller, read during the call only.  Frequencies in MHz, times in us. */
+typedef struct {
+  int32_t n;               /* qubits (1..32) */
+  int32_t ncouple;         /* capacitively coupled pairs */
+  const double* t1;        /* [n] T1 > 0 */
+  const double* t2;        /* [n] T2 > 0, the dephasing time of Eq. (depht2) */
+  const double* excited;   /* [n] thermal excited population p_j in [0,1] (Eq. thermalstate); gamp relaxes
+                              towards it (gamp's ground population 1 - p_j) */
+  const double* freq;      /* [n] qubit frequencies */
+  const double* anharm;    /* [n] anharmonicities alpha_j, used with the sign given */
+  const int32_t* couple;   /* [2*ncouple] pairs (c, t), distinct qubits */
+  const double* coupling;  /* [ncouple] coupling strengths J */
+  const double* fid_read;  /* [n] readout fidelities in [1/4,1], or NULL for no readout depolarisation */
+  double dur_rxy;          /* duration of Rx, Ry; Rz is virtual and takes no time */
+  double dur_zx;           /* duration of the cross-resonance ZX */
+  double dur_zz;           /* duration of the siZZle ZZ */
+  double dur_meas;         /* readout duration (the gamp(t_M) before the readout) */
+  uint32_t flags;          /* VQD_SC_NO_PASSIVE | VQD_SC_NO_STATIC_ZZ */
+} vqd_sc_device;
+#define VQD_SC_NO_PASSIVE 1u    /* no T1/T2 decay (passive and readout gamp) */
+#define VQD_SC_NO_STATIC_ZZ 2u  /* no static ZZ crosstalk */
+
+/* Compile a logical circuit of Rx, Ry, Rz, ZX, ZZ ops (others: VQD_EINVAL) for the device.  Gates are
+ * exact and run in parallel: each starts in the first layer where all its qubits are free; a layer
+ * lasts as long as its longest gate.  Per layer with nonzero length L, in this order: its gates
+ * (program order); for every coupled pair (c, t) with J != 0 not under a ZZ gate of the layer, a
+ * VQD_OP_ZZ_STATIC with parameters 2 pi L (J, f_c - f_t, alpha_t, alpha_c); for every qubit j whose
+ * gate in the layer (if any) is shorter than L, by dt = L - its gate's duration: gamp(dt, T1_j,
+ * 1 - p_j) then deph1((1 - e^{-dt/T2_j})/2).  With readout != 0, for every qubit: gamp(t_M, T1_j,
+ * 1 - p_j) (when t_M > 0), then depol1(1 - F_j) (when fid_read is given).  out == NULL only counts:
+ * *nout receives the number of ops; otherwise out has room for cap ops (VQD_EINVAL if too few). */
+int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                   vqd_native_op* out, int* nout);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);

@@ -1,0 +1,102 @@
+"""Oracle of the superconducting device compiler (test infrastructure: only tests, the smoke check and
+the benchmark's CPU baseline use it).
+
+It follows the superconducting error model of Sec. 8 and its App. C parameter table, step by step, in
+plain Python:
+
+- Gates are exact and run fully in parallel. A gate starts in the first layer where all its qubits
+  are free, and a layer lasts as long as its longest gate. Rz is virtual and takes no time.
+- Errors come only from passive noise over each layer of length L:
+  - the static ZZ of every capacitively coupled pair, exp(-i beta Z Z) with
+    beta = J^2 (1/(Delta_ct - alpha_t) - 1/(Delta_ct + alpha_c)). A pair under a siZZle (ZZ) gate
+    is exempt: the gate absorbs its static ZZ.
+  - on every qubit not busy for the whole layer, for its idle time dt: generalised amplitude damping
+    towards the thermal state (Eq. gdamp, ground population 1 - p_j), then the dephasing of
+    Eq. (depht2).
+- Readout, when asked for: gamp(t_M) then depol(eps), with eps = 1 - F (the part before the
+  measurement in Sec. 8's readout circuit).
+
+Readings, also used by the library:
+- Table frequencies are in MHz and times in us. The static ZZ phase is beta computed from the angular
+  frequencies 2 pi f, times L.
+- The ZZ op is handed the four angles 2 pi L (J, f_c - f_t, alpha_t, alpha_c). beta is homogeneous of
+  degree one, so beta of these angles is the accumulated phase.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Sequence
+
+from workloads.circuits import NativeOp
+
+DURATION_KEYS = {"rx": "dur_rxy", "ry": "dur_rxy", "zx": "dur_zx", "zz": "dur_zz"}
+
+
+def gate_duration(dev: Dict, op: NativeOp) -> float:
+    """Duration of one superconducting native gate (Sec. 8: Rz virtual; App. C durations)."""
+    if op.name == "rz":
+        return 0.0
+    if op.name not in DURATION_KEYS:
+        raise ValueError(f"{op.name} is not a superconducting native gate")
+    return float(dev[DURATION_KEYS[op.name]])
+
+
+def asap_layers(n: int, ops: Sequence[NativeOp]) -> List[List[int]]:
+    """Indices of the ops in each parallel layer: every op joins the first layer after the last one that
+    used any of its qubits."""
+    free_from = [0] * n
+    layers: List[List[int]] = []
+    for i, op in enumerate(ops):
+        layer = max(free_from[q] for q in op.qubits)
+        for q in op.qubits:
+            free_from[q] = layer + 1
+        while len(layers) <= layer:
+            layers.append([])
+        layers[layer].append(i)
+    return layers
+
+
+def thermal_decay(dev: Dict, j: int, dt: float) -> List[NativeOp]:
+    """Free-induction decay of qubit j over dt: gamp towards the thermal state, then deph of Eq. (depht2)."""
+    p_excited = float(dev["excited"][j])
+    return [NativeOp("gamp", (j,), (dt, float(dev["t1"][j]), 1.0 - p_excited)),
+            NativeOp("deph1", (j,), (0.5 * (1.0 - math.exp(-dt / float(dev["t2"][j]))),))]
+
+
+def sc_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> List[NativeOp]:
+    """Logical circuit -> native op list of the superconducting device (Sec. 8, App. C)."""
+    n = int(dev["n"])
+    flags = int(dev.get("flags", 0))
+    passive, static_zz = not (flags & 1), not (flags & 2)
+    out: List[NativeOp] = []
+    for layer in asap_layers(n, ops):
+        length = max(gate_duration(dev, ops[i]) for i in layer)
+        busy_for = [0.0] * n
+        for i in layer:
+            out.append(ops[i])
+            for q in ops[i].qubits:
+                busy_for[q] = gate_duration(dev, ops[i])
+        if length <= 0:
+            continue
+        if static_zz:
+            sizzle_pairs = {frozenset(ops[i].qubits) for i in layer if ops[i].name == "zz"}
+            for (c, t), J in zip(dev["couple"], dev["coupling"]):
+                if J == 0 or frozenset((c, t)) in sizzle_pairs:
+                    continue
+                angle = 2.0 * math.pi * length
+                out.append(NativeOp("zz_static", (int(c), int(t)),
+                                    (angle * J, angle * (dev["freq"][c] - dev["freq"][t]),
+                                     angle * dev["anharm"][t], angle * dev["anharm"][c])))
+        if passive:
+            for j in range(n):
+                idle = length - busy_for[j]
+                if idle > 0:
+                    out.extend(thermal_decay(dev, j, idle))
+    if readout:
+        for j in range(n):
+            if passive and dev["dur_meas"] > 0:
+                out.append(NativeOp("gamp", (j,), (float(dev["dur_meas"]), float(dev["t1"][j]),
+                                                   1.0 - float(dev["excited"][j]))))
+            if dev.get("fid_read") is not None:
+                out.append(NativeOp("depol1", (j,), (1.0 - float(dev["fid_read"][j]),)))
+    return out

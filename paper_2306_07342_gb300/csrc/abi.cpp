@@ -612,6 +612,117 @@ int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int
   API_END(nullptr)
 }
 
+// Superconducting device compiler, Sec. 8 and the superconducting table of App. C: gates are exact
+// and run in parallel (ASAP layers); the errors are the passive T1/T2 decay (gamp towards the thermal
+// state, then the dephasing of Eq. depht2) of qubits outside an active gate, the static ZZ of every
+// capacitively coupled pair not under a siZZle gate, and the readout's gamp(t_M) then depol(1 - F).
+int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                   vqd_native_op* out, int* nout) {
+  API_BEGIN
+  if (!dev || !nout || nin < 0 || (nin > 0 && !in) || (out && cap < 0)) throw Error(VQD_EINVAL, "bad argument");
+  const int n = dev->n;
+  if (n < 1 || n > 32 || dev->ncouple < 0 || (dev->ncouple > 0 && (!dev->couple || !dev->coupling)))
+    throw Error(VQD_EINVAL, "bad device: qubit count or coupling list");
+  if (!dev->t1 || !dev->t2 || !dev->excited || !dev->freq || !dev->anharm) throw Error(VQD_EINVAL, "bad device: NULL table");
+  for (int j = 0; j < n; j++) {
+    if (!(dev->t1[j] > 0) || !(dev->t2[j] > 0)) throw Error(VQD_EINVAL, "bad device: T1 and T2 must be positive");
+    if (!(dev->excited[j] >= 0 && dev->excited[j] <= 1)) throw Error(VQD_EINVAL, "bad device: excited population outside [0,1]");
+    if (dev->fid_read && !(dev->fid_read[j] >= 0.25 && dev->fid_read[j] <= 1))
+      throw Error(VQD_EINVAL, "bad device: readout fidelity outside [1/4,1]");
+  }
+  for (int k = 0; k < dev->ncouple; k++) {
+    const int a = dev->couple[2 * k], b = dev->couple[2 * k + 1];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b) throw Error(VQD_EINVAL, "bad device: coupled pair");
+  }
+  if (!(dev->dur_rxy >= 0 && dev->dur_zx >= 0 && dev->dur_zz >= 0 && dev->dur_meas >= 0))
+    throw Error(VQD_EINVAL, "bad device: negative duration");
+  const bool passive = !(dev->flags & VQD_SC_NO_PASSIVE), static_zz = !(dev->flags & VQD_SC_NO_STATIC_ZZ);
+  // layer of every gate (a gate starts once all its qubits are free), and its duration
+  std::vector<int> layer(nin), ready(n, 0);
+  std::vector<double> dur(nin);
+  int nl = 0;
+  for (int i = 0; i < nin; i++) {
+    const vqd_native_op& o = in[i];
+    switch (o.code) {
+      case VQD_OP_RX: case VQD_OP_RY: dur[i] = dev->dur_rxy; break;
+      case VQD_OP_RZ: dur[i] = 0; break;  // virtual Z (Sec. 8)
+      case VQD_OP_ZX: dur[i] = dev->dur_zx; break;
+      case VQD_OP_ZZ: dur[i] = dev->dur_zz; break;
+      default: throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a superconducting native gate");
+    }
+    const int ar = native_arity(o.code);
+    if (o.nq != ar) throw Error(VQD_EINVAL, "bad arity at op " + std::to_string(i));
+    int l = 0;
+    for (int j = 0; j < ar; j++) {
+      if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
+        throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
+      l = std::max(l, ready[o.q[j]]);
+    }
+    for (int j = 0; j < ar; j++) ready[o.q[j]] = l + 1;
+    layer[i] = l;
+    nl = std::max(nl, l + 1);
+  }
+  std::vector<std::vector<int>> by_layer(nl);
+  for (int i = 0; i < nin; i++) by_layer[layer[i]].push_back(i);
+  int cnt = 0;
+  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2, double p3) {
+    if (out) {
+      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+      vqd_native_op& o = out[cnt];
+      std::memset(&o, 0, sizeof(o));
+      o.code = code;
+      o.nq = q1 < 0 ? 1 : 2;
+      o.q[0] = q0;
+      o.q[1] = q1 < 0 ? 0 : q1;
+      o.par[0] = p0; o.par[1] = p1; o.par[2] = p2; o.par[3] = p3;
+    }
+    cnt++;
+  };
+  const double two_pi = 2 * 3.14159265358979323846;
+  auto decay = [&](int j, double dt) {  // free-induction decay of qubit j over dt
+    emit(VQD_OP_GAMP, j, -1, dt, dev->t1[j], 1 - dev->excited[j], 0);
+    emit(VQD_OP_DEPH1, j, -1, 0.5 * (1 - std::exp(-dt / dev->t2[j])), 0, 0, 0);
+  };
+  for (int l = 0; l < nl; l++) {
+    double len = 0;
+    std::vector<double> busy(n, 0.0);
+    for (int i : by_layer[l]) {
+      if (out) {
+        if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+        out[cnt] = in[i];
+      }
+      cnt++;
+      len = std::max(len, dur[i]);
+      for (int j = 0; j < in[i].nq; j++) busy[in[i].q[j]] = dur[i];
+    }
+    if (len <= 0) continue;
+    if (static_zz) {
+      for (int k = 0; k < dev->ncouple; k++) {
+        const int c = dev->couple[2 * k], t = dev->couple[2 * k + 1];
+        bool sizzle = false;  // a siZZle gate on the pair replaces its static ZZ (Sec. 8)
+        for (int i : by_layer[l])
+          if (in[i].code == VQD_OP_ZZ && ((in[i].q[0] == c && in[i].q[1] == t) || (in[i].q[0] == t && in[i].q[1] == c)))
+            sizzle = true;
+        if (sizzle || dev->coupling[k] == 0) continue;
+        // frequencies (MHz) times the layer length (us) as angles: beta is then the accumulated phase
+        const double w = two_pi * len;
+        emit(VQD_OP_ZZ_STATIC, c, t, w * dev->coupling[k], w * (dev->freq[c] - dev->freq[t]), w * dev->anharm[t],
+             w * dev->anharm[c]);
+      }
+    }
+    if (passive)
+      for (int j = 0; j < n; j++)
+        if (len - busy[j] > 0) decay(j, len - busy[j]);
+  }
+  if (readout)
+    for (int j = 0; j < n; j++) {
+      if (passive && dev->dur_meas > 0) emit(VQD_OP_GAMP, j, -1, dev->dur_meas, dev->t1[j], 1 - dev->excited[j], 0);
+      if (dev->fid_read) emit(VQD_OP_DEPOL1, j, -1, 1 - dev->fid_read[j], 0, 0, 0);
+    }
+  *nout = cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");

@@ -40,6 +40,20 @@ class kstat(ctypes.Structure):
                 ("alg_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double)]
 
 
+class sc_device(ctypes.Structure):
+    """vqd_sc_device: superconducting device table (pointers stay valid while the arrays live)."""
+    _fields_ = [("n", ctypes.c_int32), ("ncouple", ctypes.c_int32),
+                ("t1", ctypes.c_void_p), ("t2", ctypes.c_void_p), ("excited", ctypes.c_void_p),
+                ("freq", ctypes.c_void_p), ("anharm", ctypes.c_void_p), ("couple", ctypes.c_void_p),
+                ("coupling", ctypes.c_void_p), ("fid_read", ctypes.c_void_p),
+                ("dur_rxy", ctypes.c_double), ("dur_zx", ctypes.c_double), ("dur_zz", ctypes.c_double),
+                ("dur_meas", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+VQD_SC_NO_PASSIVE = 1
+VQD_SC_NO_STATIC_ZZ = 2
+
+
 class VQDError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libvqd error {code}: {msg}")
@@ -94,6 +108,7 @@ def lib() -> ctypes.CDLL:
             "vqd_measure": (I, [P, I, I, D, I, P, P]),
             "vqd_batch_reduce": (I, [P, P, P, P]),
             "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
+            "vqd_sc_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -266,6 +281,29 @@ def vqd_schedule(n: int, ops, durations, t1, t2, idle: str = "idle") -> np.ndarr
     cnt = ctypes.c_int()
     _check(lib().vqd_schedule(n, len(a), _ptr(a), _ptr(d), OP_CODE[idle], _ptr(t1a), _ptr(t2a), cap, _ptr(out),
                               ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def vqd_sc_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
+    """Compile a logical Rx/Ry/Rz/ZX/ZZ circuit for a superconducting device (host only).  ``dev`` holds
+    n, t1, t2, excited, freq, anharm, couple (pairs), coupling, fid_read (or None), dur_rxy, dur_zx,
+    dur_zz, dur_meas and optional flags.  Returns the native-op array."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    f64 = lambda key: np.ascontiguousarray(np.asarray(dev[key], dtype=np.float64))
+    keep = {k: f64(k) for k in ("t1", "t2", "excited", "freq", "anharm", "coupling")}
+    keep["couple"] = np.ascontiguousarray(np.asarray(dev["couple"], dtype=np.int32).reshape(-1))
+    fr = dev.get("fid_read")
+    keep["fid_read"] = None if fr is None else f64("fid_read")
+    d = sc_device(int(dev["n"]), len(keep["coupling"]),
+                  *[_ptr(keep[k]) if keep[k] is not None else None
+                    for k in ("t1", "t2", "excited", "freq", "anharm", "couple", "coupling", "fid_read")],
+                  float(dev["dur_rxy"]), float(dev["dur_zx"]), float(dev["dur_zz"]), float(dev["dur_meas"]),
+                  int(dev.get("flags", 0)))
+    cnt = ctypes.c_int()
+    _check(lib().vqd_sc_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), 0, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
+    _check(lib().vqd_sc_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
+                                ctypes.byref(cnt)))
     return out[: cnt.value].copy()
 
 
