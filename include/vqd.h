@@ -271,6 +271,38 @@ typedef struct {
 int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
                    vqd_native_op* out, int* nout);
 
+/* Silicon spin-qubit device of Sec. 7 with the parameters of its App. C table: a line of n qubits,
+ * controlled-phase gates between neighbours.  Host arrays owned by the caller.  MHz and us. */
+typedef struct {
+  int32_t n;               /* qubits (2..32) */
+  const double* t1;        /* [n] T1 > 0 (passive decay as depolarising, Eq. depolt1) */
+  const double* t2;        /* [n] T2 > 0 (Eq. depht2) */
+  const double* freq;      /* [n] qubit (ESR) frequencies */
+  const double* rabi;      /* [n] Rabi frequencies of the x/y rotations, > 0 */
+  const double* fid_1q;    /* [n] average fidelities of x/y rotations, in (0,1] */
+  double x_1q;             /* depolarising fraction of the single-qubit standard error, in [0,1] */
+  const double* freq_cz;   /* [n-1] controlled-phase frequencies of the pairs (k, k+1), > 0 */
+  const double* fid_cz;    /* [n-1] average fidelities of CZ/CPh on (k, k+1), in (0,1] */
+  double x_cz;             /* depolarising fraction of the two-qubit standard error */
+  const double* xtalk_on;  /* [(n-1)*(n-1)] row k = active pair, column j = passive pair; or NULL */
+  const double* xtalk_off; /* [n-1] off-state crosstalk angles of the pairs (k, k+1); or NULL */
+  uint32_t flags;          /* VQD_SI_NO_PASSIVE | VQD_SI_NO_OFFRES */
+} vqd_si_device;
+#define VQD_SI_NO_PASSIVE 1u  /* no passive T1/T2 decay */
+#define VQD_SI_NO_OFFRES 2u   /* no off-resonant drive of bystanders */
+
+/* Compile a logical circuit of Rx, Ry, Rz, CZ, CPh ops (CZ/CPh on neighbours; others: VQD_EINVAL) for
+ * the device.  Gates run one at a time, in program order.  Rz: virtual, emitted alone.  Rx/Ry(theta) on
+ * q, lasting t = |theta| / (2 pi rabi_q): the gate; stderr1(fid_1q[q], x_1q); with t > 0, for every
+ * j != q, offres(2 pi rabi_q, 2 pi |f_j - f_q|, t); for every j != q, idle_depol(t, T1_j, T2_j); for
+ * every pair (k, k+1) not containing q, crz_xtalk(xtalk_off[k]) (when given and nonzero).  CZ or
+ * CPh(theta) on (k, k+1) (CZ: theta = pi), lasting t = |theta| / (2 pi freq_cz[k]): the gate;
+ * stderr2(fid_cz[k], x_cz) on the gate's qubits; for every other pair j, crz_xtalk(xtalk_on[k][j]
+ * theta / pi) on (j, j+1) (when given and nonzero); idle_depol(t, ...) on every qubit outside the pair.
+ * out == NULL only counts; otherwise out has room for cap ops (VQD_EINVAL if too few). */
+int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, int cap, vqd_native_op* out,
+                   int* nout);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);

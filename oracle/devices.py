@@ -100,3 +100,69 @@ def sc_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Lis
             if dev.get("fid_read") is not None:
                 out.append(NativeOp("depol1", (j,), (1.0 - float(dev["fid_read"][j]),)))
     return out
+
+
+# ------------------------------------------------------------------ silicon spin qubits (Sec. 7, App. C)
+def si_compile(dev: Dict, ops: Sequence[NativeOp]) -> List[NativeOp]:
+    """Logical circuit -> native op list of the silicon device (Sec. 7, App. C).
+
+    The gates run one at a time. Readings, also used by the library:
+    - An x/y rotation by theta takes t = |theta| / (2 pi f_Rabi). A controlled phase theta takes
+      t = |theta| / (2 pi f_CZ), with CZ = CPh(pi).
+    - The off-resonant drive of a bystander j (Eq. off_resonant) uses the driven qubit's Rabi
+      frequency and the frequency difference |f_j - f_q| as a magnitude, both angular.
+    - The off-state crosstalk acts on every neighbour pair that does not contain the driven qubit,
+      once per x/y rotation. The on-state one acts on every other pair during a controlled phase:
+      controlled-Rz(delta[k][j] theta / pi), with row k the active pair and column j the passive pair.
+    - Passive qubits decay over each gate by Eq. (depolt1) then Eq. (depht2) (the idle_depol op).
+    - Rz is virtual: it takes no time and carries no noise.
+    """
+    n = int(dev["n"])
+    flags = int(dev.get("flags", 0))
+    passive, offres = not (flags & 1), not (flags & 2)
+    xon, xoff = dev.get("xtalk_on"), dev.get("xtalk_off")
+    out: List[NativeOp] = []
+
+    def bystander_decay(active, t):
+        if passive and t > 0:
+            for j in range(n):
+                if j not in active:
+                    out.append(NativeOp("idle_depol", (j,), (t, float(dev["t1"][j]), float(dev["t2"][j]))))
+
+    for op in ops:
+        if op.name == "rz":
+            out.append(op)
+        elif op.name in ("rx", "ry"):
+            q = op.qubits[0]
+            rabi = float(dev["rabi"][q])
+            t = abs(op.params[0]) / (2 * math.pi * rabi)
+            out.append(op)
+            out.append(NativeOp("stderr1", (q,), (float(dev["fid_1q"][q]), float(dev["x_1q"]))))
+            if offres and t > 0:
+                for j in range(n):
+                    if j != q:
+                        out.append(NativeOp("offres", (j,), (2 * math.pi * rabi,
+                                                             2 * math.pi * abs(dev["freq"][j] - dev["freq"][q]), t)))
+            bystander_decay((q,), t)
+            if xoff is not None:
+                for k in range(n - 1):
+                    if q not in (k, k + 1) and xoff[k] != 0:
+                        out.append(NativeOp("crz_xtalk", (k, k + 1), (float(xoff[k]),)))
+        elif op.name in ("cz", "cph"):
+            a, b = op.qubits
+            if abs(a - b) != 1:
+                raise ValueError("controlled phase on non-neighbours")
+            k = min(a, b)
+            theta = math.pi if op.name == "cz" else op.params[0]
+            t = abs(theta) / (2 * math.pi * float(dev["freq_cz"][k]))
+            out.append(op)
+            out.append(NativeOp("stderr2", (a, b), (float(dev["fid_cz"][k]), float(dev["x_cz"]))))
+            if xon is not None:
+                for j in range(n - 1):
+                    d = float(xon[k][j])
+                    if j != k and d != 0:
+                        out.append(NativeOp("crz_xtalk", (j, j + 1), (d * theta / math.pi,)))
+            bystander_decay((a, b), t)
+        else:
+            raise ValueError(f"{op.name} is not a silicon native gate")
+    return out

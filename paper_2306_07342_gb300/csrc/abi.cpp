@@ -723,6 +723,101 @@ int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, i
   API_END(nullptr)
 }
 
+// Silicon spin device compiler, Sec. 7 and the silicon table of App. C: gates run one at a time.
+// Rx/Ry: the standard error of Sec. 3.2 from the single-qubit fidelity, the off-resonant drive of
+// Eq. (off_resonant) on every other qubit, passive T1/T2 decay (Eqs. depolt1, depht2) of the other
+// qubits, and the off-state conditional-Rz crosstalk on the pairs of passive neighbours.  CZ/CPh on a
+// neighbour pair: its standard error, the on-state crosstalk controlled-Rz(delta theta / pi) on every
+// other neighbour pair, and the passive decay.  Rz is virtual: no time, no noise.
+int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, int cap, vqd_native_op* out,
+                   int* nout) {
+  API_BEGIN
+  if (!dev || !nout || nin < 0 || (nin > 0 && !in) || (out && cap < 0)) throw Error(VQD_EINVAL, "bad argument");
+  const int n = dev->n;
+  if (n < 2 || n > 32) throw Error(VQD_EINVAL, "bad device: qubit count");
+  if (!dev->t1 || !dev->t2 || !dev->freq || !dev->rabi || !dev->fid_1q || !dev->freq_cz || !dev->fid_cz)
+    throw Error(VQD_EINVAL, "bad device: NULL table");
+  for (int j = 0; j < n; j++)
+    if (!(dev->t1[j] > 0) || !(dev->t2[j] > 0) || !(dev->rabi[j] > 0) || !(dev->fid_1q[j] > 0 && dev->fid_1q[j] <= 1))
+      throw Error(VQD_EINVAL, "bad device: T1, T2, Rabi frequency or fidelity");
+  for (int k = 0; k + 1 < n; k++)
+    if (!(dev->freq_cz[k] > 0) || !(dev->fid_cz[k] > 0 && dev->fid_cz[k] <= 1))
+      throw Error(VQD_EINVAL, "bad device: CZ frequency or fidelity");
+  if (!(dev->x_1q >= 0 && dev->x_1q <= 1 && dev->x_cz >= 0 && dev->x_cz <= 1))
+    throw Error(VQD_EINVAL, "bad device: depolarising fraction outside [0,1]");
+  const bool passive = !(dev->flags & VQD_SI_NO_PASSIVE), offres = !(dev->flags & VQD_SI_NO_OFFRES);
+  const double two_pi = 2 * 3.14159265358979323846;
+  int cnt = 0;
+  auto put = [&](const vqd_native_op& o) {
+    if (out) {
+      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+      out[cnt] = o;
+    }
+    cnt++;
+  };
+  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
+    vqd_native_op o;
+    std::memset(&o, 0, sizeof(o));
+    o.code = code;
+    o.nq = q1 < 0 ? 1 : 2;
+    o.q[0] = q0;
+    o.q[1] = q1 < 0 ? 0 : q1;
+    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
+    put(o);
+  };
+  auto decay_others = [&](int a, int b, double t) {  // passive qubits over the gate's duration
+    if (!passive || t <= 0) return;
+    for (int j = 0; j < n; j++)
+      if (j != a && j != b) emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
+  };
+  for (int i = 0; i < nin; i++) {
+    const vqd_native_op& o = in[i];
+    const int ar = native_arity(o.code);
+    if (ar < 1 || o.nq != ar) throw Error(VQD_EINVAL, "bad op at index " + std::to_string(i));
+    for (int j = 0; j < ar; j++)
+      if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
+        throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
+    if (o.code == VQD_OP_RZ) {  // virtual
+      put(o);
+      continue;
+    }
+    if (o.code == VQD_OP_RX || o.code == VQD_OP_RY) {
+      const int q = o.q[0];
+      const double t = std::fabs(o.par[0]) / (two_pi * dev->rabi[q]);  // rotation angle 2 pi f_Rabi t
+      put(o);
+      emit(VQD_OP_STDERR1, q, -1, dev->fid_1q[q], dev->x_1q, 0);
+      if (offres && t > 0)
+        for (int j = 0; j < n; j++)
+          if (j != q)
+            emit(VQD_OP_OFFRES, j, -1, two_pi * dev->rabi[q], two_pi * std::fabs(dev->freq[j] - dev->freq[q]), t);
+      decay_others(q, -1, t);
+      if (dev->xtalk_off)
+        for (int k = 0; k + 1 < n; k++)
+          if (k != q && k + 1 != q && dev->xtalk_off[k] != 0) emit(VQD_OP_CRZ_XTALK, k, k + 1, dev->xtalk_off[k], 0, 0);
+      continue;
+    }
+    if (o.code == VQD_OP_CZ || o.code == VQD_OP_CPH) {
+      const int a = o.q[0], b = o.q[1];
+      if (std::abs(a - b) != 1) throw Error(VQD_EINVAL, "controlled phase on non-neighbours at op " + std::to_string(i));
+      const int k = std::min(a, b);
+      const double theta = o.code == VQD_OP_CZ ? 3.14159265358979323846 : o.par[0];
+      const double t = std::fabs(theta) / (two_pi * dev->freq_cz[k]);  // conditional phase 2 pi f_CZ t
+      put(o);
+      emit(VQD_OP_STDERR2, a, b, dev->fid_cz[k], dev->x_cz, 0);
+      if (dev->xtalk_on)
+        for (int j = 0; j + 1 < n; j++) {
+          const double d = dev->xtalk_on[k * (n - 1) + j];
+          if (j != k && d != 0) emit(VQD_OP_CRZ_XTALK, j, j + 1, d * theta / 3.14159265358979323846, 0, 0);
+        }
+      decay_others(a, b, t);
+      continue;
+    }
+    throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a silicon native gate");
+  }
+  *nout = cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");

@@ -54,6 +54,18 @@ VQD_SC_NO_PASSIVE = 1
 VQD_SC_NO_STATIC_ZZ = 2
 
 
+class si_device(ctypes.Structure):
+    """vqd_si_device: silicon spin-qubit device table."""
+    _fields_ = [("n", ctypes.c_int32), ("t1", ctypes.c_void_p), ("t2", ctypes.c_void_p), ("freq", ctypes.c_void_p),
+                ("rabi", ctypes.c_void_p), ("fid_1q", ctypes.c_void_p), ("x_1q", ctypes.c_double),
+                ("freq_cz", ctypes.c_void_p), ("fid_cz", ctypes.c_void_p), ("x_cz", ctypes.c_double),
+                ("xtalk_on", ctypes.c_void_p), ("xtalk_off", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+VQD_SI_NO_PASSIVE = 1
+VQD_SI_NO_OFFRES = 2
+
+
 class VQDError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libvqd error {code}: {msg}")
@@ -109,6 +121,7 @@ def lib() -> ctypes.CDLL:
             "vqd_batch_reduce": (I, [P, P, P, P]),
             "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
             "vqd_sc_compile": (I, [P, I, P, I, I, P, P]),
+            "vqd_si_compile": (I, [P, I, P, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -304,6 +317,26 @@ def vqd_sc_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
     out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
     _check(lib().vqd_sc_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
                                 ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def vqd_si_compile(dev: dict, ops) -> np.ndarray:
+    """Compile a logical Rx/Ry/Rz/CZ/CPh circuit for a silicon device (host only).  ``dev`` holds n, t1, t2,
+    freq, rabi, fid_1q, x_1q, freq_cz, fid_cz, x_cz, xtalk_on ((n-1) x (n-1) or None), xtalk_off (or None)
+    and optional flags.  Returns the native-op array."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    keep = {}
+    for k in ("t1", "t2", "freq", "rabi", "fid_1q", "freq_cz", "fid_cz", "xtalk_on", "xtalk_off"):
+        v = dev.get(k)
+        keep[k] = None if v is None else np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+    p = lambda k: None if keep[k] is None else _ptr(keep[k])
+    d = si_device(int(dev["n"]), p("t1"), p("t2"), p("freq"), p("rabi"), p("fid_1q"), float(dev["x_1q"]),
+                  p("freq_cz"), p("fid_cz"), float(dev["x_cz"]), p("xtalk_on"), p("xtalk_off"),
+                  int(dev.get("flags", 0)))
+    cnt = ctypes.c_int()
+    _check(lib().vqd_si_compile(ctypes.byref(d), len(a), _ptr(a), 0, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
+    _check(lib().vqd_si_compile(ctypes.byref(d), len(a), _ptr(a), cnt.value, _ptr(out), ctypes.byref(cnt)))
     return out[: cnt.value].copy()
 
 

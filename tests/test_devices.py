@@ -163,3 +163,91 @@ def test_compiled_program_gpu_parity(vqd, dev_name):
             assert np.abs(got - want).max() < TOL_F64, runner
         finally:
             vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- silicon spin qubits (Sec. 7, App. C)
+from oracle.devices import si_compile  # noqa: E402
+from workloads.devices import SI6, si_circuit  # noqa: E402
+
+
+def small_si(**kw):
+    dev = {"n": 3, "t1": [1e4, 2e4, 3e4], "t2": [20.0, 30.0, 40.0], "freq": [15600.0, 15900.0, 16300.0],
+           "rabi": [5.0, 4.0, 6.0], "fid_1q": [0.998, 0.997, 0.999], "x_1q": 0.25, "freq_cz": [12.0, 8.0],
+           "fid_cz": [0.95, 0.97], "x_cz": 0.5, "xtalk_on": [[0.0, 0.02], [0.04, 0.0]], "xtalk_off": [0.03, 0.01]}
+    dev.update(kw)
+    return dev
+
+
+def test_si_worked_example_by_hand(vqd):
+    """Rx(pi/2) on q1 (Rabi 4 MHz: t = 1/16 us); CZ on (0,1) (12 MHz: t = 1/24 us); virtual Rz on q2."""
+    dev = small_si()
+    ops = [NativeOp("rx", (1,), (math.pi / 2,)), NativeOp("cz", (0, 1)), NativeOp("rz", (2,), (0.4,))]
+    t1, t2 = 1 / 16, 1 / 24
+    w = 2 * math.pi
+    want = [ops[0], NativeOp("stderr1", (1,), (0.997, 0.25)),
+            NativeOp("offres", (0,), (w * 4.0, w * 300.0, t1)), NativeOp("offres", (2,), (w * 4.0, w * 400.0, t1)),
+            NativeOp("idle_depol", (0,), (t1, 1e4, 20.0)), NativeOp("idle_depol", (2,), (t1, 3e4, 40.0)),
+            ops[1], NativeOp("stderr2", (0, 1), (0.95, 0.5)), NativeOp("crz_xtalk", (1, 2), (0.02,)),
+            NativeOp("idle_depol", (2,), (t2, 3e4, 40.0)), ops[2]]
+    same_ops(si_compile(dev, ops), want, 1e-13)
+    same_ops(as_ops(vqd, vqd.vqd_si_compile(dev, ops)), want, 1e-12)
+    # off-state crosstalk: a rotation on q0 leaves the pair (1, 2) passive
+    out = si_compile(dev, [NativeOp("ry", (0,), (1.0,))])
+    assert [o for o in out if o.name == "crz_xtalk"] == [NativeOp("crz_xtalk", (1, 2), (0.01,))]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_si_library_matches_oracle(vqd, seed):
+    for dev in (SI6, dict(SI6, flags=seed, xtalk_on=None if seed == 1 else SI6["xtalk_on"]), small_si(flags=3 - seed)):
+        ops = si_circuit(dev, 50, seed=seed)
+        same_ops(as_ops(vqd, vqd.vqd_si_compile(dev, ops)), si_compile(dev, ops), 1e-12)
+
+
+def test_si_off_resonant_rabi_population():
+    """A bystander in |0> under the off-resonant drive of an Rx(theta) on its neighbour ends with the detuned
+    Rabi population (Omega/Omega_R)^2 sin^2(Omega_R t/2), Omega = 2 pi f_Rabi, Omega_R^2 = Omega^2 + Delta^2,
+    t = theta/Omega; at zero detuning it follows the driven qubit: sin^2(theta/2)."""
+    for df, theta in [(12.0, 2.5), (3.0, 1.1), (0.0, 0.8)]:
+        dev = small_si(n=2, freq=[15600.0, 15600.0 + df], rabi=[5.0, 5.0], fid_1q=[1.0, 1.0], freq_cz=[10.0],
+                       fid_cz=[1.0], xtalk_on=None, xtalk_off=None, flags=1)
+        rho = evolve.run_program(Program(2, si_compile(dev, [NativeOp("rx", (0,), (theta,))])))
+        om, de = 2 * math.pi * 5.0, 2 * math.pi * df
+        om_r = math.hypot(om, de)
+        want = (om / om_r) ** 2 * math.sin(om_r * (theta / om) / 2) ** 2
+        assert abs(measure.probs(rho, [1])[1] - want) < 1e-13
+        assert abs(measure.probs(rho, [0])[1] - math.sin(theta / 2) ** 2) < 1e-13
+
+
+def test_si_single_qubit_error_is_dephasing_of_the_tabulated_fidelity():
+    """With the table's 0:1 split (pure dephasing), each x/y gate multiplies the coherence by 1 - 2p with
+    p = 1 - F_e and F_e = (3F - 1)/2 (App. B): Ry(pi/2) then Rx(0) leave <X> = (3F - 2)^2."""
+    F = 0.9977
+    dev = small_si(n=2, fid_1q=[F, 1.0], x_1q=0.0, freq_cz=[10.0], fid_cz=[1.0], xtalk_on=None, xtalk_off=None,
+                   flags=3)
+    rho = evolve.run_program(Program(2, si_compile(dev, [NativeOp("ry", (0,), (math.pi / 2,)),
+                                                         NativeOp("rx", (0,), (0.0,))])))
+    assert abs(measure.expect(rho, [[1, 0]], [1.0]) - (3 * F - 2) ** 2) < 1e-13
+
+
+def test_si_rejects_bad_input(vqd):
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_si_compile(small_si(), [NativeOp("cz", (0, 2))])      # not neighbours
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_si_compile(small_si(), [NativeOp("h", (0,))])
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_si_compile(small_si(rabi=[5.0, 0.0, 6.0]), [NativeOp("rx", (0,), (0.1,))])
+
+
+@pytest.mark.gpu
+def test_si_compiled_program_gpu_parity(vqd):
+    ops = si_circuit(SI6, 60, seed=12)
+    lib_ops = vqd.vqd_si_compile(SI6, ops)
+    want = evolve.run_program(Program(6, si_compile(SI6, ops)))
+    for runner in ("plain", "fused"):
+        ctx = vqd.vqd_create(6, vqd.VQD_F64)
+        try:
+            (vqd.vqd_apply_native if runner == "plain" else vqd.vqd_run_program)(ctx, 0, lib_ops)
+            got = vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0))
+            assert np.abs(got - want).max() < TOL_F64, runner
+        finally:
+            vqd.vqd_destroy(ctx)

@@ -67,3 +67,42 @@ def sc_ansatz(dev: Dict, depth: int, seed: int = 3, sizzle_every: int = 3) -> Li
             name = "zz" if sizzle_every and layer % sizzle_every == sizzle_every - 1 else "zx"
             ops.append(NativeOp(name, (c, t), (math.pi / 2,)))
     return ops
+
+
+SI6 = {  # App. C, table of the virtual silicon qubits (MHz, us); ratios depolarising:dephasing 0:1
+    "n": 6,
+    "t1": [1e4] * 6,
+    "t2": [14.0, 21.1, 40.1, 37.2, 44.7, 26.7],
+    "freq": [15.62e3, 15.88e3, 16.3e3, 16.1e3, 15.9e3, 15.69e3],
+    "rabi": [5.0] * 6,
+    "fid_1q": [0.9977, 0.9987, 0.9996, 0.9988, 0.9991, 0.9989],
+    "x_1q": 0.0,
+    "freq_cz": [12.1, 11.1, 6.6, 9.8, 5.4],
+    "fid_cz": [0.937, 0.934, 0.929, 0.997, 0.979],
+    "x_cz": 0.0,
+    "xtalk_on": [[0, 0.023, 0.018, 0.03, 0.04],
+                 [0.05, 0, 0.03, 0.03, 0.04],
+                 [0.05, 0.03, 0, 0.07, 0.042],
+                 [0.038, 0.03, 0.031, 0, 0.25],
+                 [0.033, 0.03, 0.02, 0.03, 0]],
+    "xtalk_off": [0.039, 0.015, 0.03, 0.02, 0.028],
+}
+
+
+def si_circuit(dev: Dict, n_gates: int, seed: int = 9) -> List[NativeOp]:
+    """Random circuit in the silicon native gates: Rx, Ry (angles up to pi), virtual Rz, and CZ or CPh
+    on neighbour pairs, about one two-qubit gate in three."""
+    r = _rng(seed)
+    n = int(dev["n"])
+    ops: List[NativeOp] = []
+    for _ in range(n_gates):
+        u = r.uniform()
+        if u < 1 / 3:
+            k = int(r.integers(0, n - 1))
+            pair = (k, k + 1) if r.uniform() < 0.5 else (k + 1, k)
+            ops.append(NativeOp("cz", pair) if r.uniform() < 0.5
+                       else NativeOp("cph", pair, (float(r.uniform(0.1, math.pi)),)))
+        else:
+            name = ("rx", "ry", "rz")[int(r.integers(0, 3))]
+            ops.append(NativeOp(name, (int(r.integers(0, n)),), (float(r.uniform(-math.pi, math.pi)),)))
+    return ops
