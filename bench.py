@@ -190,6 +190,35 @@ def measure_trajectories(vqd, torch, prog, native, stream_handle, ntraj=1024):
             "z_score": (mean - exact) / se if se > 0 else None}
 
 
+def measure_sc_device(vqd, torch, stream_handle, timed, steps):
+    """A second workload: the superconducting device model of Sec. 8 on a 2x7 transmon grid (App. C
+    parameter ranges), a depth-60 hardware-efficient ansatz compiled by vqd_sc_compile (static ZZ on every
+    coupling, thermal T1/T2 decay, readout noise), run through the fused path in complex64 from the
+    thermal initial state."""
+    from workloads.devices import sc_ansatz, sc_grid_device
+    dev = sc_grid_device(2, 7)
+    logical = sc_ansatz(dev, 60)
+    t0 = time.perf_counter()
+    native = vqd.vqd_sc_compile(dev, logical, readout=True)
+    compile_s = time.perf_counter() - t0
+    n = int(dev["n"])
+    ctx = vqd.vqd_create(n, vqd.VQD_F32, stream_handle)
+    try:
+        def step():
+            vqd.vqd_init_product_diag(ctx, 0, dev["excited"])
+            vqd.vqd_run_program(ctx, 0, native)
+            vqd.vqd_prob(ctx, 0, list(range(n)))
+            vqd.vqd_trace(ctx, 0)
+        ms, st, _ = timed(step, steps, 1, ctx)
+        units = len(native) * 4.0 ** n
+        return {"value": steps * units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                "logical_gates": len(logical), "native_ops": len(native), "host_compile_s": compile_s,
+                "stages_per_step": st.get("fused_stage", {}).get("launches", 0) // steps,
+                "note": "fused path, default fusion width 6; amp-updates counted over the compiled native ops"}
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
 def measure_batch(vqd, torch, stream_handle, count):
     """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of
     persistent kernels), against one launch sequence per instance (fused and plain) on a sample."""
@@ -494,6 +523,7 @@ def main():
 
     if not args.no_extra:
         extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
+        extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed, args.steps)
 
     if not args.no_extra and args.batch_count > 0:
         extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)
