@@ -190,6 +190,29 @@ def measure_trajectories(vqd, torch, prog, native, stream_handle, ntraj=1024):
             "z_score": (mean - exact) / se if se > 0 else None}
 
 
+def measure_trajectories_spin16(vqd, stream_handle, ntraj=256):
+    """Trajectories where the density matrix is 34 GB: the 16-qubit spin chain (4000 native ops) as
+    complex64 statevectors of 512 KB, each spread over a cluster of 8 CTAs (distributed shared memory).
+    Reported: <sum_q Z_q> with its standard error, and throughput."""
+    import numpy as np
+    from workloads import config5_spin_chain
+    prog = config5_spin_chain()
+    n = prog.n
+    native = vqd.native_ops(prog.ops)
+    codes = np.zeros((n, n), np.uint8)
+    for q in range(n):
+        codes[q, q] = 3
+    coeffs = np.ones(n)
+    vqd.vqd_traj_expect(n, vqd.VQD_F32, native[:50], 8, 1, codes, coeffs, 0, stream_handle)   # warm-up
+    t0 = time.perf_counter()
+    vals, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F32, native, ntraj, 2025, codes, coeffs, 0, stream_handle)
+    wall = time.perf_counter() - t0
+    return {"trajectories": ntraj, "seconds": wall, "trajectories_per_s": ntraj / wall,
+            "statevector_amp_updates_per_s": ntraj * len(native) * 2.0 ** n / wall,
+            "native_ops": len(native), "observable": "sum_q Z_q", "mean": mean, "stderr": se,
+            "note": "16-qubit statevectors on 8-CTA clusters; the density matrix (34 GB) is the plain path's"}
+
+
 def measure_sc_device(vqd, torch, stream_handle, timed, steps):
     """A second workload: the superconducting device model of Sec. 8 on a 2x7 transmon grid (App. C
     parameter ranges), a depth-60 hardware-efficient ansatz compiled by vqd_sc_compile (static ZZ on every
@@ -524,6 +547,7 @@ def main():
     if not args.no_extra:
         extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
         extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed, args.steps)
+        extra["trajectories_spin16_c64"] = measure_trajectories_spin16(vqd, sh)
 
     if not args.no_extra and args.batch_count > 0:
         extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)

@@ -358,11 +358,13 @@ int vqd_set_state(vqd_t ctx, int inst, const vqd_c128* host_in);
  * as a 53-bit uniform u = (w0 >> 5) 2^-27 + (w1 >> 6) 2^-53; operator k is chosen when
  * sum_{j<k} p_j <= u < sum_{j<=k} p_j.
  *
- * n <= 14 (VQD_F32) or 13 (VQD_F64): every trajectory keeps its statevector in shared memory.
+ * 1 <= n <= 16.  Every trajectory keeps its statevector in shared memory: in one CTA up to n = 14
+ * (VQD_F32) or 13 (VQD_F64), beyond that split over a thread-block cluster of up to 8 CTAs (slices
+ * of 64 KB, 128 KB for 16 qubits in VQD_F64) joined by distributed shared memory.
  * paulis is nterms x n codes (0=I,1=X,2=Y,3=Z) as in vqd_expect.  out (host, ntraj) receives each
  * trajectory's value; mean and stderr_out (either may be NULL) the sample mean and its standard
- * error.  Synchronous on `stream`.  Returns VQD_ENOTSUP for n above the limit or more than 16
- * state-dependent Kraus operators in one channel; messages via vqd_last_error(NULL). */
+ * error.  Synchronous on `stream`.  Returns VQD_EINVAL for n outside 1..16, VQD_ENOTSUP for more
+ * than 16 state-dependent Kraus operators in one channel; messages via vqd_last_error(NULL). */
 int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* ops, unsigned flags, int ntraj, uint64_t seed,
                     int nterms, const uint8_t* paulis, const double* coeffs, void* stream, double* out,
                     double* mean, double* stderr_out);

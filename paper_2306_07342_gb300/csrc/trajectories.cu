@@ -8,13 +8,18 @@
 // trajectory is lost and contributes 0, so the mean still estimates Re tr(H rho).
 //
 // One CTA runs one trajectory at a time with the whole statevector in shared memory (2^n
-// amplitudes: n <= 14 for complex64, n <= 13 for complex128).  The random number of channel o in
+// amplitudes: n <= 14 for complex64, n <= 13 for complex128).  Larger statevectors (up to 16 qubits)
+// are spread over the CTAs of a thread-block cluster, 2^c CTAs with one slice each, and reached
+// across CTAs through distributed shared memory; every operator's groups are split evenly over the
+// cluster, each group read and written by one thread, with a cluster barrier between operators.  The random number of channel o in
 // trajectory t is the first Philox4x32-10 output for counter (o, t, 0, 0) and key = the seed
 // (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011); the same
 // draws can therefore be reproduced anywhere.  Channels whose Kraus operators are all multiples
 // of unitaries have state-independent probabilities and skip the norm computation.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -87,13 +92,34 @@ __device__ __forceinline__ cx<T> cmadd(cx<T> acc, const cx<T>& c, const cx<T>& x
 
 __device__ __forceinline__ uint32_t ins0(uint32_t g, int p) { return g + (g & ~((1u << p) - 1u)); }
 
-// psi <- scale * K psi on the op's qubits (K is d x d, row-major, index little-endian over q)
+// The statevector in this CTA's shared memory.
 template <class T>
-__device__ void apply_op(cx<T>* __restrict__ psi, int n, const TrajOp& op, const cx<T>* __restrict__ K, T scale) {
+struct LocalPsi {
+  cx<T>* p;
+  __device__ __forceinline__ cx<T>& operator[](uint32_t i) const { return p[i]; }
+};
+
+// The statevector spread over a cluster: amplitude i is at offset i & mask of the slice of CTA rank
+// i >> shift (distributed shared memory for the other ranks).
+template <class T>
+struct ClusterPsi {
+  cx<T>* p;
+  int shift;
+  uint32_t mask;
+  __device__ __forceinline__ cx<T>& operator[](uint32_t i) const {
+    return *cooperative_groups::this_cluster().map_shared_rank(p + (i & mask), i >> shift);
+  }
+};
+
+// psi <- scale * K psi on the op's qubits (K is d x d, row-major, index little-endian over q), for the
+// groups g0 <= g < g1 (a group: the d amplitudes that differ only on the op's qubits)
+template <class T, class Psi>
+__device__ void apply_op(const Psi& psi, const TrajOp& op, const cx<T>* __restrict__ K, T scale, uint32_t g0,
+                         uint32_t g1) {
   if (op.k == 1) {
     const uint32_t m = 1u << op.q[0];
     const cx<T> a = K[0], b = K[1], c = K[2], d = K[3];
-    for (uint32_t g = threadIdx.x; g < (1u << (n - 1)); g += kTrajThreads) {
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += kTrajThreads) {
       const uint32_t i0 = ins0(g, op.q[0]);
       const cx<T> x0 = psi[i0], x1 = psi[i0 | m];
       cx<T> y0, y1;
@@ -110,7 +136,7 @@ __device__ void apply_op(cx<T>* __restrict__ psi, int n, const TrajOp& op, const
     cx<T> U[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) U[i] = K[i];
-    for (uint32_t g = threadIdx.x; g < (1u << (n - 2)); g += kTrajThreads) {
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += kTrajThreads) {
       const uint32_t b = ins0(ins0(g, lo), hi);
       const uint32_t idx[4] = {b, b | m0, b | m1, b | m0 | m1};
       cx<T> x[4];
@@ -130,16 +156,17 @@ __device__ void apply_op(cx<T>* __restrict__ psi, int n, const TrajOp& op, const
   }
 }
 
-// p[k] = ||K_k psi||^2 for k < nK (FP64 accumulation); result in red[0..nK)
-template <class T>
-__device__ void kraus_norms(const cx<T>* __restrict__ psi, int n, const TrajOp& op, const cx<T>* __restrict__ Ks,
+// p[k] = ||K_k psi||^2 restricted to the groups g0 <= g < g1, for k < nK (FP64 accumulation, fixed
+// order); this CTA's sums in red[0..nK)
+template <class T, class Psi>
+__device__ void kraus_norms(const Psi& psi, const TrajOp& op, const cx<T>* __restrict__ Ks, uint32_t g0, uint32_t g1,
                             double* __restrict__ red) {
   double acc[kMaxKraus];
 #pragma unroll
   for (int j = 0; j < kMaxKraus; j++) acc[j] = 0.0;
   if (op.k == 1) {
     const uint32_t m = 1u << op.q[0];
-    for (uint32_t g = threadIdx.x; g < (1u << (n - 1)); g += kTrajThreads) {
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += kTrajThreads) {
       const uint32_t i0 = ins0(g, op.q[0]);
       const cx<T> x0 = psi[i0], x1 = psi[i0 | m];
 #pragma unroll
@@ -156,7 +183,7 @@ __device__ void kraus_norms(const cx<T>* __restrict__ psi, int n, const TrajOp& 
   } else {
     const int lo = min(op.q[0], op.q[1]), hi = max(op.q[0], op.q[1]);
     const uint32_t m0 = 1u << op.q[0], m1 = 1u << op.q[1];
-    for (uint32_t g = threadIdx.x; g < (1u << (n - 2)); g += kTrajThreads) {
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += kTrajThreads) {
       const uint32_t b = ins0(ins0(g, lo), hi);
       const cx<T> x[4] = {psi[b], psi[b | m0], psi[b | m1], psi[b | m0 | m1]};
 #pragma unroll
@@ -193,6 +220,134 @@ __device__ void kraus_norms(const cx<T>* __restrict__ psi, int n, const TrajOp& 
   __syncthreads();
 }
 
+// One CTA (CtaTeam) or the CTAs of a cluster (ClusterTeam) working on one statevector.  combine()
+// turns each CTA's block sums v[0..cnt) into the team's totals, summed in rank order so that every
+// CTA holds bit-identical values (and so takes the same random branch).
+struct CtaTeam {
+  int rank, c;
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void combine(double*, int) const {}
+};
+struct ClusterTeam {
+  double* part;  // [8][kMaxKraus] partial sums; rank 0's copy gathers them
+  int rank, c;
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  __device__ void combine(double* v, int cnt) const {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    if (threadIdx.x < (unsigned)cnt) *cl.map_shared_rank(part + rank * kMaxKraus + threadIdx.x, 0) = v[threadIdx.x];
+    cl.sync();
+    if (threadIdx.x < (unsigned)cnt) {
+      double acc = 0.0;
+      for (int r = 0; r < (1 << c); r++) acc += *cl.map_shared_rank(part + r * kMaxKraus + threadIdx.x, 0);
+      v[threadIdx.x] = acc;
+    }
+    cl.sync();  // rank 0's gather area is reused only after every CTA has read it
+  }
+};
+
+struct TrajShared {
+  double red[kMaxKraus];
+  double part[8 * kMaxKraus];
+  double warp[kTrajThreads / 32][2];
+  double scale;
+  int choice;
+};
+
+// One trajectory from |0...0>; returns Re <psi|H|psi> (0 if the trajectory was lost), valid in thread
+// 0 of every CTA of the team.  This CTA holds amplitudes [rank * len, (rank + 1) * len) in `slice`.
+template <class T, class Psi, class Team>
+__device__ double one_trajectory(const Psi& psi, const Team& team, cx<T>* __restrict__ slice, uint32_t len, int n,
+                                 const TrajOp* __restrict__ ops, int nops, const cx<T>* __restrict__ coef,
+                                 const double* __restrict__ wts, uint64_t seed, int t,
+                                 const PauliTerm* __restrict__ terms, int nterms, TrajShared& sh) {
+  for (uint32_t i = threadIdx.x; i < len; i += kTrajThreads) {
+    cx<T> z;
+    z.x = (team.rank == 0 && i == 0) ? (T)1 : (T)0;
+    z.y = 0;
+    slice[i] = z;
+  }
+  team.sync();
+  for (int o = 0; o < nops; o++) {
+    const TrajOp op = ops[o];
+    const int dd = op.k == 1 ? 4 : 16;
+    const uint32_t per = (1u << (n - op.k)) >> team.c, g0 = team.rank * per, g1 = g0 + per;
+    if (op.kind == TJ_UNITARY) {
+      apply_op<T>(psi, op, coef + op.coef, (T)1, g0, g1);
+      team.sync();
+      continue;
+    }
+    if (op.kind == TJ_KRAUS) {
+      kraus_norms<T>(psi, op, coef + op.coef, g0, g1, sh.red);
+      team.combine(sh.red, op.nK);
+    }
+    if (threadIdx.x == 0) {
+      const double u = draw_uniform(seed, (uint32_t)o, (uint32_t)t);
+      double cum = 0.0, pk = 0.0;
+      int choice = -1;
+      for (int j = 0; j < op.nK; j++) {
+        const double p = op.kind == TJ_MIXTURE ? wts[op.wofs + j] : sh.red[j];
+        cum += p;
+        if (u < cum) {
+          choice = j;
+          pk = p;
+          break;
+        }
+      }
+      sh.choice = choice;
+      sh.scale = (op.kind == TJ_KRAUS && choice >= 0) ? 1.0 / sqrt(pk) : 1.0;
+    }
+    __syncthreads();
+    const int choice = sh.choice;
+    if (choice < 0) return 0.0;  // the trajectory left the computational space (trace-decreasing branch)
+    apply_op<T>(psi, op, coef + op.coef + dd * choice, (T)sh.scale, g0, g1);
+    team.sync();
+  }
+  // <psi|H|psi> = sum_t c_t i^{ny} sum_x (-1)^{popc(x & zy)} conj(psi[x ^ xm]) psi[x], x over this CTA's slice
+  double total = 0.0;
+  const uint32_t x0 = team.rank * len;
+  for (int j = 0; j < nterms; j++) {
+    const PauliTerm P = terms[j];
+    double re = 0.0, im = 0.0;
+    for (uint32_t x = x0 + threadIdx.x; x < x0 + len; x += kTrajThreads) {
+      const cx<T> a = psi[x ^ P.xm], b = slice[x - x0];
+      const double sg = (__popc(x & P.zy) & 1) ? -1.0 : 1.0;
+      re += sg * ((double)a.x * b.x + (double)a.y * b.y);
+      im += sg * ((double)a.x * b.y - (double)a.y * b.x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sh.warp[threadIdx.x >> 5][0] = re;
+      sh.warp[threadIdx.x >> 5][1] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0, si = 0;
+      for (int w = 0; w < kTrajThreads / 32; w++) {
+        sr += sh.warp[w][0];
+        si += sh.warp[w][1];
+      }
+      sh.red[0] = sr;
+      sh.red[1] = si;
+    }
+    __syncthreads();
+    team.combine(sh.red, 2);
+    if (threadIdx.x == 0) {
+      // times i^{ny}: real part of (sr + i si) i^ny
+      const double sr = sh.red[0], si = sh.red[1];
+      const int r = P.ny & 3;
+      const double v = r == 0 ? sr : r == 1 ? -si : r == 2 ? -sr : si;
+      total += P.c * v;
+    }
+    __syncthreads();
+  }
+  return total;
+}
+
+// Whole statevector in this CTA's shared memory.
 template <class T>
 __global__ void __launch_bounds__(kTrajThreads) k_traj(const TrajOp* __restrict__ ops, int nops,
                                                       const cx<T>* __restrict__ coef, const double* __restrict__ wts,
@@ -201,99 +356,49 @@ __global__ void __launch_bounds__(kTrajThreads) k_traj(const TrajOp* __restrict_
                                                       double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* psi = reinterpret_cast<cx<T>*>(smraw);
-  __shared__ double red[kMaxKraus];
-  __shared__ int s_choice;
-  __shared__ double s_scale;
-  __shared__ double s_part[kTrajThreads / 32][2];
-  const uint32_t dim = 1u << n;
+  __shared__ TrajShared sh;
+  const CtaTeam team{0, 0};
+  const LocalPsi<T> P{psi};
   for (int t = blockIdx.x; t < ntraj; t += gridDim.x) {
-    for (uint32_t i = threadIdx.x; i < dim; i += kTrajThreads) {
-      cx<T> z;
-      z.x = (i == 0) ? (T)1 : (T)0;
-      z.y = 0;
-      psi[i] = z;
-    }
+    const double v = one_trajectory<T>(P, team, psi, 1u << n, n, ops, nops, coef, wts, seed, t, terms, nterms, sh);
+    if (threadIdx.x == 0) out[t] = v;
     __syncthreads();
-    bool alive = true;
-    for (int o = 0; o < nops && alive; o++) {
-      const TrajOp op = ops[o];
-      const int dd = op.k == 1 ? 4 : 16;
-      if (op.kind == TJ_UNITARY) {
-        apply_op<T>(psi, n, op, coef + op.coef, (T)1);
-        __syncthreads();
-        continue;
-      }
-      if (op.kind == TJ_KRAUS) kraus_norms<T>(psi, n, op, coef + op.coef, red);
-      if (threadIdx.x == 0) {
-        const double u = draw_uniform(seed, (uint32_t)o, (uint32_t)t);
-        double cum = 0.0;
-        int choice = -1;
-        double pk = 0.0;
-        for (int j = 0; j < op.nK; j++) {
-          const double p = op.kind == TJ_MIXTURE ? wts[op.wofs + j] : red[j];
-          cum += p;
-          if (u < cum) {
-            choice = j;
-            pk = p;
-            break;
-          }
-        }
-        s_choice = choice;
-        s_scale = (op.kind == TJ_KRAUS && choice >= 0) ? 1.0 / sqrt(pk) : 1.0;
-      }
-      __syncthreads();
-      const int choice = s_choice;
-      if (choice < 0) {  // the trajectory left the computational space (trace-decreasing branch)
-        alive = false;
-        break;
-      }
-      apply_op<T>(psi, n, op, coef + op.coef + dd * choice, (T)s_scale);
-      __syncthreads();
-    }
-    // <psi|H|psi> = sum_t c_t i^{ny} sum_x (-1)^{popc(x & zy)} conj(psi[x ^ xm]) psi[x]
-    double total = 0.0;
-    if (alive) {
-      for (int j = 0; j < nterms; j++) {
-        const PauliTerm P = terms[j];
-        double re = 0.0, im = 0.0;
-        for (uint32_t x = threadIdx.x; x < dim; x += kTrajThreads) {
-          const cx<T> a = psi[x ^ P.xm], b = psi[x];
-          const double sg = (__popc(x & P.zy) & 1) ? -1.0 : 1.0;
-          re += sg * ((double)a.x * b.x + (double)a.y * b.y);
-          im += sg * ((double)a.x * b.y - (double)a.y * b.x);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          re += __shfl_down_sync(0xffffffffu, re, o);
-          im += __shfl_down_sync(0xffffffffu, im, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-          s_part[threadIdx.x >> 5][0] = re;
-          s_part[threadIdx.x >> 5][1] = im;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double sr = 0, si = 0;
-          for (int w = 0; w < kTrajThreads / 32; w++) {
-            sr += s_part[w][0];
-            si += s_part[w][1];
-          }
-          // times i^{ny}: real part of (sr + i si) i^ny
-          const int r = P.ny & 3;
-          const double v = r == 0 ? sr : r == 1 ? -si : r == 2 ? -sr : si;
-          total += P.c * v;
-        }
-        __syncthreads();
-      }
-    }
-    if (threadIdx.x == 0) out[t] = alive ? total : 0.0;
-    __syncthreads();
+  }
+}
+
+// Statevector spread over a cluster of 2^c CTAs (launched with that cluster shape): CTA rank r of
+// cluster k holds amplitudes [r 2^{n-c}, (r+1) 2^{n-c}) of trajectory k, k + clusters, ...
+template <class T>
+__global__ void __launch_bounds__(kTrajThreads) k_traj_cluster(const TrajOp* __restrict__ ops, int nops,
+                                                              const cx<T>* __restrict__ coef,
+                                                              const double* __restrict__ wts, uint64_t seed, int ntraj,
+                                                              int n, const PauliTerm* __restrict__ terms, int nterms,
+                                                              double* __restrict__ out, int c) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<T>* slice = reinterpret_cast<cx<T>*>(smraw);
+  __shared__ TrajShared sh;
+  const ClusterTeam team{sh.part, (int)cooperative_groups::this_cluster().block_rank(), c};
+  const uint32_t len = 1u << (n - c);
+  const ClusterPsi<T> P{slice, n - c, len - 1};
+  const int nclusters = gridDim.x >> c;
+  for (int t = blockIdx.x >> c; t < ntraj; t += nclusters) {
+    const double v = one_trajectory<T>(P, team, slice, len, n, ops, nops, coef, wts, seed, t, terms, nterms, sh);
+    if (team.rank == 0 && threadIdx.x == 0) out[t] = v;
+    team.sync();
   }
 }
 
 }  // namespace dev
 
-static int max_traj_qubits(int prec) { return prec == VQD_F32 ? 14 : 13; }
+static int max_traj_qubits(int) { return VQD_MAX_QUBITS; }
+
+// Cluster size (log2) for an n-qubit statevector: 0 while it fits one CTA (n <= 14 complex64, <= 13
+// complex128), else slices of at most 64 KB (128 KB for 16 qubits in complex128) on up to 8 CTAs.
+static int traj_cluster_log(int n, size_t amp_bytes) {
+  const int single = amp_bytes == 8 ? 14 : 13;
+  if (n <= single) return 0;
+  return std::min(3, n - (single - 1));
+}
 
 template <class T>
 static cudaError_t traj_run(const std::vector<dev::TrajOp>& ops, const std::vector<cd>& coef,
@@ -323,17 +428,49 @@ static cudaError_t traj_run(const std::vector<dev::TrajOp>& ops, const std::vect
     e = cudaMemcpyAsync(d_w, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !terms.empty())
     e = cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(PauliTerm), cudaMemcpyHostToDevice, s);
-  const size_t smem = ((size_t)1 << n) * sizeof(cx<T>);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_traj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traj<T>, kTrajThreads, smem) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-    const int grid = std::max(1, std::min(ntraj, per_sm * num_sms()));
-    k_traj<T><<<grid, kTrajThreads, smem, s>>>((const TrajOp*)d_ops, (int)ops.size(), (const cx<T>*)d_coef,
-                                               (const double*)d_w, seed, ntraj, n, (const PauliTerm*)d_terms,
-                                               (int)terms.size(), (double*)d_out);
-    e = cudaGetLastError();
+  const int c = traj_cluster_log(n, sizeof(cx<T>));
+  const size_t smem = ((size_t)1 << (n - c)) * sizeof(cx<T>);
+  if (c == 0) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_traj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traj<T>, kTrajThreads, smem) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+      const int grid = std::max(1, std::min(ntraj, per_sm * num_sms()));
+      k_traj<T><<<grid, kTrajThreads, smem, s>>>((const TrajOp*)d_ops, (int)ops.size(), (const cx<T>*)d_coef,
+                                                 (const double*)d_w, seed, ntraj, n, (const PauliTerm*)d_terms,
+                                                 (int)terms.size(), (double*)d_out);
+      e = cudaGetLastError();
+    }
+  } else {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_traj_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 1u << c;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(kTrajThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3((unsigned)(1 << c));
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_traj_cluster<T>, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        clusters = 1;
+      }
+      clusters = std::max(1, std::min(ntraj, clusters));
+      cfg.gridDim = dim3((unsigned)(clusters << c));
+      e = cudaLaunchKernelEx(&cfg, k_traj_cluster<T>, (const TrajOp*)d_ops, (int)ops.size(), (const cx<T>*)d_coef,
+                             (const double*)d_w, seed, ntraj, n, (const PauliTerm*)d_terms, (int)terms.size(),
+                             (double*)d_out, c);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d_out, (size_t)ntraj * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -351,8 +488,7 @@ extern "C" int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* o
   try {
     if (prec != VQD_F32 && prec != VQD_F64) throw Error(VQD_EINVAL, "bad precision");
     if (n < 1 || n > max_traj_qubits(prec))
-      throw Error(VQD_ENOTSUP, "trajectories hold the statevector in shared memory: n <= " +
-                                   std::to_string(max_traj_qubits(prec)) + " for this precision");
+      throw Error(VQD_EINVAL, "trajectories: n must be in 1.." + std::to_string(max_traj_qubits(prec)));
     if (ntraj < 1 || nops < 0 || (nops > 0 && !ops) || nterms < 1 || !paulis || !coeffs || !out)
       throw Error(VQD_EINVAL, "bad argument");
     std::vector<dev::TrajOp> top;

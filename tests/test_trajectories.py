@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import evolve, measure
+from oracle import compile as oc
 from oracle import trajectories as otj
 from workloads import config1_chain6
 from workloads.circuits import OP_NAMES, NativeOp, Program, random_program
@@ -108,9 +109,51 @@ def test_traj_largest_statevector_and_errors(vqd):
     codes[0, 3] = 1                                     # <X_3> = 1 - 4p/3 after H and depol1(p)
     vals, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F32, prog.ops, 2048, 5, codes, [1.0])
     assert abs(mean - (1 - 4 * 0.1 / 3)) < 5 * se + 1e-6
-    with pytest.raises(vqd.VQDError) as e:
-        vqd.vqd_traj_expect(15, vqd.VQD_F32, [], 4, 1, np.zeros((1, 15), np.uint8), [1.0])
-    assert e.value.code == vqd.VQD_ENOTSUP
-    with pytest.raises(vqd.VQDError) as e:
-        vqd.vqd_traj_expect(14, vqd.VQD_F64, [], 4, 1, np.zeros((1, 14), np.uint8), [1.0])
-    assert e.value.code == vqd.VQD_ENOTSUP
+    for p in (vqd.VQD_F32, vqd.VQD_F64):
+        with pytest.raises(vqd.VQDError) as e:
+            vqd.vqd_traj_expect(17, p, [], 4, 1, np.zeros((1, 17), np.uint8), [1.0])
+        assert e.value.code == vqd.VQD_EINVAL
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,p,ntraj", [(14, "f64", 6), (15, "f64", 4), (16, "f64", 2), (15, "f32", 4)])
+def test_traj_cluster_statevector_one_by_one(vqd, n, p, ntraj):
+    """Statevectors beyond one CTA's shared memory live on a cluster of CTAs (distributed shared memory):
+    every trajectory equals the oracle's on the same draws (every op kind, operators on the cluster-rank
+    qubits included)."""
+    rng = np.random.default_rng(30 + n)
+    prog = random_program(40 + n, n, 36)
+    hi = [NativeOp("h", (n - 1,)), NativeOp("cz", (n - 1, 0)), NativeOp("depol2", (n - 2, n - 1), (0.2,)),
+          NativeOp("amp", (n - 1,), (0.3,)), NativeOp("rx", (n - 3,), (0.7,))]
+    prog = Program(n, hi + list(prog.ops))
+    codes, coeffs = hamiltonian(n, rng)
+    codes[1, n - 1] = 1                                    # a term that flips a cluster-rank bit
+    want = otj.trajectory_values(prog, ntraj, 99, codes, coeffs)
+    got, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F64 if p == "f64" else vqd.VQD_F32, prog.ops, ntraj, 99,
+                                        codes, coeffs)
+    assert np.abs(got - want).max() < (1e-10 if p == "f64" else 5e-5)
+
+
+@pytest.mark.gpu
+def test_traj_cluster_16_qubit_unitary_exact(vqd):
+    """n = 16 in complex64 (eight CTAs of 64 KB): a unitary program gives the exact expectation in every
+    trajectory."""
+    n = 16
+    rng = np.random.default_rng(44)
+    prog = random_program(45, n, 50, names=UNITARIES)
+    codes, coeffs = hamiltonian(n, rng)
+    psi = np.zeros(2 ** n, dtype=complex)
+    psi[0] = 1
+    for o in prog.ops:
+        ((_, qs, U),) = oc.compile_op(o.name, o.qubits, o.params)
+        psi = otj._apply_vec(psi, n, qs, U)
+    exact = 0.0
+    for c, row in zip(coeffs, codes):
+        v = psi.copy()
+        for q, code in enumerate(row):
+            if code:
+                v = otj._apply_vec(v, n, (q,), [None, np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]),
+                                                np.diag([1.0, -1.0])][code])
+        exact += c * np.vdot(psi, v).real
+    vals, mean, se = vqd.vqd_traj_expect(n, vqd.VQD_F32, prog.ops, 6, 1, codes, coeffs)
+    assert np.abs(vals - exact).max() < 5e-5
