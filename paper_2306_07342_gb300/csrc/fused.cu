@@ -441,28 +441,29 @@ __device__ __forceinline__ uint64_t deposit(uint64_t t, const int* pos, int cnt)
 // masked-increment identity next = ((x | ~M) + 1) & M.  Each thread moves its amplitudes in
 // batches of 16 independent accesses, so that 16 loads per thread are in flight at once.
 template <class T, bool LOAD>
-__device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base, const int* bits,
+__device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base64, const int* bits,
                                         int nbits) {
   const uint32_t size = 1u << nbits;
   const int lowbits = min(nbits, 8);  // blockDim == 256
   if (threadIdx.x >= size) return;
-  uint64_t lo = 0;
-  for (int j = 0; j < lowbits; j++) lo |= (uint64_t)((threadIdx.x >> j) & 1u) << bits[j];
-  uint64_t M = 0;
-  for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
+  // element offsets fit 32 bits (4^16 amplitudes at most)
+  cx<T>* __restrict__ sb = st + base64;
+  uint32_t lo = 0;
+  for (int j = 0; j < lowbits; j++) lo |= ((threadIdx.x >> j) & 1u) << bits[j];
+  uint32_t M = 0;
+  for (int j = 8; j < nbits; j++) M |= 1u << bits[j];
   const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
-  // sw() only mixes bits 0..7 of the local index, so sw(tid + 256 it) = sw(tid) + 256 it
   const uint32_t swt = sw<T>(threadIdx.x);
-  uint64_t hi = 0;
+  uint32_t hi = 0;
   constexpr int K = 8;
   for (int it0 = 0; it0 < iters; it0 += K) {
     cx<T> v[K];
-    uint64_t h = hi;
+    uint32_t h = hi;
     if (LOAD) {
 #pragma unroll
       for (int k = 0; k < K; k++) {
-        if (it0 + k < iters) v[k] = st[base + lo + h];
-        h = ((h | ~M) + 1ull) & M;
+        if (it0 + k < iters) v[k] = sb[lo + h];
+        h = ((h | ~M) + 1u) & M;
       }
 #pragma unroll
       for (int k = 0; k < K; k++)
@@ -473,8 +474,8 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
         if (it0 + k < iters) v[k] = sm[swt + 256u * (uint32_t)(it0 + k)];
 #pragma unroll
       for (int k = 0; k < K; k++) {
-        if (it0 + k < iters) st[base + lo + h] = v[k];
-        h = ((h | ~M) + 1ull) & M;
+        if (it0 + k < iters) sb[lo + h] = v[k];
+        h = ((h | ~M) + 1u) & M;
       }
     }
     hi = h;
@@ -484,27 +485,28 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
 // Asynchronous tile load (cp.async): each thread issues all of its copies straight into shared memory
 // (no register staging, so every copy of the tile is in flight at once), then waits for them.
 template <class T>
-__device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base,
+__device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base64,
                                                 const int* bits, int nbits) {
   const uint32_t size = 1u << nbits;
   const int lowbits = min(nbits, 8);
   if (threadIdx.x >= size) return;
-  uint64_t lo = 0;
-  for (int j = 0; j < lowbits; j++) lo |= (uint64_t)((threadIdx.x >> j) & 1u) << bits[j];
-  uint64_t M = 0;
-  for (int j = 8; j < nbits; j++) M |= 1ull << bits[j];
+  const cx<T>* __restrict__ sb = st + base64;
+  uint32_t lo = 0;
+  for (int j = 0; j < lowbits; j++) lo |= ((threadIdx.x >> j) & 1u) << bits[j];
+  uint32_t M = 0;
+  for (int j = 8; j < nbits; j++) M |= 1u << bits[j];
   const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
   const uint32_t swt = sw<T>(threadIdx.x);
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
-  uint64_t hi = 0;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm) + swt * (uint32_t)sizeof(cx<T>);
+  uint32_t hi = 0;
   for (int it = 0; it < iters; it++) {
-    const uint32_t dst = sbase + (swt + 256u * (uint32_t)it) * (uint32_t)sizeof(cx<T>);
-    const cx<T>* src = st + base + lo + hi;
+    const uint32_t dst = sbase + 256u * (uint32_t)sizeof(cx<T>) * (uint32_t)it;
+    const cx<T>* src = sb + (lo + hi);
     if (sizeof(T) == 4)
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
     else
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-    hi = ((hi | ~M) + 1ull) & M;
+    hi = ((hi | ~M) + 1u) & M;
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -566,7 +568,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
     for (int i = 0; i < 16; i++) u[i] = c[i];
   }
   const Inserter<4> ins(B.lsorted);
-  #pragma unroll 2
+  #pragma unroll 1
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     cx<T> x[16];
