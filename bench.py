@@ -323,8 +323,18 @@ def device_view(torch, ptr: int, count: int, prec_f32: bool):
     return torch.view_as_complex(t.view(-1, 2))
 
 
+def split_view(torch, ptr: int, count: int):
+    """Zero-copy view of a float-float state as (count, 4) float32 rows: re.hi, re.lo, im.hi, im.lo."""
+    class _A:
+        pass
+    a = _A()
+    a.__cuda_array_interface__ = {"shape": (4 * count,), "typestr": "<f4", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(a, device="cuda").view(-1, 4)
+
+
 def run_precision(args):
-    """Error of the complex64 plain and fused paths against the FP64 plain path on one workload."""
+    """Error of the complex64 and float-float plain and fused paths against the FP64 plain path on one
+    workload."""
     import numpy as np
     import torch
     from paper_2306_07342_gb300 import build as _b
@@ -357,14 +367,22 @@ def run_precision(args):
     out["f64_plain_s"] = t64
     out["f64_trace"] = vqd.vqd_trace(ref, 0).real
     out["f64_purity"] = pur_ref
-    for path, fuse in [("plain", 0), ("fused", 4), ("fused", 5), ("fused", 6)]:
-        ctx, t = run(vqd.VQD_F32, path, fuse)
-        x = device_view(torch, vqd.vqd_state_ptr(ctx, 0), N, True)
+    runs = [(vqd.VQD_F32, "plain", 0), (vqd.VQD_F32, "fused", 4), (vqd.VQD_F32, "fused", 5),
+            (vqd.VQD_F32, "fused", 6), (vqd.VQD_F32_SPLIT, "plain", 0), (vqd.VQD_F32_SPLIT, "fused", 6)]
+    for prec, path, fuse in runs:
+        ctx, t = run(prec, path, fuse)
+        split = prec == vqd.VQD_F32_SPLIT
+        x = (split_view(torch, vqd.vqd_state_ptr(ctx, 0), N) if split
+             else device_view(torch, vqd.vqd_state_ptr(ctx, 0), N, True))
         maxabs, fro2, tr_rs = 0.0, 0.0, 0.0
         chunk = 1 << 26
         for i in range(0, N, chunk):
             a = r[i:i + chunk]
-            b = x[i:i + chunk].to(torch.complex128)
+            if split:
+                w = x[i:i + chunk].to(torch.float64)
+                b = torch.complex(w[:, 0] + w[:, 1], w[:, 2] + w[:, 3])
+            else:
+                b = x[i:i + chunk].to(torch.complex128)
             d = b - a
             maxabs = max(maxabs, float(d.abs().max()))
             fro2 += float((d.real ** 2 + d.imag ** 2).sum())
@@ -372,7 +390,7 @@ def run_precision(args):
         p = vqd.vqd_prob(ctx, 0, list(range(n)))
         pur = vqd.vqd_purity(ctx, 0)
         sup_fid = tr_rs + np.sqrt(max(0.0, (1 - pur_ref) * (1 - pur)))
-        key = "c64_plain" if path == "plain" else f"c64_fused_f{fuse}"
+        key = ("split_" if split else "c64_") + ("plain" if path == "plain" else f"fused_f{fuse}")
         out[key] = {"seconds": t, "max_abs": maxabs, "frobenius": fro2 ** 0.5,
                     "trace_distance_bound": 0.5 * 2 ** (n / 2) * fro2 ** 0.5,
                     "prob_tv_distance": 0.5 * float(np.abs(p - p_ref).sum()),
@@ -543,6 +561,16 @@ def main():
                                      "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
                                                    for k, v in dstats.items()}}
         vqd.vqd_destroy(ctx64)
+        # ---- the same sample with float-float storage (FP64-class accuracy on the FP32 pipes)
+        ctxs = vqd.vqd_create(n, vqd.VQD_F32_SPLIT, sh)
+        for path in ("plain", "fused"):
+            tms, tst, _ = timed(make_step(ctxs, path, sample), 1, 1, ctxs)
+            kms = sum(v["total_ms"] for k, v in tst.items() if k not in ("reduce", "init"))
+            extra[f"{path}_split_sample"] = {
+                "value": world * len(sample) * 4.0 ** n / (kms * 1e-3), "unit": UNIT,
+                "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
+                "vs_f64_plain": (len(sample) * 4.0 ** n / (kms * 1e-3)) / fp64_rate}
+        vqd.vqd_destroy(ctxs)
 
     if not args.no_extra:
         extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)

@@ -22,8 +22,13 @@
  *   - Rotations R_s(theta) = exp(-i theta s / 2); SX = Rx(pi/2).
  *
  * Precision: VQD_F64 stores complex128 and computes in FP64.  VQD_F32 stores complex64 and
- * computes in FP32.  Operators are always composed on the host in FP64; every reduction
- * (probabilities, expectation values, trace, purity) accumulates in FP64.
+ * computes in FP32.  VQD_F32_SPLIT stores every real and imaginary part as a float-float pair
+ * hi + lo (|lo| <= ulp(hi)/2, about 48 significant bits; 16 bytes per amplitude, laid out as
+ * re.hi, re.lo, im.hi, im.lo) and computes in float-float arithmetic on the FP32 pipes; its
+ * operator coefficients are float-float roundings of the FP64 ones.  Operators are always composed
+ * on the host in FP64; every reduction (probabilities, expectation values, trace, purity)
+ * accumulates in FP64.  vqd_get_state / vqd_set_state convert to and from complex128 (hi + lo in
+ * FP64; a double is split into its nearest float and the float of the remainder).
  *
  * Errors: every int-returning call returns 0 (VQD_OK) or a negative VQD_E* code and never
  * throws.  vqd_last_error(ctx) gives a human-readable message (ctx may be NULL for errors
@@ -50,7 +55,7 @@ extern "C" {
 #define VQD_EDEVICE (-4) /* CUDA error (message in vqd_last_error) */
 #define VQD_ENOTSUP (-5) /* operation not supported in this configuration */
 
-typedef enum { VQD_F64 = 0, VQD_F32 = 1 } vqd_prec;
+typedef enum { VQD_F64 = 0, VQD_F32 = 1, VQD_F32_SPLIT = 2 } vqd_prec;
 
 typedef struct {
   double re, im;
@@ -205,8 +210,8 @@ int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int
                    vqd_c128* mat);
 
 /* Tile shape of the fused and batched paths of a context: tile_bits index bits per shared-memory tile
- * (<= 13 for VQD_F32, <= 12 for VQD_F64: a 64 KB tile; 0 = that maximum) of which passenger_bits
- * (0..3; -1 = default 3 for VQD_F32, 2 for VQD_F64) are the lowest row bits, carried along so that
+ * (<= 13 for VQD_F32, <= 12 for VQD_F64 and VQD_F32_SPLIT: a 64 KB tile; 0 = that maximum) of which
+ * passenger_bits (0..3; -1 = default 3 for VQD_F32, 2 otherwise) are the lowest row bits, carried along so that
  * every tile is made of contiguous DRAM runs.  Needs 4 + passenger_bits <= tile_bits.  Results do
  * not depend on the shape; speed does (the autotuner in the Python package picks it). */
 int vqd_set_tile_shape(vqd_t ctx, int tile_bits, int passenger_bits);
@@ -358,6 +363,7 @@ int vqd_set_state(vqd_t ctx, int inst, const vqd_c128* host_in);
  * as a 53-bit uniform u = (w0 >> 5) 2^-27 + (w1 >> 6) 2^-53; operator k is chosen when
  * sum_{j<k} p_j <= u < sum_{j<=k} p_j.
  *
+ * prec is VQD_F32 or VQD_F64 (VQD_F32_SPLIT: VQD_EINVAL).
  * 1 <= n <= 16.  Every trajectory keeps its statevector in shared memory: in one CTA up to n = 14
  * (VQD_F32) or 13 (VQD_F64), beyond that split over a thread-block cluster of up to 8 CTAs (slices
  * of 64 KB, 128 KB for 16 qubits in VQD_F64) joined by distributed shared memory.
@@ -380,7 +386,7 @@ int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* ops, unsigne
  * 2^14 doubles (128 KB), which every GPU that loads libvqd holds until the process exits.
  *
  *   dev_state  device address of an n-qubit state in the layout above (complex64 if prec ==
- *              VQD_F32, else complex128); read only.
+ *              VQD_F32, float-float pairs if VQD_F32_SPLIT, else complex128); read only.
  *   qubits     host array of m distinct qubits, 1 <= m <= VQD_PROB_STATIC_MAX_M (qubits[0] is the
  *              least significant bit of the output index, as in vqd_prob).
  *   dev_out    DEVICE array of 2^m doubles, written on `stream` (a cudaStream_t; NULL = legacy

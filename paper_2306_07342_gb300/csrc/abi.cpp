@@ -190,7 +190,8 @@ static void free_ctx(vqd_ctx* c) {
 }
 
 static vqd_ctx* make_ctx(int count, const int* n, int prec, void* stream, void* dev, size_t dev_bytes) {
-  if (prec != VQD_F64 && prec != VQD_F32) throw Error(VQD_EINVAL, "precision must be VQD_F64 or VQD_F32");
+  if (prec != VQD_F64 && prec != VQD_F32 && prec != VQD_F32_SPLIT)
+    throw Error(VQD_EINVAL, "precision must be VQD_F64, VQD_F32 or VQD_F32_SPLIT");
   if (count < 1) throw Error(VQD_EINVAL, "count must be >= 1");
   std::unique_ptr<vqd_ctx, void (*)(vqd_ctx*)> c(new vqd_ctx, free_ctx);
   c->prec = prec;
@@ -518,7 +519,7 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
                   int passenger_bits, unsigned flags, int64_t* info) {
   API_BEGIN
   if (!info || n < 1 || n > VQD_MAX_QUBITS || nops < 0 || (nops > 0 && !ops)) throw Error(VQD_EINVAL, "bad argument");
-  if (prec != VQD_F64 && prec != VQD_F32) throw Error(VQD_EINVAL, "bad precision");
+  if (prec != VQD_F64 && prec != VQD_F32 && prec != VQD_F32_SPLIT) throw Error(VQD_EINVAL, "bad precision");
   std::vector<Op> list;
   list.reserve(nops);
   for (int i = 0; i < nops; i++) {
@@ -997,6 +998,12 @@ int vqd_get_state(vqd_t c, int inst, vqd_c128* host) {
   if (c->prec == VQD_F64) {
     cuda_check(cudaMemcpyAsync(host, c->ptr(inst), N * 16, cudaMemcpyDeviceToHost, c->stream), "D2H state");
     cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  } else if (c->prec == VQD_F32_SPLIT) {  // (re.hi, re.lo, im.hi, im.lo) -> hi + lo in FP64
+    std::vector<float> tmp(4 * N);
+    cuda_check(cudaMemcpyAsync(tmp.data(), c->ptr(inst), N * 16, cudaMemcpyDeviceToHost, c->stream), "D2H state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+    for (size_t i = 0; i < N; i++)
+      host[i] = {(double)tmp[4 * i] + (double)tmp[4 * i + 1], (double)tmp[4 * i + 2] + (double)tmp[4 * i + 3]};
   } else {
     std::vector<float> tmp(2 * N);
     cuda_check(cudaMemcpyAsync(tmp.data(), c->ptr(inst), N * 8, cudaMemcpyDeviceToHost, c->stream), "D2H state");
@@ -1014,6 +1021,18 @@ int vqd_set_state(vqd_t c, int inst, const vqd_c128* host) {
   const size_t N = (size_t)1 << (2 * c->n[inst]);
   if (c->prec == VQD_F64) {
     cuda_check(cudaMemcpyAsync(c->ptr(inst), host, N * 16, cudaMemcpyHostToDevice, c->stream), "H2D state");
+    cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
+  } else if (c->prec == VQD_F32_SPLIT) {  // each double -> its nearest float and the float of the rest
+    std::vector<float> tmp(4 * N);
+    auto split = [](double d, float* w) {
+      w[0] = (float)d;
+      w[1] = (float)(d - (double)w[0]);
+    };
+    for (size_t i = 0; i < N; i++) {
+      split(host[i].re, &tmp[4 * i]);
+      split(host[i].im, &tmp[4 * i + 2]);
+    }
+    cuda_check(cudaMemcpyAsync(c->ptr(inst), tmp.data(), N * 16, cudaMemcpyHostToDevice, c->stream), "H2D state");
     cuda_check(cudaStreamSynchronize(c->stream), "synchronise");
   } else {
     std::vector<float> tmp(2 * N);

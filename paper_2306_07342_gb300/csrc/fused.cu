@@ -24,6 +24,7 @@
 
 #include "fused.h"
 #include "kernels.h"
+#include "numeric.h"
 
 namespace vqd {
 
@@ -382,10 +383,6 @@ BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int
 // ================================================================== device side
 namespace dev {
 
-template <class T> struct V2;
-template <> struct V2<float> { using t = float2; };
-template <> struct V2<double> { using t = double2; };
-template <class T> using cx = typename V2<T>::t;
 
 template <class T>
 __device__ __forceinline__ void cmac(cx<T>& acc, const cx<T>& c, const cx<T>& x) {
@@ -785,6 +782,7 @@ static void upload_common(FusedCache& c, const FusedPlan& p, cudaStream_t s) {
 
 void upload_plan(FusedCache& c, const FusedPlan& p, int prec, cudaStream_t s) {
   if (prec == VQD_F32) upload_common<float>(c, p, s);
+  else if (prec == VQD_F32_SPLIT) upload_common<df>(c, p, s);
   else upload_common<double>(c, p, s);
 }
 
@@ -816,6 +814,7 @@ static cudaError_t stage_t(FusedCache& c, const FusedPlan& p, int stage, void* s
 cudaError_t launch_stage(FusedCache& c, const FusedPlan& p, int stage, int prec, void* state, int n, cudaStream_t s) {
   (void)n;
   if (prec == VQD_F32) return stage_t<float>(c, p, stage, state, s);
+  if (prec == VQD_F32_SPLIT) return stage_t<df>(c, p, stage, state, s);
   return stage_t<double>(c, p, stage, state, s);
 }
 
@@ -856,6 +855,7 @@ static cudaError_t batch_t(FusedCache& c, const BatchPlan& p, void* base, cudaSt
 
 cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base, cudaStream_t s) {
   if (prec == VQD_F32) return batch_t<float>(c, p, base, s);
+  if (prec == VQD_F32_SPLIT) return batch_t<df>(c, p, base, s);
   return batch_t<double>(c, p, base, s);
 }
 

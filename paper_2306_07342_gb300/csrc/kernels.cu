@@ -20,14 +20,10 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "numeric.h"
 
 namespace vqd {
 namespace dev {
-
-template <class T> struct V2;
-template <> struct V2<float> { using t = float2; };
-template <> struct V2<double> { using t = double2; };
-template <class T> using cx = typename V2<T>::t;
 
 enum { FL_ZERO = 0, FL_ONE = 1, FL_REAL = 2, FL_IMAG = 3, FL_CPLX = 4 };
 
@@ -477,9 +473,12 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
     }
     // conj keeps the flag class except ONE stays ONE; an entry equal to 1 has conj 1 as well.
     const uint64_t ng = N / 16;
-    if (!fp64) k_uni2_pair<T><<<grid_for(k_uni2_pair<T>, 2 * ng), 256, 0, s>>>(st, ng, P);
-    else if (use_sparse(p.coef, fp64)) k_uni2_whole<T, true><<<grid_for(k_uni2_whole<T, true>, ng), 256, 0, s>>>(st, ng, P);
-    else k_uni2_whole<T, false><<<grid_for(k_uni2_whole<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    if constexpr (sizeof(T) == 4) {
+      k_uni2_pair<T><<<grid_for(k_uni2_pair<T>, 2 * ng), 256, 0, s>>>(st, ng, P);
+    } else {
+      if (use_sparse(p.coef, fp64)) k_uni2_whole<T, true><<<grid_for(k_uni2_whole<T, true>, ng), 256, 0, s>>>(st, ng, P);
+      else k_uni2_whole<T, false><<<grid_for(k_uni2_whole<T, false>, ng), 256, 0, s>>>(st, ng, P);
+    }
     return cudaGetLastError();
   }
   if (p.kind == KK_SUP2) {
@@ -496,6 +495,7 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
 
 cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s) {
   if (prec == VQD_F32) return launch_pass_t<float>((cx<float>*)state, n, p, s);
+  if (prec == VQD_F32_SPLIT) return launch_pass_t<df>((cx<df>*)state, n, p, s);
   return launch_pass_t<double>((cx<double>*)state, n, p, s);
 }
 
@@ -509,6 +509,7 @@ static cudaError_t init_classical_t(cx<T>* st, int n, uint64_t basis, cudaStream
 }
 cudaError_t launch_init_classical(int prec, void* state, int n, uint64_t basis, cudaStream_t s) {
   if (prec == VQD_F32) return init_classical_t<float>((cx<float>*)state, n, basis, s);
+  if (prec == VQD_F32_SPLIT) return init_classical_t<df>((cx<df>*)state, n, basis, s);
   return init_classical_t<double>((cx<double>*)state, n, basis, s);
 }
 
@@ -524,6 +525,7 @@ static cudaError_t init_product_t(cx<T>* st, int n, const double* e, cudaStream_
 }
 cudaError_t launch_init_product_diag(int prec, void* state, int n, const double* excited, cudaStream_t s) {
   if (prec == VQD_F32) return init_product_t<float>((cx<float>*)state, n, excited, s);
+  if (prec == VQD_F32_SPLIT) return init_product_t<df>((cx<df>*)state, n, excited, s);
   return init_product_t<double>((cx<double>*)state, n, excited, s);
 }
 
@@ -550,6 +552,7 @@ static cudaError_t purity_t(const cx<T>* st, int n, double* scratch, double* out
 }
 cudaError_t launch_purity(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s) {
   if (prec == VQD_F32) return purity_t<float>((const cx<float>*)state, n, scratch, out, s);
+  if (prec == VQD_F32_SPLIT) return purity_t<df>((const cx<df>*)state, n, scratch, out, s);
   return purity_t<double>((const cx<double>*)state, n, scratch, out, s);
 }
 
@@ -562,6 +565,7 @@ static cudaError_t trace_t(const cx<T>* st, int n, double* scratch, double* out,
 }
 cudaError_t launch_trace(int prec, const void* state, int n, double* scratch, double* out, cudaStream_t s) {
   if (prec == VQD_F32) return trace_t<float>((const cx<float>*)state, n, scratch, out, s);
+  if (prec == VQD_F32_SPLIT) return trace_t<df>((const cx<df>*)state, n, scratch, out, s);
   return trace_t<double>((const cx<double>*)state, n, scratch, out, s);
 }
 
@@ -586,6 +590,7 @@ static cudaError_t prob_t(const cx<T>* st, int n, int m, const int* qubits, doub
 cudaError_t launch_prob(int prec, const void* state, int n, int m, const int* qubits, double* scratch, double* out,
                         cudaStream_t s) {
   if (prec == VQD_F32) return prob_t<float>((const cx<float>*)state, n, m, qubits, scratch, out, s);
+  if (prec == VQD_F32_SPLIT) return prob_t<df>((const cx<df>*)state, n, m, qubits, scratch, out, s);
   return prob_t<double>((const cx<double>*)state, n, m, qubits, scratch, out, s);
 }
 
@@ -609,6 +614,7 @@ static cudaError_t expect_t(const cx<T>* st, int n, int nterms, const uint32_t* 
 cudaError_t launch_expect(int prec, const void* state, int n, int nterms, const uint32_t* xmask, const uint32_t* zymask,
                           double* scratch, double* out, cudaStream_t s) {
   if (prec == VQD_F32) return expect_t<float>((const cx<float>*)state, n, nterms, xmask, zymask, scratch, out, s);
+  if (prec == VQD_F32_SPLIT) return expect_t<df>((const cx<df>*)state, n, nterms, xmask, zymask, scratch, out, s);
   return expect_t<double>((const cx<double>*)state, n, nterms, xmask, zymask, scratch, out, s);
 }
 
@@ -657,6 +663,9 @@ cudaError_t launch_batch_reduce(int prec, const void* base, const std::vector<in
   if (prec == VQD_F32)
     dev::k_batch_reduce<float><<<(unsigned)nitems, 256, 0, s>>>((const cx<float>*)base, (const dev::BatchRedItem*)d_items,
                                                                 d_probs, d_part);
+  else if (prec == VQD_F32_SPLIT)
+    dev::k_batch_reduce<dev::df><<<(unsigned)nitems, 256, 0, s>>>((const cx<dev::df>*)base,
+                                                                  (const dev::BatchRedItem*)d_items, d_probs, d_part);
   else
     dev::k_batch_reduce<double><<<(unsigned)nitems, 256, 0, s>>>((const cx<double>*)base, (const dev::BatchRedItem*)d_items,
                                                                  d_probs, d_part);
@@ -743,7 +752,8 @@ extern "C" int vqd_prob_static(const void* dev_state, int n, int prec, int m, co
   using namespace vqd;
   if (!dev_state || !qubits || !dev_out) return report_static_error(VQD_EINVAL, "vqd_prob_static: NULL argument");
   if (n < 1 || n > VQD_MAX_QUBITS) return report_static_error(VQD_EINVAL, "vqd_prob_static: n outside 1..16");
-  if (prec != VQD_F64 && prec != VQD_F32) return report_static_error(VQD_EINVAL, "vqd_prob_static: bad precision");
+  if (prec != VQD_F64 && prec != VQD_F32 && prec != VQD_F32_SPLIT)
+    return report_static_error(VQD_EINVAL, "vqd_prob_static: bad precision");
   if (m < 1 || m > n) return report_static_error(VQD_EINVAL, "vqd_prob_static: need 1 <= m <= n measured qubits");
   if (m > VQD_PROB_STATIC_MAX_M)
     return report_static_error(VQD_EINVAL,
@@ -759,6 +769,7 @@ extern "C" int vqd_prob_static(const void* dev_state, int n, int prec, int m, co
   if (e == cudaSuccess) {
     cudaStream_t s = (cudaStream_t)stream;
     if (prec == VQD_F32) e = prob_static_t<float>((const cx<float>*)dev_state, n, m, qubits, scratch, dev_out, s);
+    else if (prec == VQD_F32_SPLIT) e = prob_static_t<df>((const cx<df>*)dev_state, n, m, qubits, scratch, dev_out, s);
     else e = prob_static_t<double>((const cx<double>*)dev_state, n, m, qubits, scratch, dev_out, s);
   }
   if (e != cudaSuccess) {

@@ -17,6 +17,17 @@ def tol_f32(n_ops: int) -> float:
     return 1e-6 * math.sqrt(max(1, n_ops))
 
 
+def tol_split(n_ops: int) -> float:
+    """Float-float (VQD_F32_SPLIT) max-abs tolerance after n_ops compiled operators.
+
+    Float-float numbers round at about u^2 = 2^-48 = 3.6e-15 (u = 2^-24), and each operation of the
+    double-word sum and product adds a few u^2 of relative error.  One pass forms each amplitude from at
+    most 16 products, a random error of about sqrt(16) * 3 u^2 = 4e-14; over m passes these add like a
+    random walk.  The bound is 5x that estimate: 2e-13 * sqrt(m), and never below 2e-13.
+    """
+    return 2e-13 * math.sqrt(max(1, n_ops))
+
+
 def get_lib():
     from paper_2306_07342_gb300 import build as _b
     _b.build()

@@ -12,7 +12,7 @@ from oracle import compile as oc
 from workloads import config1_chain6, config2_sc_grid, config3_ion_alltoall, config5_spin_chain
 from workloads.circuits import NativeOp, OP_NAMES, Program, random_program
 
-from ._lib import TOL_F64, get_lib, rand_kraus, rand_state, rand_unitary, tol_f32
+from ._lib import TOL_F64, get_lib, rand_kraus, rand_state, rand_unitary, tol_f32, tol_split
 
 pytestmark = pytest.mark.gpu
 
@@ -22,15 +22,15 @@ def vqd():
     return get_lib()
 
 
-PRECS = ["f64", "f32"]
+PRECS = ["f64", "f32", "split"]
 
 
 def prec_code(vqd, p):
-    return vqd.VQD_F64 if p == "f64" else vqd.VQD_F32
+    return {"f64": vqd.VQD_F64, "f32": vqd.VQD_F32, "split": vqd.VQD_F32_SPLIT}[p]
 
 
 def tol(p, nops):
-    return TOL_F64 if p == "f64" else tol_f32(nops)
+    return {"f64": TOL_F64, "f32": tol_f32(nops), "split": tol_split(nops)}[p]
 
 
 def gpu_state(vqd, ctx, inst=0):
@@ -203,6 +203,25 @@ def test_thermal_init_and_t2_flag(vqd, p):
     assert abs(got[0, 1] - 0.5 * math.exp(-3.0 / 25.0)) < tol(p, 2)
 
 
+def test_split_precision_is_fp64_class(vqd):
+    """Float-float storage on the 6-qubit chain (682 native ops): the plain and fused paths stay within
+    the float-float bound of the FP64 oracle, at least 10^4 times closer than complex64."""
+    prog = config1_chain6()
+    want = evolve.run_program(prog)
+    err = {}
+    for p in ("f32", "split"):
+        for path in ("plain", "fused"):
+            ctx = vqd.vqd_create(prog.n, prec_code(vqd, p))
+            try:
+                (vqd.vqd_apply_native if path == "plain" else vqd.vqd_run_program)(ctx, 0, prog.ops)
+                err[p, path] = np.abs(gpu_state(vqd, ctx) - want).max()
+            finally:
+                vqd.vqd_destroy(ctx)
+    for path in ("plain", "fused"):
+        assert err["split", path] < tol_split(len(prog.ops)), err
+        assert err["split", path] < 1e-4 * err["f32", path], err
+
+
 # ---------------------------------------------------------------- reductions
 @pytest.mark.parametrize("p", PRECS)
 def test_reductions(vqd, p):
@@ -225,7 +244,7 @@ def test_reductions(vqd, p):
 
 
 # ---------------------------------------------------------------- batched persistent path
-@pytest.mark.parametrize("p,fuse", [("f64", 0), ("f32", 0), ("f32", 3)])
+@pytest.mark.parametrize("p,fuse", [("f64", 0), ("f32", 0), ("f32", 3), ("split", 0)])
 def test_batch_matches_per_instance_oracle(vqd, p, fuse):
     """Uneven instances in one batched run: single-tile instances, and (n = 9, 10) multi-stage ones
     whose stages span several waves and tile chunks."""
