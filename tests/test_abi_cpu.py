@@ -112,6 +112,20 @@ def test_state_bytes(vqd):
     assert vqd.vqd_state_bytes(14, vqd.VQD_F32) == 8 * 4 ** 14
     assert vqd.vqd_state_bytes(16, vqd.VQD_F64) == 16 * 4 ** 16
     assert vqd.vqd_state_bytes(17, vqd.VQD_F64) == 0
+    assert vqd.vqd_state_bytes(14, vqd.VQD_F32_SPLIT) == 16 * 4 ** 14     # float-float pairs, like complex128
+
+
+def test_precision_enum_matches_header(vqd):
+    src = open(HEADER).read()
+    assert "VQD_F64 = 0, VQD_F32 = 1, VQD_F32_SPLIT = 2" in src
+    assert (vqd.VQD_F64, vqd.VQD_F32, vqd.VQD_F32_SPLIT) == (0, 1, 2)
+
+
+def test_trajectories_refuse_split_precision(vqd):
+    """Checked on the host before any device work: trajectories run in complex64 or complex128 only."""
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_traj_expect(3, vqd.VQD_F32_SPLIT, [NativeOp("h", (0,))], 4, 1, np.ones((1, 3), np.uint8), [1.0])
+    assert e.value.code == vqd.VQD_EINVAL
 
 
 def test_schedule_worked_example_and_oracle(vqd):
