@@ -242,6 +242,41 @@ def measure_sc_device(vqd, torch, stream_handle, timed, steps):
         vqd.vqd_destroy(ctx)
 
 
+def measure_nv_noise_sweep(vqd, torch, count=32, props=16):
+    """A second workload with the shape of the paper's NV-centre study (Sec. 5): a 5-qubit NV centre (App. C
+    table) running BCS-shaped propagators of 200 native gates, swept over `count` noise scales (log-uniform
+    0.1..10).  Each scale is one instance of one batched run (stage waves replayed as a CUDA graph)."""
+    import numpy as np
+    from workloads.devices import NV5, nv_bcs_shape, nv_scaled
+    scales = np.logspace(-1, 1, count)
+    logical = nv_bcs_shape(NV5, props, 200)
+    t0 = time.perf_counter()
+    arrays = [vqd.vqd_nv_compile(nv_scaled(NV5, float(sc)), logical, readout=True) for sc in scales]
+    compile_s = time.perf_counter() - t0
+    units = sum(len(a) * 4.0 ** 5 for a in arrays)
+    bstream = torch.cuda.Stream()
+    ctx = vqd.vqd_create_batch([5] * count, vqd.VQD_F32, bstream.cuda_stream)
+    try:
+        t0 = time.perf_counter()
+        vqd.vqd_run_batch(ctx, arrays)
+        bstream.synchronize()
+        first = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for i in range(count):
+            vqd.vqd_init_zero(ctx, i)
+        vqd.vqd_run_batch(ctx, arrays)
+        probs, trs, purs = vqd.vqd_batch_reduce(ctx, [5] * count)
+        wall = time.perf_counter() - t0
+        p1 = [float(pr.reshape(-1)[1::2].sum()) for pr in probs]   # electron reads 1
+        return {"value": units / wall, "unit": UNIT, "instances": count, "logical_gates": len(logical),
+                "native_ops_per_instance": int(np.mean([len(a) for a in arrays])), "host_compile_s": compile_s,
+                "first_run_s": first, "wall_s": wall,
+                "electron_p1_at_scales": {f"{scales[i]:.3g}": p1[i] for i in (0, count // 2, count - 1)},
+                "note": "complex64; value = re-initialise, one graph replay of the batch, batched reductions"}
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
 def measure_batch(vqd, torch, stream_handle, count):
     """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of
     persistent kernels), against one launch sequence per instance (fused and plain) on a sample."""
@@ -576,6 +611,7 @@ def main():
         extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
         extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed, args.steps)
         extra["trajectories_spin16_c64"] = measure_trajectories_spin16(vqd, sh)
+        extra["nv5_noise_sweep_batch_c64"] = measure_nv_noise_sweep(vqd, torch)
 
     if not args.no_extra and args.batch_count > 0:
         extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)

@@ -115,7 +115,10 @@ typedef enum {
                            exp(-i beta Z Z), beta = J^2 (1/(Delta-alpha_t) - 1/(Delta+alpha_c)), Sec. 8;
                            the parameters are frequencies times the idle duration, so beta is the
                            accumulated phase; a zero denominator is VQD_EINVAL                       */
-  VQD_OP_COUNT = 34
+  VQD_OP_ZY = 34,       /* q0 = control, q1 = target; theta: NV conditional rotation CRy+-(theta) =
+                           |0><0| (x) Ry(theta) + |1><1| (x) Ry(-theta) = exp(-i theta/2 Z Y), Sec. 5
+                           Eq. (conditional_rots); CRx+- is VQD_OP_ZX                                   */
+  VQD_OP_COUNT = 35
 } vqd_op_code;
 
 typedef struct {
@@ -307,6 +310,42 @@ typedef struct {
  * out == NULL only counts; otherwise out has room for cap ops (VQD_EINVAL if too few). */
 int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, int cap, vqd_native_op* out,
                    int* nout);
+
+/* NV-centre device of Sec. 5 with the parameters of its App. C table: qubit 0 is the electron spin,
+ * qubits 1..n-1 are nuclear spins coupled only to it (a star).  Host arrays owned by the caller.
+ * Times and frequencies in any consistent units (the table's: seconds and Hz). */
+typedef struct {
+  int32_t n;               /* qubits (2..32) */
+  const double* t1;        /* [n] T1 > 0 (passive decay as depolarising, Eq. depolt1) */
+  const double* t2;        /* [n] T2 > 0 (Eq. depht2) */
+  const double* freq_xy;   /* [n] Rabi frequencies of the x/y rotations, > 0 */
+  const double* freq_z;    /* [n] frequencies of the z rotations, > 0 */
+  const double* fid_xy;    /* [n] average fidelities of x/y rotations, in (0,1] */
+  const double* fid_z;     /* [n] average fidelities of z rotations (1: noiseless virtual Z) */
+  double x_xy;             /* depolarising fraction of the x/y rotations' standard error, in [0,1] */
+  const double* freq_crot; /* [n-1] frequencies of the conditional rotations on nuclear spins 1..n-1, > 0 */
+  const double* fid_crot;  /* [n-1] their average fidelities */
+  double x_crot;           /* depolarising fraction of the conditional rotations' standard error */
+  double freq_zz;          /* weak ZZ coupling frequency among passive nuclear spins (0: none) */
+  double fid_meas;         /* electron readout fidelity (readout bias 1 - fid_meas), in [0,1] */
+  double dur_meas;         /* electron readout duration */
+  uint32_t flags;          /* VQD_NV_NO_PASSIVE */
+} vqd_nv_device;
+#define VQD_NV_NO_PASSIVE 1u  /* no passive T1/T2 decay or weak ZZ */
+
+/* Compile a logical circuit of Rx, Ry, Rz on any qubit and the conditional rotations CRx+- (VQD_OP_ZX)
+ * and CRy+- (VQD_OP_ZY) with control 0 and a nuclear target (others: VQD_EINVAL) for the device.  Gates
+ * run one at a time, in program order.  Rx/Ry(theta) on q lasts t = |theta| / (2 pi freq_xy[q]) and is
+ * followed by stderr1(fid_xy[q], x_xy); Rz(theta) lasts |theta| / (2 pi freq_z[q]) and is followed by
+ * stderr1(fid_z[q], 0) when fid_z[q] < 1; a conditional rotation theta on (0, j) lasts
+ * |theta| / (2 pi freq_crot[j-1]) and is followed by stderr2(fid_crot[j-1], x_crot).  During a gate of
+ * length t > 0, on the qubits outside it: zz_idle(t, freq_zz) on every pair (i, k), 1 <= i < k, of
+ * nuclear spins (when freq_zz != 0), then idle_depol(t, T1_j, T2_j) on every such qubit j.  With
+ * readout != 0, the electron readout bias ends the program: rx(pi), amp(1 - fid_meas), rx(pi) on
+ * qubit 0, then the passive noise of the other qubits over dur_meas.  out == NULL only counts;
+ * otherwise out has room for cap ops (VQD_EINVAL if too few). */
+int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                   vqd_native_op* out, int* nout);
 
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */

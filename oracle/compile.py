@@ -93,6 +93,14 @@ def zx(theta):
     return pauli_rot2(Z, X, theta / 2)
 
 
+def zy(theta):
+    """NV conditional rotation CRy+-(theta) of Sec. 5, Eq. (conditional_rots), as printed:
+    |0><0|_c (x) Ry(theta)_t + |1><1|_c (x) Ry(-theta)_t, control c = first qubit."""
+    p0 = np.diag([1, 0]).astype(complex)
+    p1 = np.diag([0, 1]).astype(complex)
+    return two(p0, ry(theta)) + two(p1, ry(-theta))
+
+
 def zz(theta):
     return pauli_rot2(Z, Z, theta / 2)
 
@@ -309,6 +317,7 @@ def compile_op(name: str, qubits: Sequence[int], params: Sequence[float], t2_is_
         "czphi": lambda: czphi(*P), "zx": lambda: zx(*P), "zz": lambda: zz(*P), "xx": lambda: xx(*P),
         "zzphase": lambda: zzphase(*P), "zz_idle": lambda: zz_idle(*P), "crz_xtalk": lambda: crz_xtalk(*P),
         "exchange": lambda: exchange(*P), "offres": lambda: off_resonant(*P), "zz_static": lambda: zz_static(*P),
+        "zy": lambda: zy(*P),
     }
     if name in unitary:
         return [("U", q, unitary[name]())]

@@ -166,3 +166,67 @@ def si_compile(dev: Dict, ops: Sequence[NativeOp]) -> List[NativeOp]:
         else:
             raise ValueError(f"{op.name} is not a silicon native gate")
     return out
+
+
+# ------------------------------------------------------------------ NV centre (Sec. 5, App. C)
+def nv_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> List[NativeOp]:
+    """Logical circuit -> native op list of the NV-centre device (Sec. 5, App. C).
+
+    Qubit 0 is the electron spin, the others are nuclear spins. The gates run one at a time
+    (dynamical decoupling keeps the passive qubits at their T2, and gates are serial). Steps:
+    - Rx/Ry: the gate, then the standard error of Sec. 3.2 from the gate's fidelity with the table's
+      depolarising:dephasing split.
+    - Rz: the gate, then a pure dephasing standard error when its fidelity is below 1.
+    - CRx+- / CRy+- (zx / zy, control = electron): the gate, then the two-qubit standard error.
+    - During a gate, every other qubit: the weak ZZ of every pair of passive nuclear spins
+      (zz_idle), then T1 as depolarising and the T2 dephasing (idle_depol).
+    - Readout: the electron's bias, amplitude damping between two X gates (Sec. 5), with p = 1 - F
+      read as the net probability that |0> is recorded as 1.
+
+    Readings, also used by the library:
+    - A rotation by theta lasts |theta| / (2 pi f), with f the table's frequency for that kind of
+      rotation and qubit.
+    - The weak ZZ rate is a conditional frequency, as for the superconducting grid (pi f dt / 2).
+    """
+    n = int(dev["n"])
+    passive = not (int(dev.get("flags", 0)) & 1)
+    out: List[NativeOp] = []
+
+    def outside(active, t):
+        if not passive or t <= 0:
+            return
+        if dev["freq_zz"] != 0:
+            for i in range(1, n):
+                for k in range(i + 1, n):
+                    if i not in active and k not in active:
+                        out.append(NativeOp("zz_idle", (i, k), (t, float(dev["freq_zz"]))))
+        for j in range(n):
+            if j not in active:
+                out.append(NativeOp("idle_depol", (j,), (t, float(dev["t1"][j]), float(dev["t2"][j]))))
+
+    for op in ops:
+        if op.name in ("rx", "ry", "rz"):
+            q = op.qubits[0]
+            f = dev["freq_z"][q] if op.name == "rz" else dev["freq_xy"][q]
+            t = abs(op.params[0]) / (2 * math.pi * float(f))
+            out.append(op)
+            if op.name != "rz":
+                out.append(NativeOp("stderr1", (q,), (float(dev["fid_xy"][q]), float(dev["x_xy"]))))
+            elif dev["fid_z"][q] < 1:
+                out.append(NativeOp("stderr1", (q,), (float(dev["fid_z"][q]), 0.0)))
+            outside((q,), t)
+        elif op.name in ("zx", "zy"):
+            c, j = op.qubits
+            if c != 0:
+                raise ValueError("conditional rotations are controlled by the electron spin (qubit 0)")
+            t = abs(op.params[0]) / (2 * math.pi * float(dev["freq_crot"][j - 1]))
+            out.append(op)
+            out.append(NativeOp("stderr2", (0, j), (float(dev["fid_crot"][j - 1]), float(dev["x_crot"]))))
+            outside((0, j), t)
+        else:
+            raise ValueError(f"{op.name} is not an NV-centre native gate")
+    if readout:
+        out += [NativeOp("rx", (0,), (math.pi,)), NativeOp("amp", (0,), (1.0 - float(dev["fid_meas"]),)),
+                NativeOp("rx", (0,), (math.pi,))]
+        outside((0,), float(dev["dur_meas"]))
+    return out

@@ -819,6 +819,99 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
   API_END(nullptr)
 }
 
+// NV-centre device compiler, Sec. 5 and the NV-centre table of App. C: serial gates, each followed by
+// its standard error (Sec. 3.2 with the table's depolarising:dephasing split); the qubits outside a gate
+// feel the weak ZZ among nuclear spins and the passive T1/T2 decay (Eqs. depolt1, depht2) for its
+// duration; the electron readout's bias is an amplitude damping between two X gates.
+int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                   vqd_native_op* out, int* nout) {
+  API_BEGIN
+  if (!dev || !nout || nin < 0 || (nin > 0 && !in) || (out && cap < 0)) throw Error(VQD_EINVAL, "bad argument");
+  const int n = dev->n;
+  if (n < 2 || n > 32) throw Error(VQD_EINVAL, "bad device: qubit count");
+  if (!dev->t1 || !dev->t2 || !dev->freq_xy || !dev->freq_z || !dev->fid_xy || !dev->fid_z || !dev->freq_crot ||
+      !dev->fid_crot)
+    throw Error(VQD_EINVAL, "bad device: NULL table");
+  for (int j = 0; j < n; j++)
+    if (!(dev->t1[j] > 0) || !(dev->t2[j] > 0) || !(dev->freq_xy[j] > 0) || !(dev->freq_z[j] > 0) ||
+        !(dev->fid_xy[j] > 0 && dev->fid_xy[j] <= 1) || !(dev->fid_z[j] > 0 && dev->fid_z[j] <= 1))
+      throw Error(VQD_EINVAL, "bad device: T1, T2, frequency or fidelity");
+  for (int j = 0; j + 1 < n; j++)
+    if (!(dev->freq_crot[j] > 0) || !(dev->fid_crot[j] > 0 && dev->fid_crot[j] <= 1))
+      throw Error(VQD_EINVAL, "bad device: conditional-rotation frequency or fidelity");
+  if (!(dev->x_xy >= 0 && dev->x_xy <= 1 && dev->x_crot >= 0 && dev->x_crot <= 1))
+    throw Error(VQD_EINVAL, "bad device: depolarising fraction outside [0,1]");
+  if (readout && !(dev->fid_meas >= 0 && dev->fid_meas <= 1 && dev->dur_meas >= 0))
+    throw Error(VQD_EINVAL, "bad device: readout fidelity or duration");
+  const bool passive = !(dev->flags & VQD_NV_NO_PASSIVE);
+  const double two_pi = 2 * 3.14159265358979323846;
+  int cnt = 0;
+  auto put = [&](const vqd_native_op& o) {
+    if (out) {
+      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+      out[cnt] = o;
+    }
+    cnt++;
+  };
+  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
+    vqd_native_op o;
+    std::memset(&o, 0, sizeof(o));
+    o.code = code;
+    o.nq = q1 < 0 ? 1 : 2;
+    o.q[0] = q0;
+    o.q[1] = q1 < 0 ? 0 : q1;
+    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
+    put(o);
+  };
+  auto passive_noise = [&](int a, int b, double t) {  // qubits outside the gate, for its duration
+    if (!passive || t <= 0) return;
+    if (dev->freq_zz != 0)
+      for (int i = 1; i < n; i++)
+        for (int k = i + 1; k < n; k++)
+          if (i != a && i != b && k != a && k != b) emit(VQD_OP_ZZ_IDLE, i, k, t, dev->freq_zz, 0);
+    for (int j = 0; j < n; j++)
+      if (j != a && j != b) emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
+  };
+  for (int i = 0; i < nin; i++) {
+    const vqd_native_op& o = in[i];
+    const int ar = native_arity(o.code);
+    if (ar < 1 || o.nq != ar) throw Error(VQD_EINVAL, "bad op at index " + std::to_string(i));
+    for (int j = 0; j < ar; j++)
+      if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
+        throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
+    if (o.code == VQD_OP_RX || o.code == VQD_OP_RY || o.code == VQD_OP_RZ) {
+      const int q = o.q[0];
+      const bool z = o.code == VQD_OP_RZ;
+      const double t = std::fabs(o.par[0]) / (two_pi * (z ? dev->freq_z[q] : dev->freq_xy[q]));
+      put(o);
+      if (!z) emit(VQD_OP_STDERR1, q, -1, dev->fid_xy[q], dev->x_xy, 0);
+      else if (dev->fid_z[q] < 1) emit(VQD_OP_STDERR1, q, -1, dev->fid_z[q], 0.0, 0);
+      passive_noise(q, -1, t);
+      continue;
+    }
+    if (o.code == VQD_OP_ZX || o.code == VQD_OP_ZY) {
+      if (o.q[0] != 0) throw Error(VQD_EINVAL, "conditional rotation not controlled by the electron (qubit 0) at op " +
+                                                   std::to_string(i));
+      const int j = o.q[1];
+      const double t = std::fabs(o.par[0]) / (two_pi * dev->freq_crot[j - 1]);
+      put(o);
+      emit(VQD_OP_STDERR2, 0, j, dev->fid_crot[j - 1], dev->x_crot, 0);
+      passive_noise(0, j, t);
+      continue;
+    }
+    throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not an NV-centre native gate");
+  }
+  if (readout) {
+    const double pi = 3.14159265358979323846;
+    emit(VQD_OP_RX, 0, -1, pi, 0, 0);
+    emit(VQD_OP_AMP, 0, -1, 1 - dev->fid_meas, 0, 0);
+    emit(VQD_OP_RX, 0, -1, pi, 0, 0);
+    passive_noise(0, -1, dev->dur_meas);
+  }
+  *nout = cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");

@@ -187,7 +187,7 @@ void require(bool ok, const char* msg) {
 
 int native_arity(int code) {
   static const int ar[VQD_OP_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2,
-                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2};
+                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2, 2};
   if (code < 0 || code >= VQD_OP_COUNT) return -1;
   return ar[code];
 }
@@ -239,6 +239,7 @@ Op compile_native(const vqd_native_op& o, unsigned flags) {
     case VQD_OP_CZPHI: U1(diag4(1, std::exp(I1 * P[0]), std::exp(I1 * P[0]), std::exp(I1 * (2 * P[0] - PI)))); break;
     case VQD_OP_ZX: U1(pauli_exp2(3, 1, P[0] / 2)); break;   // Z on the control (first, low bit), X on the target
     case VQD_OP_ZZ: U1(pauli_exp2(3, 3, P[0] / 2)); break;
+    case VQD_OP_ZY: U1(pauli_exp2(3, 2, P[0] / 2)); break;  // CRy+-: Z on the control (low bit), Y on the target
     case VQD_OP_XX: U1(pauli_exp2(1, 1, P[0] / 2)); break;
     case VQD_OP_ZZPHASE: U1(pauli_exp2(3, 3, P[0])); break;
     case VQD_OP_ZZ_IDLE: U1(pauli_exp2(3, 3, PI * P[1] * P[0] / 2)); break;  // conditional phase 2 pi xi dt = 4 alpha

@@ -24,7 +24,7 @@ VQD_MAX_FUSE = 6
 OP_CODES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
             "crz_xtalk", "exchange", "depol1", "depol2", "deph1", "deph2", "amp", "bitflip", "bitflip2", "gamp",
             "idle", "idle_depol", "stderr1", "stderr2", "ampdeph2", "leak_init", "leak_cz",
-            "offres", "zz_static"]
+            "offres", "zz_static", "zy"]
 OP_CODE = {name: i for i, name in enumerate(OP_CODES)}
 
 NATIVE_OP_DTYPE = np.dtype([("code", "<i4"), ("nq", "<i4"), ("q", "<i4", (2,)), ("par", "<f8", (4,))])
@@ -64,6 +64,18 @@ class si_device(ctypes.Structure):
 
 VQD_SI_NO_PASSIVE = 1
 VQD_SI_NO_OFFRES = 2
+
+
+class nv_device(ctypes.Structure):
+    """vqd_nv_device: NV-centre device table (qubit 0 = electron spin)."""
+    _fields_ = [("n", ctypes.c_int32), ("t1", ctypes.c_void_p), ("t2", ctypes.c_void_p),
+                ("freq_xy", ctypes.c_void_p), ("freq_z", ctypes.c_void_p), ("fid_xy", ctypes.c_void_p),
+                ("fid_z", ctypes.c_void_p), ("x_xy", ctypes.c_double), ("freq_crot", ctypes.c_void_p),
+                ("fid_crot", ctypes.c_void_p), ("x_crot", ctypes.c_double), ("freq_zz", ctypes.c_double),
+                ("fid_meas", ctypes.c_double), ("dur_meas", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+VQD_NV_NO_PASSIVE = 1
 
 
 class VQDError(RuntimeError):
@@ -122,6 +134,7 @@ def lib() -> ctypes.CDLL:
             "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
             "vqd_sc_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_si_compile": (I, [P, I, P, I, P, P]),
+            "vqd_nv_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -337,6 +350,25 @@ def vqd_si_compile(dev: dict, ops) -> np.ndarray:
     _check(lib().vqd_si_compile(ctypes.byref(d), len(a), _ptr(a), 0, None, ctypes.byref(cnt)))
     out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
     _check(lib().vqd_si_compile(ctypes.byref(d), len(a), _ptr(a), cnt.value, _ptr(out), ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def vqd_nv_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
+    """Compile a logical Rx/Ry/Rz/CRx+-(zx)/CRy+-(zy) circuit for an NV-centre device (host only).  ``dev``
+    holds n, t1, t2, freq_xy, freq_z, fid_xy, fid_z, x_xy, freq_crot, fid_crot, x_crot, freq_zz, fid_meas,
+    dur_meas and optional flags.  Returns the native-op array."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    keep = {k: np.ascontiguousarray(np.asarray(dev[k], dtype=np.float64))
+            for k in ("t1", "t2", "freq_xy", "freq_z", "fid_xy", "fid_z", "freq_crot", "fid_crot")}
+    p = lambda k: _ptr(keep[k])
+    d = nv_device(int(dev["n"]), p("t1"), p("t2"), p("freq_xy"), p("freq_z"), p("fid_xy"), p("fid_z"),
+                  float(dev["x_xy"]), p("freq_crot"), p("fid_crot"), float(dev["x_crot"]), float(dev["freq_zz"]),
+                  float(dev["fid_meas"]), float(dev["dur_meas"]), int(dev.get("flags", 0)))
+    cnt = ctypes.c_int()
+    _check(lib().vqd_nv_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), 0, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
+    _check(lib().vqd_nv_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
+                                ctypes.byref(cnt)))
     return out[: cnt.value].copy()
 
 

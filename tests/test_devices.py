@@ -251,3 +251,97 @@ def test_si_compiled_program_gpu_parity(vqd):
             assert np.abs(got - want).max() < TOL_F64, runner
         finally:
             vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- NV centre (Sec. 5, App. C)
+from oracle.devices import nv_compile  # noqa: E402
+from workloads.devices import NV5, nv_bcs_shape, nv_scaled  # noqa: E402
+
+
+def small_nv(**kw):
+    dev = {"n": 3, "t1": [100.0, 50.0, 40.0], "t2": [2.0, 8.0, 6.0], "freq_xy": [1e4, 500.0, 250.0],
+           "freq_z": [1e7, 4e5, 2e5], "fid_xy": [0.999, 0.995, 0.99], "fid_z": [1.0, 1.0, 0.999], "x_xy": 0.75,
+           "freq_crot": [1000.0, 2000.0], "fid_crot": [0.98, 0.97], "x_crot": 0.9, "freq_zz": 3.0,
+           "fid_meas": 0.95, "dur_meas": 2e-5}
+    dev.update(kw)
+    return dev
+
+
+def test_nv_worked_example_by_hand(vqd):
+    """Rx(pi/2) on nuclear spin 1 (500 Hz: t = 1/2000 s); CRy+-(1.2) from the electron to spin 2 (2000 Hz:
+    t = 1.2/(4000 pi) s); Rz(0.4) on the electron (1e7 Hz), during which the passive nuclear pair (1, 2)
+    feels the weak ZZ; Rz(0.3) on spin 2 (fidelity 0.999: a dephasing standard error)."""
+    dev = small_nv()
+    ops = [NativeOp("rx", (1,), (math.pi / 2,)), NativeOp("zy", (0, 2), (1.2,)), NativeOp("rz", (0,), (0.4,)),
+           NativeOp("rz", (2,), (0.3,))]
+    t1, t2, t3, t4 = 1 / 2000, 1.2 / (4000 * math.pi), 0.4 / (2e7 * math.pi), 0.3 / (4e5 * math.pi)
+    want = [ops[0], NativeOp("stderr1", (1,), (0.995, 0.75)),
+            NativeOp("idle_depol", (0,), (t1, 100.0, 2.0)), NativeOp("idle_depol", (2,), (t1, 40.0, 6.0)),
+            ops[1], NativeOp("stderr2", (0, 2), (0.97, 0.9)), NativeOp("idle_depol", (1,), (t2, 50.0, 8.0)),
+            ops[2], NativeOp("zz_idle", (1, 2), (t3, 3.0)),
+            NativeOp("idle_depol", (1,), (t3, 50.0, 8.0)), NativeOp("idle_depol", (2,), (t3, 40.0, 6.0)),
+            ops[3], NativeOp("stderr1", (2,), (0.999, 0.0)),
+            NativeOp("idle_depol", (0,), (t4, 100.0, 2.0)), NativeOp("idle_depol", (1,), (t4, 50.0, 8.0))]
+    same_ops(nv_compile(dev, ops), want, 1e-15)
+    same_ops(as_ops(vqd, vqd.vqd_nv_compile(dev, ops)), want, 1e-12)
+    tail = as_ops(vqd, vqd.vqd_nv_compile(dev, ops, readout=True))[len(want):]
+    same_ops(tail[:3], [NativeOp("rx", (0,), (math.pi,)), NativeOp("amp", (0,), (0.05,)),
+                        NativeOp("rx", (0,), (math.pi,))], 1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_nv_library_matches_oracle(vqd, seed):
+    for dev in (NV5, nv_scaled(NV5, 10.0 ** (seed - 1)), dict(NV5, flags=1), small_nv(freq_zz=0.0)):
+        ops = nv_bcs_shape(dev, 2, 60, seed=seed)
+        for readout in (False, True):
+            same_ops(as_ops(vqd, vqd.vqd_nv_compile(dev, ops, readout)), nv_compile(dev, ops, readout), 1e-12)
+
+
+def test_nv_readout_bias_closed_form():
+    """Sec. 5: the electron readout damps towards |1> between two X gates, so |0> reads 1 with probability
+    p = 1 - F and |1> always reads 1."""
+    dev = small_nv(fid_xy=[1.0, 1.0, 1.0], flags=1)
+    rho = evolve.run_program(Program(3, nv_compile(dev, [], readout=True)))
+    assert abs(measure.probs(rho, [0])[1] - 0.05) < 1e-14
+    rho = evolve.run_program(Program(3, nv_compile(dev, [NativeOp("rx", (0,), (math.pi,))], readout=True)))
+    assert abs(measure.probs(rho, [0])[1] - 1.0) < 1e-14
+
+
+def test_nv_weak_zz_phase_closed_form():
+    """Nuclear spins 1, 2 in |+>, then 50 electron rotations Rx(2 pi) of 1/f = 1 ms each: the passive pair
+    accumulates the weak ZZ phase, <X_1> = cos(pi f_zz T) with T = 0.05 s (conditional-frequency reading);
+    T1, T2 are made long enough not to matter."""
+    dev = small_nv(t1=[1e30] * 3, t2=[1e30] * 3, freq_xy=[1e3, 500.0, 500.0], fid_xy=[1.0] * 3)
+    ops = [NativeOp("ry", (1,), (math.pi / 2,)), NativeOp("ry", (2,), (math.pi / 2,))]
+    ops += [NativeOp("rx", (0,), (2 * math.pi,)) for _ in range(50)]
+    rho = evolve.run_program(Program(3, nv_compile(dev, ops)))
+    assert abs(measure.expect(rho, [[0, 1, 0]], [1.0]) - math.cos(math.pi * 3.0 * 0.05)) < 1e-12
+
+
+def test_nv_rejects_bad_input(vqd):
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_nv_compile(small_nv(), [NativeOp("zx", (1, 2), (0.3,))])    # not controlled by the electron
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_nv_compile(small_nv(), [NativeOp("cz", (0, 1))])
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_nv_compile(small_nv(freq_crot=[1000.0, 0.0]), [NativeOp("rx", (0,), (0.1,))])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p", ["f64", "split"])
+def test_nv_compiled_program_gpu_parity(vqd, p):
+    """Four BCS-shaped propagators (800 native gates) on the App. C NV centre, compiled by the library, plain
+    and fused, against the oracle's compile and evolution."""
+    from ._lib import tol_split
+    ops = nv_bcs_shape(NV5, 4, 200, seed=21)
+    lib_ops = vqd.vqd_nv_compile(NV5, ops, readout=True)
+    want = evolve.run_program(Program(5, nv_compile(NV5, ops, readout=True)))
+    t = TOL_F64 if p == "f64" else tol_split(len(lib_ops))
+    for runner in ("plain", "fused"):
+        ctx = vqd.vqd_create(5, vqd.VQD_F64 if p == "f64" else vqd.VQD_F32_SPLIT)
+        try:
+            (vqd.vqd_apply_native if runner == "plain" else vqd.vqd_run_program)(ctx, 0, lib_ops)
+            got = vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0))
+            assert np.abs(got - want).max() < t, runner
+        finally:
+            vqd.vqd_destroy(ctx)

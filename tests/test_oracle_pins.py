@@ -389,12 +389,26 @@ def test_static_zz_invariants():
         oc.static_zz_beta(0.1, -2.5, -2.5, -2.0)
 
 
+def test_nv_conditional_rotations_are_zx_and_zy():
+    """Sec. 5, Eq. (conditional_rots): |0><0|_c (x) R(theta)_t + |1><1|_c (x) R(-theta)_t is exp(-i theta/2 Z_c S_t)
+    for S = X (CRx+-, the zx op) and S = Y (CRy+-, the zy op); control = first (low) qubit."""
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Y = np.array([[0, -1j], [1j, 0]])
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    p0, p1 = np.diag([1.0, 0.0]), np.diag([0.0, 1.0])
+    for theta in (0.3, 1.9, -2.4):
+        crx = np.kron(oc.rx(theta), p0) + np.kron(oc.rx(-theta), p1)
+        assert np.abs(oc.zx(theta) - crx).max() < 1e-15
+        assert np.abs(oc.zy(theta) - expm(-0.5j * theta * np.kron(Y, Z))).max() < 1e-14
+        assert np.abs(oc.zx(theta) - expm(-0.5j * theta * np.kron(X, Z))).max() < 1e-14
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4
     prog = random_program(21, n, 60, names=["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi",
                                             "zx", "zz", "xx", "zzphase", "zz_idle", "crz_xtalk", "exchange",
-                                            "offres", "zz_static"])
+                                            "offres", "zz_static", "zy"])
     psi = np.zeros(2 ** n, dtype=complex)
     psi[0] = 1
     for o in prog.ops:

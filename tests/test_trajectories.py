@@ -13,7 +13,7 @@ from workloads.circuits import OP_NAMES, NativeOp, Program, random_program
 from ._lib import get_lib
 
 UNITARIES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
-             "crz_xtalk", "exchange", "offres", "zz_static"]
+             "crz_xtalk", "exchange", "offres", "zz_static", "zy"]
 
 
 def hamiltonian(n, rng, nterms=6):

@@ -57,6 +57,7 @@ OP_NAMES = {
     # device-family crosstalk unitaries
     "offres": (1, ("omega", "delta", "t")),    # off-resonant Rabi drive on a passive qubit, Eq. (off_resonant)
     "zz_static": (2, ("j", "delta", "alpha_t", "alpha_c")),  # SC static ZZ exp(-i beta Z Z), beta from J, Delta, alpha
+    "zy": (2, ("theta",)),            # NV conditional CRy+-(theta) = exp(-i theta/2 Z_c Y_t), Eq. (conditional_rots)
 }
 
 
@@ -352,5 +353,6 @@ def _random_params(r: np.random.Generator, name: str) -> Tuple[float, ...]:
         "leak_init": lambda: (u(0, 0.1),), "leak_cz": lambda: (u(0, 0.1), u(0, 0.01)),
         "offres": lambda: (u(0.5, 2.0), u(-8.0, 8.0), u(0.0, 3.0)),
         "zz_static": lambda: (u(0.02, 0.2), u(0.2, 1.0), u(-3.0, -2.0), u(-3.0, -2.0)),
+        "zy": lambda: (u(0, 2 * math.pi),),
     }
     return table[name]()

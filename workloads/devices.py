@@ -106,3 +106,50 @@ def si_circuit(dev: Dict, n_gates: int, seed: int = 9) -> List[NativeOp]:
             name = ("rx", "ry", "rz")[int(r.integers(0, 3))]
             ops.append(NativeOp(name, (int(r.integers(0, n)),), (float(r.uniform(-math.pi, math.pi)),)))
     return ops
+
+
+NV5 = {  # App. C, table of the virtual NV centre (seconds, Hz); qubit 0 = electron, 1..4 = 13C nuclear spins
+    "n": 5,
+    "t1": [3600.0, 60.0, 60.0, 60.0, 60.0],
+    "t2": [1.5, 10.0, 10.0, 10.0, 9.0],
+    "freq_zz": 3.0,
+    "freq_xy": [15000e3, 0.5e3, 0.5e3, 0.5e3, 0.5e3],
+    "freq_z": [32e6, 0.4e6, 0.4e6, 0.4e6, 0.4e6],
+    "freq_crot": [1.5e3, 2.8e3, 0.8e3, 2e3],
+    "fid_crot": [0.98, 0.98, 0.98, 0.98],
+    "fid_xy": [0.9995, 0.995, 0.995, 0.99, 0.99],
+    "fid_z": [1.0] * 5,
+    "x_xy": 0.75,          # depolarising:dephasing 0.75:0.25
+    "x_crot": 0.9,         # depolarising:dephasing 0.9:0.1
+    "fid_meas": 0.946,
+    "dur_meas": 2e-5,
+}
+
+
+def nv_scaled(dev: Dict, scale: float) -> Dict:
+    """The device with every error scaled by `scale` (infidelities times scale, T1 and T2 divided by it),
+    as in the paper's sweeps over the scale of noise."""
+    d = dict(dev)
+    for k in ("fid_xy", "fid_z", "fid_crot"):
+        d[k] = [1.0 - scale * (1.0 - f) for f in dev[k]]
+    d["fid_meas"] = 1.0 - scale * (1.0 - dev["fid_meas"])
+    d["t1"] = [t / scale for t in dev["t1"]]
+    d["t2"] = [t / scale for t in dev["t2"]]
+    d["freq_zz"] = dev["freq_zz"] * scale
+    return d
+
+
+def nv_bcs_shape(dev: Dict, n_props: int = 64, gates_per_prop: int = 200, seed: int = 13) -> List[NativeOp]:
+    """Synthetic circuit with the shape of the paper's BCS propagators on the NV star (Sec. 5): n_props
+    propagators of `gates_per_prop` native gates; about one gate in three is a conditional rotation
+    CRx+- / CRy+- from the electron to a nuclear spin, the rest single rotations on any spin."""
+    r = _rng(seed)
+    n = int(dev["n"])
+    ops: List[NativeOp] = []
+    for _ in range(n_props * gates_per_prop):
+        th = float(r.uniform(-math.pi, math.pi))
+        if r.uniform() < 1 / 3:
+            ops.append(NativeOp(("zx", "zy")[int(r.integers(0, 2))], (0, int(r.integers(1, n))), (th,)))
+        else:
+            ops.append(NativeOp(("rx", "ry", "rz")[int(r.integers(0, 3))], (int(r.integers(0, n)),), (th,)))
+    return ops
