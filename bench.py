@@ -242,7 +242,7 @@ def measure_sc_device(vqd, torch, stream_handle, timed, steps):
         vqd.vqd_destroy(ctx)
 
 
-def measure_nv_noise_sweep(vqd, torch, count=32, props=16):
+def measure_nv_noise_sweep(vqd, torch, count=256, props=16):
     """A second workload with the shape of the paper's NV-centre study (Sec. 5): a 5-qubit NV centre (App. C
     table) running BCS-shaped propagators of 200 native gates, swept over `count` noise scales (log-uniform
     0.1..10).  Each scale is one instance of one batched run (stage waves replayed as a CUDA graph)."""
