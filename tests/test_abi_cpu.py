@@ -175,3 +175,15 @@ def test_schedule_random_programs_match_oracle(vqd):
     for o, g in zip(orc, got):
         assert vqd.OP_CODES[g["code"]] == o.name and tuple(g["q"][: g["nq"]]) == o.qubits
         assert np.allclose(g["par"][: len(o.params)], o.params, rtol=0, atol=1e-15)
+
+
+def test_fused_plan_splits_tensor_product_channels(vqd):
+    """The fused planner applies a two-qubit channel that is a tensor product of one-qubit channels (T1/T2
+    decay of both qubits of a pair) as two one-qubit sweeps, and keeps a correlated one (depol2) dense."""
+    prod = [NativeOp("ampdeph2", (0, 2), (0.3, 40.0, 30.0))]
+    info = vqd.vqd_plan_info(4, vqd.VQD_F32, prod, fuse_qubits=4)
+    assert info["sup2"] == 0 and info["sup1"] == 2
+    corr = [NativeOp("depol2", (0, 2), (0.1,))]
+    info = vqd.vqd_plan_info(4, vqd.VQD_F32, corr, fuse_qubits=4)
+    assert info["sup2"] == 1 and info["sup1"] == 0
+
