@@ -358,6 +358,21 @@ def device_view(torch, ptr: int, count: int, prec_f32: bool):
     return torch.view_as_complex(t.view(-1, 2))
 
 
+def fp64_alu_roof(stats, n):
+    """FP64 elementwise passes as an ALU-bound kernel: a complex phase multiply is 4 FP64 instructions per
+    amplitude (2 DMUL + 2 DFMA), against 0.625e12 FP64 FMA instructions/s (the GPU's nominal 1.25 TFLOP/s
+    FP64; no measured FP64 peak is on file)."""
+    s = stats.get("elem")
+    if not s or not s.get("launches"):
+        return None
+    per_launch_s = s["total_ms"] * 1e-3 / s["launches"]
+    achieved = 4.0 * 4.0 ** n / per_launch_s
+    peak = 0.625e12
+    return {"bound": "alu", "kernel": "elem (k_diag1/k_diag2, complex factors)", "achieved": achieved, "peak": peak,
+            "unit": "FP64 instructions/s", "frac": achieved / peak, "peak_source": "nominal 1.25 TFLOP/s FP64",
+            "instructions_per_amplitude": 4}
+
+
 def split_view(torch, ptr: int, count: int):
     """Zero-copy view of a float-float state as (count, 4) float32 rows: re.hi, re.lo, im.hi, im.lo."""
     class _A:
@@ -593,6 +608,7 @@ def main():
         extra["plain_f64_sample"] = {"value": world * fp64_rate, "unit": UNIT,
                                      "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
                                      "roofline_hbm": droof,
+                                     "roofline_fp64_alu": fp64_alu_roof(dstats, n),
                                      "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
                                                    for k, v in dstats.items()}}
         vqd.vqd_destroy(ctx64)

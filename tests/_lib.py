@@ -3,7 +3,7 @@ import math
 
 import numpy as np
 
-# FP64 parity bar (north-star): max-abs difference to the FP64 oracle.
+# FP64 parity bar: max-abs difference to the FP64 oracle.
 TOL_F64 = 1e-12
 
 
