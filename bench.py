@@ -360,17 +360,18 @@ def device_view(torch, ptr: int, count: int, prec_f32: bool):
 
 def fp64_alu_roof(stats, n):
     """FP64 elementwise passes as an ALU-bound kernel: a complex phase multiply is 4 FP64 instructions per
-    amplitude (2 DMUL + 2 DFMA), against 0.625e12 FP64 FMA instructions/s (the GPU's nominal 1.25 TFLOP/s
-    FP64; no measured FP64 peak is on file)."""
+    amplitude it changes (2 DMUL + 2 DFMA; amplitudes with factor 1 are skipped), against 0.625e12 FP64 FMA
+    instructions/s (the GPU's nominal 1.25 TFLOP/s FP64; no measured FP64 peak is on file)."""
     s = stats.get("elem")
     if not s or not s.get("launches"):
         return None
     per_launch_s = s["total_ms"] * 1e-3 / s["launches"]
-    achieved = 4.0 * 4.0 ** n / per_launch_s
+    amps = s["alg_bytes"] / s["launches"] / 32.0        # amplitudes each launch reads and writes (16 B each way)
+    achieved = 4.0 * amps / per_launch_s
     peak = 0.625e12
     return {"bound": "alu", "kernel": "elem (k_diag1/k_diag2, complex factors)", "achieved": achieved, "peak": peak,
             "unit": "FP64 instructions/s", "frac": achieved / peak, "peak_source": "nominal 1.25 TFLOP/s FP64",
-            "instructions_per_amplitude": 4}
+            "instructions_per_changed_amplitude": 4}
 
 
 def split_view(torch, ptr: int, count: int):

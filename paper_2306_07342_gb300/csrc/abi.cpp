@@ -156,7 +156,7 @@ static void apply_op(vqd_ctx* c, int inst, const Op& op) {
   Pass p = classify(op);
   const int n = c->n[inst];
   static const int cls_of[4] = {SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2};
-  timed(c, cls_of[p.kind], 2.0 * c->bytes(inst), op.weight * std::ldexp(1.0, 2 * n), 1,
+  timed(c, cls_of[p.kind], 2.0 * c->bytes(inst) * pass_touched_fraction(p), op.weight * std::ldexp(1.0, 2 * n), 1,
         [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
 }
 
@@ -1011,7 +1011,8 @@ int vqd_measure(vqd_t c, int inst, int q, double u, int force, int* outcome, dou
   p.q[0] = q;
   p.coef.assign(4, 0.0);
   p.coef[m | (m << 1)] = 1.0 / pm;
-  timed(c, SC_ELEM, 2.0 * c->bytes(inst), 0, 1, [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
+  timed(c, SC_ELEM, 2.0 * c->bytes(inst) * pass_touched_fraction(p), 0, 1,
+        [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
   if (outcome) *outcome = m;
   if (prob) *prob = pm / tot;
   API_END(c)

@@ -214,17 +214,22 @@ __device__ __forceinline__ void scale(cx<T>& v, const cx<T>& f) {
   if (REAL) { v.x *= f.x; v.y *= f.x; }
   else { const T re = fma(v.x, f.x, -v.y * f.y); v.y = fma(v.x, f.y, v.y * f.x); v.x = re; }
 }
-template <class T> struct Diag1P { Group<4> g; cx<T> f[4]; };
-template <class T> struct Diag2P { Group<16> g; cx<T> f[16]; };
+// skip: members whose factor is exactly 1 (bit s for member s).  They are neither read nor written:
+// a diagonal phase or dephasing leaves half of the amplitudes unchanged (those whose row and column
+// bits agree on the targets, or have equal parity), so the pass moves half the bytes.
+template <class T> struct Diag1P { Group<4> g; cx<T> f[4]; uint32_t skip; };
+template <class T> struct Diag2P { Group<16> g; cx<T> f[16]; uint32_t skip; };
 template <class T, bool REAL>
 __global__ void __launch_bounds__(256) k_diag1(cx<T>* __restrict__ st, uint64_t ngroups, const Diag1P<T> P) {
   GRID_STRIDE_LOOP(g, ngroups) {
     const uint64_t base = insert_zeros<2>(g, P.g.pos);
     cx<T> x[4];
 #pragma unroll
-    for (int s = 0; s < 4; s++) x[s] = st[base + P.g.off[s]];
+    for (int s = 0; s < 4; s++)
+      if (!(P.skip >> s & 1u)) x[s] = st[base + P.g.off[s]];
 #pragma unroll
-    for (int s = 0; s < 4; s++) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
+    for (int s = 0; s < 4; s++)
+      if (!(P.skip >> s & 1u)) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
   }
 }
 template <class T, bool REAL>
@@ -233,9 +238,11 @@ __global__ void __launch_bounds__(256) k_diag2(cx<T>* __restrict__ st, uint64_t 
     const uint64_t base = insert_zeros<4>(g, P.g.pos);
     cx<T> x[16];
 #pragma unroll
-    for (int s = 0; s < 16; s++) x[s] = st[base + P.g.off[s]];
+    for (int s = 0; s < 16; s++)
+      if (!(P.skip >> s & 1u)) x[s] = st[base + P.g.off[s]];
 #pragma unroll
-    for (int s = 0; s < 16; s++) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
+    for (int s = 0; s < 16; s++)
+      if (!(P.skip >> s & 1u)) { scale<T, REAL>(x[s], P.f[s]); st[base + P.g.off[s]] = x[s]; }
   }
 }
 
@@ -440,14 +447,22 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
     if (p.k == 1) {
       Diag1P<T> P;
       P.g = make_group<4>(n, 1, p.q);
-      for (int i = 0; i < 4; i++) P.f[i] = to_cx<T>(p.coef[i]);
+      P.skip = 0;
+      for (int i = 0; i < 4; i++) {
+        P.f[i] = to_cx<T>(p.coef[i]);
+        if (is_unit_factor(p.coef[i])) P.skip |= 1u << i;
+      }
       const uint64_t ng = N / 4;
       if (real) k_diag1<T, true><<<grid_for(k_diag1<T, true>, ng), 256, 0, s>>>(st, ng, P);
       else k_diag1<T, false><<<grid_for(k_diag1<T, false>, ng), 256, 0, s>>>(st, ng, P);
     } else {
       Diag2P<T> P;
       P.g = make_group<16>(n, 2, p.q);
-      for (int i = 0; i < 16; i++) P.f[i] = to_cx<T>(p.coef[i]);
+      P.skip = 0;
+      for (int i = 0; i < 16; i++) {
+        P.f[i] = to_cx<T>(p.coef[i]);
+        if (is_unit_factor(p.coef[i])) P.skip |= 1u << i;
+      }
       const uint64_t ng = N / 16;
       if (real) k_diag2<T, true><<<grid_for(k_diag2<T, true>, ng), 256, 0, s>>>(st, ng, P);
       else k_diag2<T, false><<<grid_for(k_diag2<T, false>, ng), 256, 0, s>>>(st, ng, P);
@@ -491,6 +506,14 @@ static cudaError_t launch_pass_t(cx<T>* st, int n, const Pass& p, cudaStream_t s
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
+}
+
+double pass_touched_fraction(const Pass& p) {
+  if (p.kind != KK_ELEM) return 1.0;
+  int touched = 0;
+  for (const cd& c : p.coef)
+    if (!is_unit_factor(c)) touched++;
+  return p.coef.empty() ? 1.0 : (double)touched / (double)p.coef.size();
 }
 
 cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <complex>
 #include <cstdint>
 #include <vector>
 
@@ -11,6 +12,15 @@
 namespace vqd {
 
 // Launch one plain-path pass over an n-qubit state (complex64 if prec == VQD_F32, else complex128).
+// A diagonal factor within a few ulps of 1: the entries |d_r|^2 of a diagonal unitary's superoperator
+// are exactly 1 but arrive rounded from their FP64 product.  Elementwise passes leave such amplitudes
+// untouched (factor exactly 1).
+inline bool is_unit_factor(const std::complex<double>& c) {
+  return std::abs(c.real() - 1.0) <= 1e-15 && std::abs(c.imag()) <= 1e-15;
+}
+// Fraction of the state's amplitudes a plain pass reads and writes: elementwise passes skip the
+// amplitudes whose factor is 1; every other pass touches all of them.
+double pass_touched_fraction(const Pass& p);
 cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s);
 
 // Initialisation.
