@@ -294,6 +294,10 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
     BlockOp bo;
     bo.coef = (int)plan.coef.size() - sd.coef_begin;
     bo.kind = member_coefs(o, o.k, o.q, plan.coef);
+    bo.skip = 0;
+    if (bo.kind == BK_DIAG_A || bo.kind == BK_DIAG_B || bo.kind == BK_DIAG2)
+      for (size_t t = (size_t)bo.coef + sd.coef_begin; t < plan.coef.size(); t++)
+        if (is_unit_factor(plan.coef[t])) bo.skip |= 1u << (t - bo.coef - sd.coef_begin);
     plan.ops.push_back(bo);
     sd.weight += o.weight;
     tb.op_end = (int)plan.ops.size();
@@ -568,7 +572,7 @@ __device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx
 // sw(base) ^ sw(off), so a member address costs one XOR.
 template <class T, bool DIAG>
 __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
-                                       const cx<T>* __restrict__ c) {
+                                       const cx<T>* __restrict__ c, uint32_t skip) {
   const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
   const uint32_t ng = 1u << (nbits - 2);
   cx<T> S[DIAG ? 4 : 16];
@@ -580,12 +584,16 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
     const uint32_t b = sw<T>(ins(g));
     const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
     cx<T> x[4];
+    if (DIAG) {  // members with factor 1 are left as they are
 #pragma unroll
-    for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
-    if (DIAG) {
+      for (int t = 0; t < 4; t++)
+        if (!(skip >> t & 1u)) x[t] = sm[a[t]];
 #pragma unroll
-      for (int t = 0; t < 4; t++) sm[a[t]] = cmul<T>(x[t], S[t]);
+      for (int t = 0; t < 4; t++)
+        if (!(skip >> t & 1u)) sm[a[t]] = cmul<T>(x[t], S[t]);
     } else {
+#pragma unroll
+      for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
 #pragma unroll
       for (int t = 0; t < 4; t++) {
         cx<T> y;
@@ -601,7 +609,7 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
 // kind: BK_DIAG2, BK_UNI2 (U A U^dagger on the 4x4 block A[r][c] = member r | c << 2) or BK_SUP2
 template <class T, int KIND>
 __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
-                                       const cx<T>* __restrict__ c) {
+                                       const cx<T>* __restrict__ c, uint32_t skip) {
   uint32_t soff[16];
 #pragma unroll
   for (int s = 0; s < 16; s++) {
@@ -618,16 +626,22 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
     for (int i = 0; i < 16; i++) u[i] = c[i];
   }
   const Inserter<4> ins(B.lsorted);
+  if constexpr (KIND == BK_DIAG2) {  // members with factor 1 are left as they are
+  #pragma unroll 1
+    for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
+      const uint32_t b = sw<T>(ins(g));
+#pragma unroll
+      for (int s = 0; s < 16; s++)
+        if (!(skip >> s & 1u)) sm[b ^ soff[s]] = cmul<T>(sm[b ^ soff[s]], u[s]);
+    }
+  } else {
   #pragma unroll 1
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     cx<T> x[16];
 #pragma unroll
     for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
-    if (KIND == BK_DIAG2) {
-#pragma unroll
-      for (int s = 0; s < 16; s++) sm[b ^ soff[s]] = cmul<T>(x[s], u[s]);
-    } else if (KIND == BK_UNI2) {
+    if (KIND == BK_UNI2) {
 #pragma unroll
       for (int cc = 0; cc < 4; cc++) {  // columns: A[:,c] <- U A[:,c]
         cx<T> t[4];
@@ -671,6 +685,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
       }
     }
   }
+}  // KIND != BK_DIAG2
 }
 
 // Apply the stage's operators (one block each) to the tile, one sweep per operator.
@@ -683,11 +698,11 @@ __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>*
     const BlockOp bo = sops[B.op_begin - op0];
     const cx<T>* c = csm + bo.coef;
     switch (bo.kind) {
-      case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c); break;
-      case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c); break;
-      case BK_DIAG2: sweep2<T, BK_DIAG2>(sm, nbits, B, c); break;
-      case BK_UNI2: sweep2<T, BK_UNI2>(sm, nbits, B, c); break;
-      default: sweep2<T, BK_SUP2>(sm, nbits, B, c); break;
+      case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c, bo.skip); break;
+      case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c, 0u); break;
+      case BK_DIAG2: sweep2<T, BK_DIAG2>(sm, nbits, B, c, bo.skip); break;
+      case BK_UNI2: sweep2<T, BK_UNI2>(sm, nbits, B, c, 0u); break;
+      default: sweep2<T, BK_SUP2>(sm, nbits, B, c, 0u); break;
     }
     __syncthreads();
   }

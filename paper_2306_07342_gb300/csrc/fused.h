@@ -18,7 +18,8 @@ enum BlockOpKind { BK_DIAG_A = 0, BK_SUP1_A, BK_DIAG_B, BK_SUP1_B, BK_DIAG2, BK_
 
 struct BlockOp {
   int kind;
-  int coef;  // offset within the stage's coefficients
+  int coef;       // offset within the stage's coefficients
+  uint32_t skip;  // diagonal kinds: members whose factor is 1 (left untouched)
 };
 
 // A block: operators acting within one qubit (nq = 1) or one pair (nq = 2), applied back to back
