@@ -222,6 +222,31 @@ def test_split_precision_is_fp64_class(vqd):
         assert err["split", path] < 1e-4 * err["f32", path], err
 
 
+@pytest.mark.parametrize("p", ["f32", "f64"])
+def test_diagonal_passes_touch_only_changed_amplitudes(vqd, p):
+    """A phase (Rz, ZZ crosstalk) or a dephasing leaves half of the amplitudes unchanged (factor exactly 1);
+    the elementwise pass skips them, so its accounted bytes are half of a full pass, and results match."""
+    n = 6
+    rng = np.random.default_rng(77)
+    rho = rand_state(n, rng)
+    ops = [NativeOp("rz", (3,), (0.9,)), NativeOp("zz_idle", (1, 4), (0.3, 0.2)), NativeOp("deph1", (5,), (0.2,)),
+           NativeOp("sx", (2,))]
+    ctx = make_ctx(vqd, n, p, rho)
+    try:
+        vqd.vqd_profile(ctx, 2)
+        vqd.vqd_profile_reset(ctx)
+        vqd.vqd_apply_native(ctx, 0, ops)
+        st = vqd.vqd_profile_read(ctx)
+        vqd.vqd_profile(ctx, 0)
+        full = 2 * vqd.vqd_state_bytes(n, prec_code(vqd, p))
+        assert st["elem"]["launches"] == 3 and abs(st["elem"]["alg_bytes"] - 3 * full / 2) < 1
+        assert st["sup1"]["launches"] == 1 and abs(st["sup1"]["alg_bytes"] - full) < 1
+        want = evolve.run_program(Program(n, ops), rho0=rho)
+        assert np.abs(gpu_state(vqd, ctx) - want).max() < tol(p, len(ops))
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
 # ---------------------------------------------------------------- reductions
 @pytest.mark.parametrize("p", PRECS)
 def test_reductions(vqd, p):
