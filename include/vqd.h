@@ -301,13 +301,15 @@ typedef struct {
 
 /* Compile a logical circuit of Rx, Ry, Rz, CZ, CPh ops (CZ/CPh on neighbours; others: VQD_EINVAL) for
  * the device.  Gates run one at a time, in program order.  Rz: virtual, emitted alone.  Rx/Ry(theta) on
- * q, lasting t = |theta| / (2 pi rabi_q): the gate; stderr1(fid_1q[q], x_1q); with t > 0, for every
+ * q, lasting t = |theta| / (2 pi rabi_q): the gate; its standard error (below) from fid_1q[q], x_1q; with t > 0, for every
  * j != q, offres(2 pi rabi_q, 2 pi |f_j - f_q|, t); for every j != q, idle_depol(t, T1_j, T2_j); for
  * every pair (k, k+1) not containing q, crz_xtalk(xtalk_off[k]) (when given and nonzero).  CZ or
  * CPh(theta) on (k, k+1) (CZ: theta = pi), lasting t = |theta| / (2 pi freq_cz[k]): the gate;
- * stderr2(fid_cz[k], x_cz) on the gate's qubits; for every other pair j, crz_xtalk(xtalk_on[k][j]
+ * its standard error from fid_cz[k], x_cz on the gate's qubits; for every other pair j, crz_xtalk(xtalk_on[k][j]
  * theta / pi) on (j, j+1) (when given and nonzero); idle_depol(t, ...) on every qubit outside the pair.
- * out == NULL only counts; otherwise out has room for cap ops (VQD_EINVAL if too few). */
+ * A gate's standard error is App. B's deph(p) o depol(q) for its fidelity and depolarising fraction, with
+ * App. C's angle rule (severities times |theta| / pi): depol(q |theta|/pi) then deph(p |theta|/pi), each
+ * left out when zero.  out == NULL only counts; otherwise out has room for cap ops (VQD_EINVAL if too few). */
 int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, int cap, vqd_native_op* out,
                    int* nout);
 
@@ -336,9 +338,11 @@ typedef struct {
 /* Compile a logical circuit of Rx, Ry, Rz on any qubit and the conditional rotations CRx+- (VQD_OP_ZX)
  * and CRy+- (VQD_OP_ZY) with control 0 and a nuclear target (others: VQD_EINVAL) for the device.  Gates
  * run one at a time, in program order.  Rx/Ry(theta) on q lasts t = |theta| / (2 pi freq_xy[q]) and is
- * followed by stderr1(fid_xy[q], x_xy); Rz(theta) lasts |theta| / (2 pi freq_z[q]) and is followed by
- * stderr1(fid_z[q], 0) when fid_z[q] < 1; a conditional rotation theta on (0, j) lasts
- * |theta| / (2 pi freq_crot[j-1]) and is followed by stderr2(fid_crot[j-1], x_crot).  During a gate of
+ * followed by its standard error from fid_xy[q], x_xy; Rz(theta) lasts |theta| / (2 pi freq_z[q]) and is
+ * followed by a dephasing standard error from fid_z[q] when fid_z[q] < 1; a conditional rotation theta on
+ * (0, j) lasts |theta| / (2 pi freq_crot[j-1]) and is followed by its two-qubit standard error from
+ * fid_crot[j-1], x_crot.  Standard errors are depol(q |theta|/pi) then deph(p |theta|/pi) (App. B's
+ * severities with App. C's angle rule; zero ones left out).  During a gate of
  * length t > 0, on the qubits outside it: zz_idle(t, freq_zz) on every pair (i, k), 1 <= i < k, of
  * nuclear spins (when freq_zz != 0), then idle_depol(t, T1_j, T2_j) on every such qubit j.  With
  * readout != 0, the electron readout bias ends the program: rx(pi), amp(1 - fid_meas), rx(pi) on

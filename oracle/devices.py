@@ -29,6 +29,8 @@ from typing import Dict, List, Sequence
 
 from workloads.circuits import NativeOp
 
+from .compile import stderr_params
+
 DURATION_KEYS = {"rx": "dur_rxy", "ry": "dur_rxy", "zx": "dur_zx", "zz": "dur_zz"}
 
 
@@ -102,6 +104,19 @@ def sc_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Lis
     return out
 
 
+def scaled_standard_error(nq: int, qubits, fbar: float, x: float, theta: float) -> List[NativeOp]:
+    """Standard error of a parameterised gate (Sec. 3.2, App. B) with App. C's angle rule: every severity is
+    scaled by |theta| / pi. deph(p) o depol(q) becomes depol(q s) then deph(p s); zero severities are dropped."""
+    p, q = stderr_params(fbar, x, nq)
+    s = abs(theta) / math.pi
+    out = []
+    if q * s > 0:
+        out.append(NativeOp("depol1" if nq == 1 else "depol2", tuple(qubits), (q * s,)))
+    if p * s > 0:
+        out.append(NativeOp("deph1" if nq == 1 else "deph2", tuple(qubits), (p * s,)))
+    return out
+
+
 # ------------------------------------------------------------------ silicon spin qubits (Sec. 7, App. C)
 def si_compile(dev: Dict, ops: Sequence[NativeOp]) -> List[NativeOp]:
     """Logical circuit -> native op list of the silicon device (Sec. 7, App. C).
@@ -137,7 +152,7 @@ def si_compile(dev: Dict, ops: Sequence[NativeOp]) -> List[NativeOp]:
             rabi = float(dev["rabi"][q])
             t = abs(op.params[0]) / (2 * math.pi * rabi)
             out.append(op)
-            out.append(NativeOp("stderr1", (q,), (float(dev["fid_1q"][q]), float(dev["x_1q"]))))
+            out += scaled_standard_error(1, (q,), float(dev["fid_1q"][q]), float(dev["x_1q"]), op.params[0])
             if offres and t > 0:
                 for j in range(n):
                     if j != q:
@@ -156,7 +171,7 @@ def si_compile(dev: Dict, ops: Sequence[NativeOp]) -> List[NativeOp]:
             theta = math.pi if op.name == "cz" else op.params[0]
             t = abs(theta) / (2 * math.pi * float(dev["freq_cz"][k]))
             out.append(op)
-            out.append(NativeOp("stderr2", (a, b), (float(dev["fid_cz"][k]), float(dev["x_cz"]))))
+            out += scaled_standard_error(2, (a, b), float(dev["fid_cz"][k]), float(dev["x_cz"]), theta)
             if xon is not None:
                 for j in range(n - 1):
                     d = float(xon[k][j])
@@ -211,9 +226,9 @@ def nv_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Lis
             t = abs(op.params[0]) / (2 * math.pi * float(f))
             out.append(op)
             if op.name != "rz":
-                out.append(NativeOp("stderr1", (q,), (float(dev["fid_xy"][q]), float(dev["x_xy"]))))
+                out += scaled_standard_error(1, (q,), float(dev["fid_xy"][q]), float(dev["x_xy"]), op.params[0])
             elif dev["fid_z"][q] < 1:
-                out.append(NativeOp("stderr1", (q,), (float(dev["fid_z"][q]), 0.0)))
+                out += scaled_standard_error(1, (q,), float(dev["fid_z"][q]), 0.0, op.params[0])
             outside((q,), t)
         elif op.name in ("zx", "zy"):
             c, j = op.qubits
@@ -221,7 +236,7 @@ def nv_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Lis
                 raise ValueError("conditional rotations are controlled by the electron spin (qubit 0)")
             t = abs(op.params[0]) / (2 * math.pi * float(dev["freq_crot"][j - 1]))
             out.append(op)
-            out.append(NativeOp("stderr2", (0, j), (float(dev["fid_crot"][j - 1]), float(dev["x_crot"]))))
+            out += scaled_standard_error(2, (0, j), float(dev["fid_crot"][j - 1]), float(dev["x_crot"]), op.params[0])
             outside((0, j), t)
         else:
             raise ValueError(f"{op.name} is not an NV-centre native gate")

@@ -766,6 +766,15 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
     o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
     put(o);
   };
+  // App. C: the error severities of a parameterised gate scale with its angle, eps -> eps |theta| / pi.
+  // The standard error deph(p) o depol(q) of the gate's fidelity (App. B) becomes depol(q s) then deph(p s).
+  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
+    double pd, qd;
+    stderr_params(nq, fbar, x, &pd, &qd);
+    const double sc = std::fabs(theta) / 3.14159265358979323846;
+    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
+    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
+  };
   auto decay_others = [&](int a, int b, double t) {  // passive qubits over the gate's duration
     if (!passive || t <= 0) return;
     for (int j = 0; j < n; j++)
@@ -786,7 +795,7 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
       const int q = o.q[0];
       const double t = std::fabs(o.par[0]) / (two_pi * dev->rabi[q]);  // rotation angle 2 pi f_Rabi t
       put(o);
-      emit(VQD_OP_STDERR1, q, -1, dev->fid_1q[q], dev->x_1q, 0);
+      scaled_stderr(1, q, -1, dev->fid_1q[q], dev->x_1q, o.par[0]);
       if (offres && t > 0)
         for (int j = 0; j < n; j++)
           if (j != q)
@@ -804,7 +813,7 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
       const double theta = o.code == VQD_OP_CZ ? 3.14159265358979323846 : o.par[0];
       const double t = std::fabs(theta) / (two_pi * dev->freq_cz[k]);  // conditional phase 2 pi f_CZ t
       put(o);
-      emit(VQD_OP_STDERR2, a, b, dev->fid_cz[k], dev->x_cz, 0);
+      scaled_stderr(2, a, b, dev->fid_cz[k], dev->x_cz, theta);
       if (dev->xtalk_on)
         for (int j = 0; j + 1 < n; j++) {
           const double d = dev->xtalk_on[k * (n - 1) + j];
@@ -863,6 +872,15 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
     o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
     put(o);
   };
+  // App. C: the error severities of a parameterised gate scale with its angle, eps -> eps |theta| / pi.
+  // The standard error deph(p) o depol(q) of the gate's fidelity (App. B) becomes depol(q s) then deph(p s).
+  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
+    double pd, qd;
+    stderr_params(nq, fbar, x, &pd, &qd);
+    const double sc = std::fabs(theta) / 3.14159265358979323846;
+    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
+    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
+  };
   auto passive_noise = [&](int a, int b, double t) {  // qubits outside the gate, for its duration
     if (!passive || t <= 0) return;
     if (dev->freq_zz != 0)
@@ -884,8 +902,8 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
       const bool z = o.code == VQD_OP_RZ;
       const double t = std::fabs(o.par[0]) / (two_pi * (z ? dev->freq_z[q] : dev->freq_xy[q]));
       put(o);
-      if (!z) emit(VQD_OP_STDERR1, q, -1, dev->fid_xy[q], dev->x_xy, 0);
-      else if (dev->fid_z[q] < 1) emit(VQD_OP_STDERR1, q, -1, dev->fid_z[q], 0.0, 0);
+      if (!z) scaled_stderr(1, q, -1, dev->fid_xy[q], dev->x_xy, o.par[0]);
+      else if (dev->fid_z[q] < 1) scaled_stderr(1, q, -1, dev->fid_z[q], 0.0, o.par[0]);
       passive_noise(q, -1, t);
       continue;
     }
@@ -895,7 +913,7 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
       const int j = o.q[1];
       const double t = std::fabs(o.par[0]) / (two_pi * dev->freq_crot[j - 1]);
       put(o);
-      emit(VQD_OP_STDERR2, 0, j, dev->fid_crot[j - 1], dev->x_crot, 0);
+      scaled_stderr(2, 0, j, dev->fid_crot[j - 1], dev->x_crot, o.par[0]);
       passive_noise(0, j, t);
       continue;
     }

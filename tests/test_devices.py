@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import evolve, measure
+from oracle.compile import stderr_params as oc_stderr
 from oracle.devices import sc_compile
 from workloads.circuits import NativeOp, Program
 from workloads.devices import SC6, sc_ansatz, sc_grid_device
@@ -179,15 +180,19 @@ def small_si(**kw):
 
 
 def test_si_worked_example_by_hand(vqd):
-    """Rx(pi/2) on q1 (Rabi 4 MHz: t = 1/16 us); CZ on (0,1) (12 MHz: t = 1/24 us); virtual Rz on q2."""
+    """Rx(pi/2) on q1 (Rabi 4 MHz: t = 1/16 us); CZ on (0,1) (12 MHz: t = 1/24 us); virtual Rz on q2.  The
+    standard errors follow App. C's angle rule: severities times |theta| / pi."""
     dev = small_si()
     ops = [NativeOp("rx", (1,), (math.pi / 2,)), NativeOp("cz", (0, 1)), NativeOp("rz", (2,), (0.4,))]
     t1, t2 = 1 / 16, 1 / 24
     w = 2 * math.pi
-    want = [ops[0], NativeOp("stderr1", (1,), (0.997, 0.25)),
+    p1, q1 = oc_stderr(0.997, 0.25, 1)                   # App. B inversion (pinned in the oracle tests)
+    p2, q2 = oc_stderr(0.95, 0.5, 2)
+    want = [ops[0], NativeOp("depol1", (1,), (q1 / 2,)), NativeOp("deph1", (1,), (p1 / 2,)),   # |theta|/pi = 1/2
             NativeOp("offres", (0,), (w * 4.0, w * 300.0, t1)), NativeOp("offres", (2,), (w * 4.0, w * 400.0, t1)),
             NativeOp("idle_depol", (0,), (t1, 1e4, 20.0)), NativeOp("idle_depol", (2,), (t1, 3e4, 40.0)),
-            ops[1], NativeOp("stderr2", (0, 1), (0.95, 0.5)), NativeOp("crz_xtalk", (1, 2), (0.02,)),
+            ops[1], NativeOp("depol2", (0, 1), (q2,)), NativeOp("deph2", (0, 1), (p2,)),             # CZ: theta = pi
+            NativeOp("crz_xtalk", (1, 2), (0.02,)),
             NativeOp("idle_depol", (2,), (t2, 3e4, 40.0)), ops[2]]
     same_ops(si_compile(dev, ops), want, 1e-13)
     same_ops(as_ops(vqd, vqd.vqd_si_compile(dev, ops)), want, 1e-12)
@@ -219,14 +224,14 @@ def test_si_off_resonant_rabi_population():
 
 
 def test_si_single_qubit_error_is_dephasing_of_the_tabulated_fidelity():
-    """With the table's 0:1 split (pure dephasing), each x/y gate multiplies the coherence by 1 - 2p with
-    p = 1 - F_e and F_e = (3F - 1)/2 (App. B): Ry(pi/2) then Rx(0) leave <X> = (3F - 2)^2."""
+    """With the table's 0:1 split (pure dephasing) the severity is p = 1 - F_e, F_e = (3F - 1)/2 (App. B), scaled by
+    |theta|/pi (App. C): Ry(pi/2) dephases with p/2, so <X> = 1 - p = F_e; Rx(0) adds no error."""
     F = 0.9977
     dev = small_si(n=2, fid_1q=[F, 1.0], x_1q=0.0, freq_cz=[10.0], fid_cz=[1.0], xtalk_on=None, xtalk_off=None,
                    flags=3)
     rho = evolve.run_program(Program(2, si_compile(dev, [NativeOp("ry", (0,), (math.pi / 2,)),
                                                          NativeOp("rx", (0,), (0.0,))])))
-    assert abs(measure.expect(rho, [[1, 0]], [1.0]) - (3 * F - 2) ** 2) < 1e-13
+    assert abs(measure.expect(rho, [[1, 0]], [1.0]) - (3 * F - 1) / 2) < 1e-13
 
 
 def test_si_rejects_bad_input(vqd):
@@ -275,12 +280,17 @@ def test_nv_worked_example_by_hand(vqd):
     ops = [NativeOp("rx", (1,), (math.pi / 2,)), NativeOp("zy", (0, 2), (1.2,)), NativeOp("rz", (0,), (0.4,)),
            NativeOp("rz", (2,), (0.3,))]
     t1, t2, t3, t4 = 1 / 2000, 1.2 / (4000 * math.pi), 0.4 / (2e7 * math.pi), 0.3 / (4e5 * math.pi)
-    want = [ops[0], NativeOp("stderr1", (1,), (0.995, 0.75)),
+    pa, qa = oc_stderr(0.995, 0.75, 1)
+    pb, qb = oc_stderr(0.97, 0.9, 2)
+    pz, _ = oc_stderr(0.999, 0.0, 1)
+    sb, sz = 1.2 / math.pi, 0.3 / math.pi                 # App. C: severities times |theta| / pi
+    want = [ops[0], NativeOp("depol1", (1,), (qa / 2,)), NativeOp("deph1", (1,), (pa / 2,)),
             NativeOp("idle_depol", (0,), (t1, 100.0, 2.0)), NativeOp("idle_depol", (2,), (t1, 40.0, 6.0)),
-            ops[1], NativeOp("stderr2", (0, 2), (0.97, 0.9)), NativeOp("idle_depol", (1,), (t2, 50.0, 8.0)),
+            ops[1], NativeOp("depol2", (0, 2), (qb * sb,)), NativeOp("deph2", (0, 2), (pb * sb,)),
+            NativeOp("idle_depol", (1,), (t2, 50.0, 8.0)),
             ops[2], NativeOp("zz_idle", (1, 2), (t3, 3.0)),
             NativeOp("idle_depol", (1,), (t3, 50.0, 8.0)), NativeOp("idle_depol", (2,), (t3, 40.0, 6.0)),
-            ops[3], NativeOp("stderr1", (2,), (0.999, 0.0)),
+            ops[3], NativeOp("deph1", (2,), (pz * sz,)),
             NativeOp("idle_depol", (0,), (t4, 100.0, 2.0)), NativeOp("idle_depol", (1,), (t4, 50.0, 8.0))]
     same_ops(nv_compile(dev, ops), want, 1e-15)
     same_ops(as_ops(vqd, vqd.vqd_nv_compile(dev, ops)), want, 1e-12)
