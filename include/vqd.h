@@ -118,7 +118,9 @@ typedef enum {
   VQD_OP_ZY = 34,       /* q0 = control, q1 = target; theta: NV conditional rotation CRy+-(theta) =
                            |0><0| (x) Ry(theta) + |1><1| (x) Ry(-theta) = exp(-i theta/2 Z Y), Sec. 5
                            Eq. (conditional_rots); CRx+- is VQD_OP_ZX                                   */
-  VQD_OP_COUNT = 35
+  VQD_OP_IDLE_T2S = 35, /* q0; dt, T1, T2*: depol(3/4(1-e^{-dt/T1})) then deph(1/2(1-e^{-(dt/T2*)^2})), Eqs. (depolt1),
+                           (depht2s): passive decay with a Gaussian T2* (VQD_T2_IS_TOTAL does not apply)      */
+  VQD_OP_COUNT = 36
 } vqd_op_code;
 
 typedef struct {

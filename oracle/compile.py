@@ -256,6 +256,11 @@ def t2_deph_param(dt, t2):
     return 0.5 * (1 - math.exp(-dt / t2))
 
 
+def t2s_deph_param(dt, t2s):
+    """Eq. (depht2s): deph(1/2 (1 - exp(-(dt/T2*)^2))), the Gaussian free-induction decay."""
+    return 0.5 * (1 - math.exp(-((dt / t2s) ** 2)))
+
+
 def pure_dephasing_time(t1, t2):
     """T_phi with 1/T2 = 1/(2 T1) + 1/T_phi (used when T2 is read as the total coherence time)."""
     return 1.0 / (1.0 / t2 - 1.0 / (2.0 * t1))
@@ -337,6 +342,9 @@ def compile_op(name: str, qubits: Sequence[int], params: Sequence[float], t2_is_
             return [("K", q, depol1(t1_depol_param(dt, t1))), ("K", q, dephk)]
         one = compose_kraus(amp(t1_damping_param(dt, t1)), dephk)   # deph o amp on one qubit
         return [("K", q, tensor_kraus(one, one))]
+    if name == "idle_t2s":          # Eq. (depolt1) then Eq. (depht2s)
+        dt, t1, t2s = P
+        return [("K", q, depol1(t1_depol_param(dt, t1))), ("K", q, deph1(t2s_deph_param(dt, t2s)))]
     if name in ("stderr1", "stderr2"):
         nq = 1 if name == "stderr1" else 2
         p, qd = stderr_params(P[0], P[1], nq)

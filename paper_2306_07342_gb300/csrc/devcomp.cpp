@@ -172,6 +172,10 @@ Mat sup_tensor(const Mat& lo, const Mat& hi) {
 double t1_amp_p(double dt, double t1) { return 1 - std::exp(-dt / t1); }           // Eq. (ampt1)
 double t1_depol_p(double dt, double t1) { return 0.75 * (1 - std::exp(-dt / t1)); } // Eq. (depolt1)
 double t2_deph_p(double dt, double t2) { return 0.5 * (1 - std::exp(-dt / t2)); }   // Eq. (depht2)
+double t2s_deph_p(double dt, double t2s) {                                            // Eq. (depht2s)
+  const double x = dt / t2s;
+  return 0.5 * (1 - std::exp(-x * x));
+}
 double dephasing_time(double t1, double t2, unsigned flags) {
   if (!(flags & VQD_T2_IS_TOTAL)) return t2;
   double inv = 1.0 / t2 - 1.0 / (2.0 * t1);
@@ -187,7 +191,7 @@ void require(bool ok, const char* msg) {
 
 int native_arity(int code) {
   static const int ar[VQD_OP_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2,
-                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2, 2};
+                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2, 2, 1};
   if (code < 0 || code >= VQD_OP_COUNT) return -1;
   return ar[code];
 }
@@ -284,6 +288,10 @@ Op compile_native(const vqd_native_op& o, unsigned flags) {
       if (o.code == VQD_OP_AMPDEPH2) S(sup_tensor(one, one)); else S(one);
       break;
     }
+    case VQD_OP_IDLE_T2S:
+      require(P[0] >= 0 && P[1] > 0 && P[2] > 0, "idle_t2s: need dt >= 0, T1 > 0, T2* > 0");
+      S(mul(sup_deph1(t2s_deph_p(P[0], P[2])), sup_depol1(t1_depol_p(P[0], P[1])), 4));  // dephasing after T1
+      break;
     case VQD_OP_STDERR1:
     case VQD_OP_STDERR2: {
       double p, q;
@@ -516,6 +524,12 @@ KrausForm compile_kraus_form(const vqd_native_op& o, unsigned flags) {
       } else {
         f.K = one;
       }
+      break;
+    }
+    case VQD_OP_IDLE_T2S: {
+      const double q = t1_depol_p(P[0], P[1]), pd = t2s_deph_p(P[0], P[2]);
+      double wq[4] = {1 - q, q / 3, q / 3, q / 3}, wd[4] = {1 - pd, 0, 0, pd};
+      f.K = kraus_then(kraus_pauli1(wq), kraus_pauli1(wd), 2);
       break;
     }
     case VQD_OP_STDERR1:

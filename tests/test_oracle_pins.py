@@ -403,6 +403,19 @@ def test_nv_conditional_rotations_are_zx_and_zy():
         assert np.abs(oc.zx(theta) - expm(-0.5j * theta * np.kron(X, Z))).max() < 1e-14
 
 
+@pytest.mark.parametrize("dt,t1,t2s", [(3.0, 50.0, 10.0), (0.5, 1e9, 1.0), (20.0, 40.0, 1e6)])
+def test_idle_t2s_closed_forms(dt, t1, t2s):
+    """Eqs. (depolt1), (depht2s): after an idle of dt from |+>, <X> = e^{-dt/T1} e^{-(dt/T2*)^2} (depolarising
+    shrinks the Bloch vector by 1 - 4p/3 = e^{-dt/T1}, Gaussian dephasing by 1 - 2p = e^{-(dt/T2*)^2}); from |1>,
+    the population relaxes towards 1/2 as P(1) = 1/2 + e^{-dt/T1}/2."""
+    from workloads.circuits import NativeOp, Program
+    rho = evolve.run_program(Program(1, [NativeOp("h", (0,)), NativeOp("idle_t2s", (0,), (dt, t1, t2s))]))
+    want = math.exp(-dt / t1) * math.exp(-((dt / t2s) ** 2))
+    assert abs(measure.expect(rho, [[1]], [1.0]) - want) < 1e-14
+    rho = evolve.run_program(Program(1, [NativeOp("rx", (0,), (math.pi,)), NativeOp("idle_t2s", (0,), (dt, t1, t2s))]))
+    assert abs(measure.probs(rho, [0])[1] - (0.5 + 0.5 * math.exp(-dt / t1))) < 1e-14
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4
