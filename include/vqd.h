@@ -353,6 +353,33 @@ typedef struct {
 int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
                    vqd_native_op* out, int* nout);
 
+/* Trapped-ion device of Sec. 4 with the parameters of its App. C table (every ion identical).  Zones,
+ * shuttling, splitting and remote entanglement are not modelled: any two ions may take a CZ.  MHz, us. */
+typedef struct {
+  int32_t n;               /* ions (1..32) */
+  double t1;               /* T1 > 0 (passive decay as depolarising, Eq. depolt1) */
+  double t2s;              /* T2* > 0 (Gaussian dephasing, Eq. depht2s) */
+  double rabi;             /* Rabi frequency of the x/y rotations, > 0 */
+  double fid_xy, x_xy;     /* x/y rotation fidelity in (0,1] and depolarising fraction in [0,1] */
+  double freq_cz;          /* CZ gate frequency, > 0 */
+  double fid_cz, x_cz;     /* CZ fidelity in (0,1] and depolarising fraction in [0,1] */
+  double bf_read;          /* readout bit-flip probability in [0,1/2] */
+  double dur_read;         /* duration of one ion's readout, >= 0 */
+  uint32_t flags;          /* VQD_ION_NO_PASSIVE */
+} vqd_ion_device;
+#define VQD_ION_NO_PASSIVE 1u  /* no passive T1/T2* decay */
+
+/* Compile a logical circuit of Rx, Ry, Rz and CZ ops (others: VQD_EINVAL) for the ions.  Gates run one at
+ * a time, in program order.  Rx/Ry(theta) lasts t = |theta| / (2 pi rabi) and is followed by depol1(q s)
+ * then deph1(p s), s = |theta| / pi, (p, q) = App. B's severities for fid_xy, x_xy (zero ones left out);
+ * Rz is virtual: instantaneous and exact; CZ lasts 1 / (2 freq_cz) and is followed by depol2(q) then
+ * deph2(p) for fid_cz, x_cz.  During a gate of length t > 0, every other ion gets idle_t2s(t, t1, t2s).
+ * With readout != 0 the ions are read one at a time, 0 first: bitflip(bf_read) on ion j, then
+ * idle_t2s(dur_read, t1, t2s) on the ions not yet read.  out == NULL only counts; otherwise out has room
+ * for cap ops (VQD_EINVAL if too few). */
+int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                    vqd_native_op* out, int* nout);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);

@@ -245,3 +245,46 @@ def nv_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Lis
                 NativeOp("rx", (0,), (math.pi,))]
         outside((0,), float(dev["dur_meas"]))
     return out
+
+
+# ------------------------------------------------------------------ trapped ions (Sec. 4, App. C)
+def ion_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> List[NativeOp]:
+    """Logical circuit -> native op list of the trapped-ion device (Sec. 4, App. C), without zones or shuttling.
+
+    Serial gates:
+    - Rx/Ry last |theta| / (2 pi f_Rabi) and carry the standard error of their fidelity, scaled by |theta|/pi.
+    - Rz is virtual: instantaneous and exact.
+    - CZ lasts 1 / (2 f_CZ) (a phase pi at the gate frequency) and carries its standard error.
+    - The other ions decay passively over each gate: T1 as depolarising, then Gaussian T2* dephasing.
+    - Readout flips each ion's bit with the tabulated probability, one ion at a time; the ions not yet
+      read decay during each readout.
+    """
+    n = int(dev["n"])
+    passive = not (int(dev.get("flags", 0)) & 1)
+    out: List[NativeOp] = []
+
+    def idle_others(active, t, first=0):
+        if passive and t > 0:
+            for j in range(first, n):
+                if j not in active:
+                    out.append(NativeOp("idle_t2s", (j,), (t, float(dev["t1"]), float(dev["t2s"]))))
+
+    for op in ops:
+        if op.name == "rz":
+            out.append(op)
+        elif op.name in ("rx", "ry"):
+            out.append(op)
+            out += scaled_standard_error(1, op.qubits, float(dev["fid_xy"]), float(dev["x_xy"]), op.params[0])
+            idle_others(op.qubits, abs(op.params[0]) / (2 * math.pi * float(dev["rabi"])))
+        elif op.name == "cz":
+            out.append(op)
+            out += scaled_standard_error(2, op.qubits, float(dev["fid_cz"]), float(dev["x_cz"]), math.pi)
+            idle_others(op.qubits, 1.0 / (2 * float(dev["freq_cz"])))
+        else:
+            raise ValueError(f"{op.name} is not a trapped-ion native gate")
+    if readout:
+        for j in range(n):
+            if dev["bf_read"] > 0:
+                out.append(NativeOp("bitflip", (j,), (float(dev["bf_read"]),)))
+            idle_others((), float(dev["dur_read"]), j + 1)
+    return out

@@ -930,6 +930,85 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
   API_END(nullptr)
 }
 
+// Trapped-ion device compiler, Sec. 4 and the trapped-ion table of App. C (zones and shuttling left
+// out): serial gates, each x/y rotation or CZ followed by its standard error (App. B, App. C's angle
+// rule), passive T1 as depolarising and Gaussian T2* dephasing on the other ions, and readout as a
+// symmetric bit flip per ion, one ion at a time.
+int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
+                    vqd_native_op* out, int* nout) {
+  API_BEGIN
+  if (!dev || !nout || nin < 0 || (nin > 0 && !in) || (out && cap < 0)) throw Error(VQD_EINVAL, "bad argument");
+  const int n = dev->n;
+  if (n < 1 || n > 32) throw Error(VQD_EINVAL, "bad device: ion count");
+  if (!(dev->t1 > 0) || !(dev->t2s > 0) || !(dev->rabi > 0) || !(dev->freq_cz > 0))
+    throw Error(VQD_EINVAL, "bad device: T1, T2*, Rabi or CZ frequency");
+  if (!(dev->fid_xy > 0 && dev->fid_xy <= 1) || !(dev->fid_cz > 0 && dev->fid_cz <= 1) ||
+      !(dev->x_xy >= 0 && dev->x_xy <= 1) || !(dev->x_cz >= 0 && dev->x_cz <= 1))
+    throw Error(VQD_EINVAL, "bad device: fidelity or depolarising fraction");
+  if (readout && !(dev->bf_read >= 0 && dev->bf_read <= 0.5 && dev->dur_read >= 0))
+    throw Error(VQD_EINVAL, "bad device: readout bit flip or duration");
+  const bool passive = !(dev->flags & VQD_ION_NO_PASSIVE);
+  const double pi = 3.14159265358979323846;
+  int cnt = 0;
+  auto put = [&](const vqd_native_op& o) {
+    if (out) {
+      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+      out[cnt] = o;
+    }
+    cnt++;
+  };
+  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
+    vqd_native_op o;
+    std::memset(&o, 0, sizeof(o));
+    o.code = code;
+    o.nq = q1 < 0 ? 1 : 2;
+    o.q[0] = q0;
+    o.q[1] = q1 < 0 ? 0 : q1;
+    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
+    put(o);
+  };
+  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
+    double pd, qd;
+    stderr_params(nq, fbar, x, &pd, &qd);
+    const double sc = std::fabs(theta) / pi;
+    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
+    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
+  };
+  auto idle_others = [&](int a, int b, double t, int from) {  // ions from.. outside the gate, for t
+    if (!passive || t <= 0) return;
+    for (int j = from; j < n; j++)
+      if (j != a && j != b) emit(VQD_OP_IDLE_T2S, j, -1, t, dev->t1, dev->t2s);
+  };
+  for (int i = 0; i < nin; i++) {
+    const vqd_native_op& o = in[i];
+    const int ar = native_arity(o.code);
+    if (ar < 1 || o.nq != ar) throw Error(VQD_EINVAL, "bad op at index " + std::to_string(i));
+    for (int j = 0; j < ar; j++)
+      if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
+        throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
+    if (o.code == VQD_OP_RZ) {  // virtual: instantaneous and exact
+      put(o);
+    } else if (o.code == VQD_OP_RX || o.code == VQD_OP_RY) {
+      put(o);
+      scaled_stderr(1, o.q[0], -1, dev->fid_xy, dev->x_xy, o.par[0]);
+      idle_others(o.q[0], -1, std::fabs(o.par[0]) / (2 * pi * dev->rabi), 0);
+    } else if (o.code == VQD_OP_CZ) {
+      put(o);
+      scaled_stderr(2, o.q[0], o.q[1], dev->fid_cz, dev->x_cz, pi);
+      idle_others(o.q[0], o.q[1], 1.0 / (2 * dev->freq_cz), 0);
+    } else {
+      throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a trapped-ion native gate");
+    }
+  }
+  if (readout)
+    for (int j = 0; j < n; j++) {
+      if (dev->bf_read > 0) emit(VQD_OP_BITFLIP, j, -1, dev->bf_read, 0, 0);
+      idle_others(-1, -1, dev->dur_read, j + 1);
+    }
+  *nout = cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");

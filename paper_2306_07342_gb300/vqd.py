@@ -78,6 +78,17 @@ class nv_device(ctypes.Structure):
 VQD_NV_NO_PASSIVE = 1
 
 
+class ion_device(ctypes.Structure):
+    """vqd_ion_device: trapped-ion device table (every ion identical)."""
+    _fields_ = [("n", ctypes.c_int32), ("t1", ctypes.c_double), ("t2s", ctypes.c_double), ("rabi", ctypes.c_double),
+                ("fid_xy", ctypes.c_double), ("x_xy", ctypes.c_double), ("freq_cz", ctypes.c_double),
+                ("fid_cz", ctypes.c_double), ("x_cz", ctypes.c_double), ("bf_read", ctypes.c_double),
+                ("dur_read", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+VQD_ION_NO_PASSIVE = 1
+
+
 class VQDError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libvqd error {code}: {msg}")
@@ -135,6 +146,7 @@ def lib() -> ctypes.CDLL:
             "vqd_sc_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_si_compile": (I, [P, I, P, I, P, P]),
             "vqd_nv_compile": (I, [P, I, P, I, I, P, P]),
+            "vqd_ion_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -369,6 +381,20 @@ def vqd_nv_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
     out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
     _check(lib().vqd_nv_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
                                 ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def vqd_ion_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
+    """Compile a logical Rx/Ry/Rz/CZ circuit for a trapped-ion device (host only).  ``dev`` holds n, t1, t2s,
+    rabi, fid_xy, x_xy, freq_cz, fid_cz, x_cz, bf_read, dur_read and optional flags."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    d = ion_device(int(dev["n"]), *[float(dev[k]) for k in ("t1", "t2s", "rabi", "fid_xy", "x_xy", "freq_cz", "fid_cz",
+                                                            "x_cz", "bf_read", "dur_read")], int(dev.get("flags", 0)))
+    cnt = ctypes.c_int()
+    _check(lib().vqd_ion_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), 0, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
+    _check(lib().vqd_ion_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
+                                 ctypes.byref(cnt)))
     return out[: cnt.value].copy()
 
 

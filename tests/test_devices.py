@@ -355,3 +355,85 @@ def test_nv_compiled_program_gpu_parity(vqd, p):
             assert np.abs(got - want).max() < t, runner
         finally:
             vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- trapped ions (Sec. 4, App. C)
+from oracle.devices import ion_compile  # noqa: E402
+from workloads.devices import ION, ion_circuit  # noqa: E402
+
+
+def small_ion(**kw):
+    dev = {"n": 3, "t1": 1000.0, "t2s": 20.0, "rabi": 0.25, "fid_xy": 0.999, "x_xy": 1.0, "freq_cz": 0.05,
+           "fid_cz": 0.99, "x_cz": 0.1, "bf_read": 0.01, "dur_read": 5.0}
+    dev.update(kw)
+    return dev
+
+
+def test_ion_worked_example_by_hand(vqd):
+    """Ry(pi/2) on ion 1 (0.25 MHz: t = 1 us), virtual Rz on ion 0, CZ on (2, 0) (0.05 MHz: t = 10 us); readout
+    one ion at a time (5 us each)."""
+    dev = small_ion()
+    ops = [NativeOp("ry", (1,), (math.pi / 2,)), NativeOp("rz", (0,), (0.4,)), NativeOp("cz", (2, 0))]
+    p1, q1 = oc_stderr(0.999, 1.0, 1)                     # pure depolarising: p1 = 0
+    p2, q2 = oc_stderr(0.99, 0.1, 2)
+    idle = lambda j, t: NativeOp("idle_t2s", (j,), (t, 1000.0, 20.0))
+    want = [ops[0], NativeOp("depol1", (1,), (q1 / 2,)), idle(0, 1.0), idle(2, 1.0),
+            ops[1],
+            ops[2], NativeOp("depol2", (2, 0), (q2,)), NativeOp("deph2", (2, 0), (p2,)), idle(1, 10.0),
+            NativeOp("bitflip", (0,), (0.01,)), idle(1, 5.0), idle(2, 5.0),
+            NativeOp("bitflip", (1,), (0.01,)), idle(2, 5.0),
+            NativeOp("bitflip", (2,), (0.01,))]
+    assert p1 == 0.0
+    same_ops(ion_compile(dev, ops, readout=True), want, 1e-15)
+    same_ops(as_ops(vqd, vqd.vqd_ion_compile(dev, ops, readout=True)), want, 1e-12)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ion_library_matches_oracle(vqd, seed):
+    for dev in (ION, dict(ION, flags=1), small_ion(bf_read=0.0)):
+        ops = ion_circuit(dev, 80, seed=seed)
+        for readout in (False, True):
+            same_ops(as_ops(vqd, vqd.vqd_ion_compile(dev, ops, readout)), ion_compile(dev, ops, readout), 1e-12)
+
+
+def test_ion_gaussian_t2s_accumulates_per_gate():
+    """Ion 1 in |+> idles through m Rx(pi) gates on ion 0 (t = 2 us each, exact gates): every gate is its own
+    Gaussian free-induction interval (Eq. depht2s), so <X_1> = exp(-m t/T1 - m (t/T2*)^2)."""
+    dev = small_ion(n=2, fid_xy=1.0)
+    m, t = 12, 2.0
+    ops = [NativeOp("ry", (1,), (math.pi / 2,))] + [NativeOp("rx", (0,), (math.pi,)) for _ in range(m)]
+    rho = evolve.run_program(Program(2, ion_compile(dev, ops)))
+    # the Ry(pi/2) itself (1 us) only idles ion 0
+    assert abs(measure.expect(rho, [[0, 1]], [1.0]) - math.exp(-m * t / 1000.0 - m * (t / 20.0) ** 2)) < 1e-13
+
+
+def test_ion_readout_flip_closed_form():
+    """Readout flips each ion's outcome with probability b (symmetric bit flip, Eq. bf).  Ion 2 is flipped by an
+    Rx(pi) whose standard error is pure depolarising with q = 3(1 - F)/2 (App. B, x = 1), so its population
+    error is 2q/3 = 1 - F and it reads 1 with probability F(1 - b) + (1 - F) b; ion 0 reads 1 with probability b."""
+    F, b = 0.999, 0.03
+    dev = small_ion(flags=1, bf_read=b, fid_xy=F)
+    rho = evolve.run_program(Program(3, ion_compile(dev, [NativeOp("rx", (2,), (math.pi,))], readout=True)))
+    assert abs(measure.probs(rho, [0])[1] - b) < 1e-14
+    assert abs(measure.probs(rho, [2])[1] - (F * (1 - b) + (1 - F) * b)) < 1e-13
+
+
+def test_ion_rejects_bad_input(vqd):
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_ion_compile(small_ion(), [NativeOp("cph", (0, 1), (0.3,))])
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_ion_compile(small_ion(freq_cz=0.0), [NativeOp("rx", (0,), (0.1,))])
+
+
+@pytest.mark.gpu
+def test_ion_compiled_program_gpu_parity(vqd):
+    ops = ion_circuit(ION, 120, seed=23)
+    lib_ops = vqd.vqd_ion_compile(ION, ops, readout=True)
+    want = evolve.run_program(Program(8, ion_compile(ION, ops, readout=True)))
+    for runner in ("plain", "fused"):
+        ctx = vqd.vqd_create(8, vqd.VQD_F64)
+        try:
+            (vqd.vqd_apply_native if runner == "plain" else vqd.vqd_run_program)(ctx, 0, lib_ops)
+            assert np.abs(vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0)) - want).max() < TOL_F64, runner
+        finally:
+            vqd.vqd_destroy(ctx)

@@ -153,3 +153,34 @@ def nv_bcs_shape(dev: Dict, n_props: int = 64, gates_per_prop: int = 200, seed: 
         else:
             ops.append(NativeOp(("rx", "ry", "rz")[int(r.integers(0, 3))], (int(r.integers(0, n)),), (th,)))
     return ops
+
+
+ION = {  # App. C, table of the virtual trapped ions (us, MHz); every ion identical; ratios depolarising:dephasing
+    "n": 8,
+    "t1": 3e9,
+    "t2s": 10e5,
+    "rabi": 10.0,
+    "fid_xy": 0.99999,
+    "x_xy": 1.0,           # 1:0
+    "freq_cz": 0.1,
+    "fid_cz": 0.999,
+    "x_cz": 0.1,           # 0.1:0.9
+    "bf_read": 0.001,
+    "dur_read": 50.0,
+}
+
+
+def ion_circuit(dev: Dict, n_gates: int, seed: int = 17) -> List[NativeOp]:
+    """Random circuit in the trapped-ion native gates: Rx, Ry (angles up to pi), virtual Rz, and CZ on any
+    pair of ions, about one gate in four a CZ."""
+    r = _rng(seed)
+    n = int(dev["n"])
+    ops: List[NativeOp] = []
+    for _ in range(n_gates):
+        if n > 1 and r.uniform() < 0.25:
+            a, b = (int(x) for x in r.choice(n, size=2, replace=False))
+            ops.append(NativeOp("cz", (a, b)))
+        else:
+            name = ("rx", "ry", "rz")[int(r.integers(0, 3))]
+            ops.append(NativeOp(name, (int(r.integers(0, n)),), (float(r.uniform(-math.pi, math.pi)),)))
+    return ops
