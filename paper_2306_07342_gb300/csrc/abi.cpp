@@ -613,6 +613,41 @@ int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int
   API_END(nullptr)
 }
 
+// Output of the device compilers: counts every op and, when out is given, stores it (VQD_EINVAL once
+// cap is exceeded).
+struct OpSink {
+  vqd_native_op* out;
+  int cap;
+  int cnt = 0;
+  void put(const vqd_native_op& o) {
+    if (out) {
+      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
+      out[cnt] = o;
+    }
+    cnt++;
+  }
+  void emit(int code, int q0, int q1, double p0, double p1 = 0, double p2 = 0, double p3 = 0) {
+    vqd_native_op o;
+    std::memset(&o, 0, sizeof(o));
+    o.code = code;
+    o.nq = q1 < 0 ? 1 : 2;
+    o.q[0] = q0;
+    o.q[1] = q1 < 0 ? 0 : q1;
+    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2; o.par[3] = p3;
+    put(o);
+  }
+  // App. C: the error severities of a parameterised gate scale with its angle, eps -> eps |theta| / pi.
+  // The standard error deph(p) o depol(q) of the gate's fidelity (App. B) becomes depol(q s) then
+  // deph(p s); zero severities are left out.
+  void scaled_stderr(int nq, int a, int b, double fbar, double x, double theta) {
+    double pd, qd;
+    stderr_params(nq, fbar, x, &pd, &qd);
+    const double sc = std::fabs(theta) / 3.14159265358979323846;
+    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc);
+    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc);
+  }
+};
+
 // Superconducting device compiler, Sec. 8 and the superconducting table of App. C: gates are exact
 // and run in parallel (ASAP layers); the errors are the passive T1/T2 decay (gamp towards the thermal
 // state, then the dephasing of Eq. depht2) of qubits outside an active gate, the static ZZ of every
@@ -665,34 +700,17 @@ int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, i
   }
   std::vector<std::vector<int>> by_layer(nl);
   for (int i = 0; i < nin; i++) by_layer[layer[i]].push_back(i);
-  int cnt = 0;
-  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2, double p3) {
-    if (out) {
-      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
-      vqd_native_op& o = out[cnt];
-      std::memset(&o, 0, sizeof(o));
-      o.code = code;
-      o.nq = q1 < 0 ? 1 : 2;
-      o.q[0] = q0;
-      o.q[1] = q1 < 0 ? 0 : q1;
-      o.par[0] = p0; o.par[1] = p1; o.par[2] = p2; o.par[3] = p3;
-    }
-    cnt++;
-  };
+  OpSink sink{out, cap};
   const double two_pi = 2 * 3.14159265358979323846;
   auto decay = [&](int j, double dt) {  // free-induction decay of qubit j over dt
-    emit(VQD_OP_GAMP, j, -1, dt, dev->t1[j], 1 - dev->excited[j], 0);
-    emit(VQD_OP_DEPH1, j, -1, 0.5 * (1 - std::exp(-dt / dev->t2[j])), 0, 0, 0);
+    sink.emit(VQD_OP_GAMP, j, -1, dt, dev->t1[j], 1 - dev->excited[j], 0);
+    sink.emit(VQD_OP_DEPH1, j, -1, 0.5 * (1 - std::exp(-dt / dev->t2[j])), 0, 0, 0);
   };
   for (int l = 0; l < nl; l++) {
     double len = 0;
     std::vector<double> busy(n, 0.0);
     for (int i : by_layer[l]) {
-      if (out) {
-        if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
-        out[cnt] = in[i];
-      }
-      cnt++;
+      sink.put(in[i]);
       len = std::max(len, dur[i]);
       for (int j = 0; j < in[i].nq; j++) busy[in[i].q[j]] = dur[i];
     }
@@ -707,7 +725,7 @@ int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, i
         if (sizzle || dev->coupling[k] == 0) continue;
         // frequencies (MHz) times the layer length (us) as angles: beta is then the accumulated phase
         const double w = two_pi * len;
-        emit(VQD_OP_ZZ_STATIC, c, t, w * dev->coupling[k], w * (dev->freq[c] - dev->freq[t]), w * dev->anharm[t],
+        sink.emit(VQD_OP_ZZ_STATIC, c, t, w * dev->coupling[k], w * (dev->freq[c] - dev->freq[t]), w * dev->anharm[t],
              w * dev->anharm[c]);
       }
     }
@@ -717,10 +735,10 @@ int vqd_sc_compile(const vqd_sc_device* dev, int nin, const vqd_native_op* in, i
   }
   if (readout)
     for (int j = 0; j < n; j++) {
-      if (passive && dev->dur_meas > 0) emit(VQD_OP_GAMP, j, -1, dev->dur_meas, dev->t1[j], 1 - dev->excited[j], 0);
-      if (dev->fid_read) emit(VQD_OP_DEPOL1, j, -1, 1 - dev->fid_read[j], 0, 0, 0);
+      if (passive && dev->dur_meas > 0) sink.emit(VQD_OP_GAMP, j, -1, dev->dur_meas, dev->t1[j], 1 - dev->excited[j], 0);
+      if (dev->fid_read) sink.emit(VQD_OP_DEPOL1, j, -1, 1 - dev->fid_read[j], 0, 0, 0);
     }
-  *nout = cnt;
+  *nout = sink.cnt;
   API_END(nullptr)
 }
 
@@ -748,37 +766,11 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
     throw Error(VQD_EINVAL, "bad device: depolarising fraction outside [0,1]");
   const bool passive = !(dev->flags & VQD_SI_NO_PASSIVE), offres = !(dev->flags & VQD_SI_NO_OFFRES);
   const double two_pi = 2 * 3.14159265358979323846;
-  int cnt = 0;
-  auto put = [&](const vqd_native_op& o) {
-    if (out) {
-      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
-      out[cnt] = o;
-    }
-    cnt++;
-  };
-  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
-    vqd_native_op o;
-    std::memset(&o, 0, sizeof(o));
-    o.code = code;
-    o.nq = q1 < 0 ? 1 : 2;
-    o.q[0] = q0;
-    o.q[1] = q1 < 0 ? 0 : q1;
-    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
-    put(o);
-  };
-  // App. C: the error severities of a parameterised gate scale with its angle, eps -> eps |theta| / pi.
-  // The standard error deph(p) o depol(q) of the gate's fidelity (App. B) becomes depol(q s) then deph(p s).
-  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
-    double pd, qd;
-    stderr_params(nq, fbar, x, &pd, &qd);
-    const double sc = std::fabs(theta) / 3.14159265358979323846;
-    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
-    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
-  };
+  OpSink sink{out, cap};
   auto decay_others = [&](int a, int b, double t) {  // passive qubits over the gate's duration
     if (!passive || t <= 0) return;
     for (int j = 0; j < n; j++)
-      if (j != a && j != b) emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
+      if (j != a && j != b) sink.emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
   };
   for (int i = 0; i < nin; i++) {
     const vqd_native_op& o = in[i];
@@ -788,22 +780,22 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
       if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
         throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
     if (o.code == VQD_OP_RZ) {  // virtual
-      put(o);
+      sink.put(o);
       continue;
     }
     if (o.code == VQD_OP_RX || o.code == VQD_OP_RY) {
       const int q = o.q[0];
       const double t = std::fabs(o.par[0]) / (two_pi * dev->rabi[q]);  // rotation angle 2 pi f_Rabi t
-      put(o);
-      scaled_stderr(1, q, -1, dev->fid_1q[q], dev->x_1q, o.par[0]);
+      sink.put(o);
+      sink.scaled_stderr(1, q, -1, dev->fid_1q[q], dev->x_1q, o.par[0]);
       if (offres && t > 0)
         for (int j = 0; j < n; j++)
           if (j != q)
-            emit(VQD_OP_OFFRES, j, -1, two_pi * dev->rabi[q], two_pi * std::fabs(dev->freq[j] - dev->freq[q]), t);
+            sink.emit(VQD_OP_OFFRES, j, -1, two_pi * dev->rabi[q], two_pi * std::fabs(dev->freq[j] - dev->freq[q]), t);
       decay_others(q, -1, t);
       if (dev->xtalk_off)
         for (int k = 0; k + 1 < n; k++)
-          if (k != q && k + 1 != q && dev->xtalk_off[k] != 0) emit(VQD_OP_CRZ_XTALK, k, k + 1, dev->xtalk_off[k], 0, 0);
+          if (k != q && k + 1 != q && dev->xtalk_off[k] != 0) sink.emit(VQD_OP_CRZ_XTALK, k, k + 1, dev->xtalk_off[k], 0, 0);
       continue;
     }
     if (o.code == VQD_OP_CZ || o.code == VQD_OP_CPH) {
@@ -812,19 +804,19 @@ int vqd_si_compile(const vqd_si_device* dev, int nin, const vqd_native_op* in, i
       const int k = std::min(a, b);
       const double theta = o.code == VQD_OP_CZ ? 3.14159265358979323846 : o.par[0];
       const double t = std::fabs(theta) / (two_pi * dev->freq_cz[k]);  // conditional phase 2 pi f_CZ t
-      put(o);
-      scaled_stderr(2, a, b, dev->fid_cz[k], dev->x_cz, theta);
+      sink.put(o);
+      sink.scaled_stderr(2, a, b, dev->fid_cz[k], dev->x_cz, theta);
       if (dev->xtalk_on)
         for (int j = 0; j + 1 < n; j++) {
           const double d = dev->xtalk_on[k * (n - 1) + j];
-          if (j != k && d != 0) emit(VQD_OP_CRZ_XTALK, j, j + 1, d * theta / 3.14159265358979323846, 0, 0);
+          if (j != k && d != 0) sink.emit(VQD_OP_CRZ_XTALK, j, j + 1, d * theta / 3.14159265358979323846, 0, 0);
         }
       decay_others(a, b, t);
       continue;
     }
     throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a silicon native gate");
   }
-  *nout = cnt;
+  *nout = sink.cnt;
   API_END(nullptr)
 }
 
@@ -854,41 +846,15 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
     throw Error(VQD_EINVAL, "bad device: readout fidelity or duration");
   const bool passive = !(dev->flags & VQD_NV_NO_PASSIVE);
   const double two_pi = 2 * 3.14159265358979323846;
-  int cnt = 0;
-  auto put = [&](const vqd_native_op& o) {
-    if (out) {
-      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
-      out[cnt] = o;
-    }
-    cnt++;
-  };
-  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
-    vqd_native_op o;
-    std::memset(&o, 0, sizeof(o));
-    o.code = code;
-    o.nq = q1 < 0 ? 1 : 2;
-    o.q[0] = q0;
-    o.q[1] = q1 < 0 ? 0 : q1;
-    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
-    put(o);
-  };
-  // App. C: the error severities of a parameterised gate scale with its angle, eps -> eps |theta| / pi.
-  // The standard error deph(p) o depol(q) of the gate's fidelity (App. B) becomes depol(q s) then deph(p s).
-  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
-    double pd, qd;
-    stderr_params(nq, fbar, x, &pd, &qd);
-    const double sc = std::fabs(theta) / 3.14159265358979323846;
-    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
-    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
-  };
+  OpSink sink{out, cap};
   auto passive_noise = [&](int a, int b, double t) {  // qubits outside the gate, for its duration
     if (!passive || t <= 0) return;
     if (dev->freq_zz != 0)
       for (int i = 1; i < n; i++)
         for (int k = i + 1; k < n; k++)
-          if (i != a && i != b && k != a && k != b) emit(VQD_OP_ZZ_IDLE, i, k, t, dev->freq_zz, 0);
+          if (i != a && i != b && k != a && k != b) sink.emit(VQD_OP_ZZ_IDLE, i, k, t, dev->freq_zz, 0);
     for (int j = 0; j < n; j++)
-      if (j != a && j != b) emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
+      if (j != a && j != b) sink.emit(VQD_OP_IDLE_DEPOL, j, -1, t, dev->t1[j], dev->t2[j]);
   };
   for (int i = 0; i < nin; i++) {
     const vqd_native_op& o = in[i];
@@ -901,9 +867,9 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
       const int q = o.q[0];
       const bool z = o.code == VQD_OP_RZ;
       const double t = std::fabs(o.par[0]) / (two_pi * (z ? dev->freq_z[q] : dev->freq_xy[q]));
-      put(o);
-      if (!z) scaled_stderr(1, q, -1, dev->fid_xy[q], dev->x_xy, o.par[0]);
-      else if (dev->fid_z[q] < 1) scaled_stderr(1, q, -1, dev->fid_z[q], 0.0, o.par[0]);
+      sink.put(o);
+      if (!z) sink.scaled_stderr(1, q, -1, dev->fid_xy[q], dev->x_xy, o.par[0]);
+      else if (dev->fid_z[q] < 1) sink.scaled_stderr(1, q, -1, dev->fid_z[q], 0.0, o.par[0]);
       passive_noise(q, -1, t);
       continue;
     }
@@ -912,8 +878,8 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
                                                    std::to_string(i));
       const int j = o.q[1];
       const double t = std::fabs(o.par[0]) / (two_pi * dev->freq_crot[j - 1]);
-      put(o);
-      scaled_stderr(2, 0, j, dev->fid_crot[j - 1], dev->x_crot, o.par[0]);
+      sink.put(o);
+      sink.scaled_stderr(2, 0, j, dev->fid_crot[j - 1], dev->x_crot, o.par[0]);
       passive_noise(0, j, t);
       continue;
     }
@@ -921,12 +887,12 @@ int vqd_nv_compile(const vqd_nv_device* dev, int nin, const vqd_native_op* in, i
   }
   if (readout) {
     const double pi = 3.14159265358979323846;
-    emit(VQD_OP_RX, 0, -1, pi, 0, 0);
-    emit(VQD_OP_AMP, 0, -1, 1 - dev->fid_meas, 0, 0);
-    emit(VQD_OP_RX, 0, -1, pi, 0, 0);
+    sink.emit(VQD_OP_RX, 0, -1, pi, 0, 0);
+    sink.emit(VQD_OP_AMP, 0, -1, 1 - dev->fid_meas, 0, 0);
+    sink.emit(VQD_OP_RX, 0, -1, pi, 0, 0);
     passive_noise(0, -1, dev->dur_meas);
   }
-  *nout = cnt;
+  *nout = sink.cnt;
   API_END(nullptr)
 }
 
@@ -949,35 +915,11 @@ int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in,
     throw Error(VQD_EINVAL, "bad device: readout bit flip or duration");
   const bool passive = !(dev->flags & VQD_ION_NO_PASSIVE);
   const double pi = 3.14159265358979323846;
-  int cnt = 0;
-  auto put = [&](const vqd_native_op& o) {
-    if (out) {
-      if (cnt >= cap) throw Error(VQD_EINVAL, "output capacity too small");
-      out[cnt] = o;
-    }
-    cnt++;
-  };
-  auto emit = [&](int code, int q0, int q1, double p0, double p1, double p2) {
-    vqd_native_op o;
-    std::memset(&o, 0, sizeof(o));
-    o.code = code;
-    o.nq = q1 < 0 ? 1 : 2;
-    o.q[0] = q0;
-    o.q[1] = q1 < 0 ? 0 : q1;
-    o.par[0] = p0; o.par[1] = p1; o.par[2] = p2;
-    put(o);
-  };
-  auto scaled_stderr = [&](int nq, int a, int b, double fbar, double x, double theta) {
-    double pd, qd;
-    stderr_params(nq, fbar, x, &pd, &qd);
-    const double sc = std::fabs(theta) / pi;
-    if (qd * sc > 0) emit(nq == 1 ? VQD_OP_DEPOL1 : VQD_OP_DEPOL2, a, nq == 1 ? -1 : b, qd * sc, 0, 0);
-    if (pd * sc > 0) emit(nq == 1 ? VQD_OP_DEPH1 : VQD_OP_DEPH2, a, nq == 1 ? -1 : b, pd * sc, 0, 0);
-  };
+  OpSink sink{out, cap};
   auto idle_others = [&](int a, int b, double t, int from) {  // ions from.. outside the gate, for t
     if (!passive || t <= 0) return;
     for (int j = from; j < n; j++)
-      if (j != a && j != b) emit(VQD_OP_IDLE_T2S, j, -1, t, dev->t1, dev->t2s);
+      if (j != a && j != b) sink.emit(VQD_OP_IDLE_T2S, j, -1, t, dev->t1, dev->t2s);
   };
   for (int i = 0; i < nin; i++) {
     const vqd_native_op& o = in[i];
@@ -987,14 +929,14 @@ int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in,
       if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
         throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
     if (o.code == VQD_OP_RZ) {  // virtual: instantaneous and exact
-      put(o);
+      sink.put(o);
     } else if (o.code == VQD_OP_RX || o.code == VQD_OP_RY) {
-      put(o);
-      scaled_stderr(1, o.q[0], -1, dev->fid_xy, dev->x_xy, o.par[0]);
+      sink.put(o);
+      sink.scaled_stderr(1, o.q[0], -1, dev->fid_xy, dev->x_xy, o.par[0]);
       idle_others(o.q[0], -1, std::fabs(o.par[0]) / (2 * pi * dev->rabi), 0);
     } else if (o.code == VQD_OP_CZ) {
-      put(o);
-      scaled_stderr(2, o.q[0], o.q[1], dev->fid_cz, dev->x_cz, pi);
+      sink.put(o);
+      sink.scaled_stderr(2, o.q[0], o.q[1], dev->fid_cz, dev->x_cz, pi);
       idle_others(o.q[0], o.q[1], 1.0 / (2 * dev->freq_cz), 0);
     } else {
       throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a trapped-ion native gate");
@@ -1002,10 +944,10 @@ int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in,
   }
   if (readout)
     for (int j = 0; j < n; j++) {
-      if (dev->bf_read > 0) emit(VQD_OP_BITFLIP, j, -1, dev->bf_read, 0, 0);
+      if (dev->bf_read > 0) sink.emit(VQD_OP_BITFLIP, j, -1, dev->bf_read, 0, 0);
       idle_others(-1, -1, dev->dur_read, j + 1);
     }
-  *nout = cnt;
+  *nout = sink.cnt;
   API_END(nullptr)
 }
 
