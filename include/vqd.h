@@ -120,7 +120,10 @@ typedef enum {
                            Eq. (conditional_rots); CRx+- is VQD_OP_ZX                                   */
   VQD_OP_IDLE_T2S = 35, /* q0; dt, T1, T2*: depol(3/4(1-e^{-dt/T1})) then deph(1/2(1-e^{-(dt/T2*)^2})), Eqs. (depolt1),
                            (depht2s): passive decay with a Gaussian T2* (VQD_T2_IS_TOTAL does not apply)      */
-  VQD_OP_COUNT = 36
+  VQD_OP_BITFLIP_ASYM = 36,/* q0; p10, p01 in [0,1]: |1> -> |0> with p10, |0> -> |1> with p01 (the asymmetric
+                           bit flip of Sec. 6): Kraus diag(sqrt(1-p01), sqrt(1-p10)), sqrt(p10)|0><1|,
+                           sqrt(p01)|1><0|                                                             */
+  VQD_OP_COUNT = 37
 } vqd_op_code;
 
 typedef struct {

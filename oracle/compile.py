@@ -256,6 +256,14 @@ def t2_deph_param(dt, t2):
     return 0.5 * (1 - math.exp(-dt / t2))
 
 
+def bitflip_asym(p10, p01):
+    """Asymmetric bit flip of Sec. 6: |1> decays to |0> with probability p10, |0> is excited to |1> with
+    probability p01; Kraus operators diag(sqrt(1-p01), sqrt(1-p10)), sqrt(p10)|0><1|, sqrt(p01)|1><0|."""
+    return [np.array([[math.sqrt(1 - p01), 0], [0, math.sqrt(1 - p10)]], dtype=complex),
+            np.array([[0, math.sqrt(p10)], [0, 0]], dtype=complex),
+            np.array([[0, 0], [math.sqrt(p01), 0]], dtype=complex)]
+
+
 def t2s_deph_param(dt, t2s):
     """Eq. (depht2s): deph(1/2 (1 - exp(-(dt/T2*)^2))), the Gaussian free-induction decay."""
     return 0.5 * (1 - math.exp(-((dt / t2s) ** 2)))
@@ -327,7 +335,8 @@ def compile_op(name: str, qubits: Sequence[int], params: Sequence[float], t2_is_
     if name in unitary:
         return [("U", q, unitary[name]())]
     simple = {"depol1": depol1, "depol2": depol2, "deph1": deph1, "deph2": deph2, "amp": amp,
-              "bitflip": bitflip, "bitflip2": bitflip2, "leak_init": leak_init, "leak_cz": leak_cz}
+              "bitflip": bitflip, "bitflip2": bitflip2, "leak_init": leak_init, "leak_cz": leak_cz,
+              "bitflip_asym": bitflip_asym}
     if name in simple:
         return [("K", q, simple[name](*P))]
     if name == "gamp":

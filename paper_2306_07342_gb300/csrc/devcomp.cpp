@@ -191,7 +191,7 @@ void require(bool ok, const char* msg) {
 
 int native_arity(int code) {
   static const int ar[VQD_OP_COUNT] = {1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2,
-                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2, 2, 1};
+                                       1, 2, 1, 2, 1, 1, 2, 1, 1, 1, 1, 2, 2, 1, 2, 1, 2, 2, 1, 1};
   if (code < 0 || code >= VQD_OP_COUNT) return -1;
   return ar[code];
 }
@@ -288,6 +288,11 @@ Op compile_native(const vqd_native_op& o, unsigned flags) {
       if (o.code == VQD_OP_AMPDEPH2) S(sup_tensor(one, one)); else S(one);
       break;
     }
+    case VQD_OP_BITFLIP_ASYM:
+      require(P[0] >= 0 && P[0] <= 1 && P[1] >= 0 && P[1] <= 1, "bitflip_asym: p10, p01 outside [0,1]");
+      S(sup_kraus(1, {{std::sqrt(1 - P[1]), 0.0, 0.0, std::sqrt(1 - P[0])}, {0.0, std::sqrt(P[0]), 0.0, 0.0},
+                      {0.0, 0.0, std::sqrt(P[1]), 0.0}}));
+      break;
     case VQD_OP_IDLE_T2S:
       require(P[0] >= 0 && P[1] > 0 && P[2] > 0, "idle_t2s: need dt >= 0, T1 > 0, T2* > 0");
       S(mul(sup_deph1(t2s_deph_p(P[0], P[2])), sup_depol1(t1_depol_p(P[0], P[1])), 4));  // dephasing after T1
@@ -526,6 +531,10 @@ KrausForm compile_kraus_form(const vqd_native_op& o, unsigned flags) {
       }
       break;
     }
+    case VQD_OP_BITFLIP_ASYM:
+      f.K = {{std::sqrt(1 - P[1]), 0.0, 0.0, std::sqrt(1 - P[0])}, {0.0, std::sqrt(P[0]), 0.0, 0.0},
+             {0.0, 0.0, std::sqrt(P[1]), 0.0}};
+      break;
     case VQD_OP_IDLE_T2S: {
       const double q = t1_depol_p(P[0], P[1]), pd = t2s_deph_p(P[0], P[2]);
       double wq[4] = {1 - q, q / 3, q / 3, q / 3}, wd[4] = {1 - pd, 0, 0, pd};

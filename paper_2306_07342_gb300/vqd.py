@@ -24,7 +24,7 @@ VQD_MAX_FUSE = 6
 OP_CODES = ["rx", "ry", "rz", "sx", "h", "u", "r", "cz", "cph", "czphi", "zx", "zz", "xx", "zzphase", "zz_idle",
             "crz_xtalk", "exchange", "depol1", "depol2", "deph1", "deph2", "amp", "bitflip", "bitflip2", "gamp",
             "idle", "idle_depol", "stderr1", "stderr2", "ampdeph2", "leak_init", "leak_cz",
-            "offres", "zz_static", "zy", "idle_t2s"]
+            "offres", "zz_static", "zy", "idle_t2s", "bitflip_asym"]
 OP_CODE = {name: i for i, name in enumerate(OP_CODES)}
 
 NATIVE_OP_DTYPE = np.dtype([("code", "<i4"), ("nq", "<i4"), ("q", "<i4", (2,)), ("par", "<f8", (4,))])

@@ -416,6 +416,20 @@ def test_idle_t2s_closed_forms(dt, t1, t2s):
     assert abs(measure.probs(rho, [0])[1] - (0.5 + 0.5 * math.exp(-dt / t1))) < 1e-14
 
 
+@pytest.mark.parametrize("p10,p01", [(0.1, 0.0001), (0.001, 0.03), (0.0, 0.0), (1.0, 0.25)])
+def test_bitflip_asym_closed_forms(p10, p01):
+    """Sec. 6's asymmetric bit flip: from |1>, P(0) = p10; from |0>, P(1) = p01; the coherence of |+> is scaled by
+    sqrt((1 - p01)(1 - p10)) (only the no-flip operator keeps it); the map preserves the trace."""
+    from workloads.circuits import NativeOp, Program
+    rho = evolve.run_program(Program(1, [NativeOp("rx", (0,), (math.pi,)), NativeOp("bitflip_asym", (0,), (p10, p01))]))
+    assert abs(measure.probs(rho, [0])[0] - p10) < 1e-14
+    rho = evolve.run_program(Program(1, [NativeOp("bitflip_asym", (0,), (p10, p01))]))
+    assert abs(measure.probs(rho, [0])[1] - p01) < 1e-14
+    rho = evolve.run_program(Program(1, [NativeOp("h", (0,)), NativeOp("bitflip_asym", (0,), (p10, p01))]))
+    assert abs(2 * rho[0, 1].real - math.sqrt((1 - p01) * (1 - p10))) < 1e-14
+    assert abs(measure.trace(rho) - 1) < 1e-14
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4

@@ -59,6 +59,7 @@ OP_NAMES = {
     "zz_static": (2, ("j", "delta", "alpha_t", "alpha_c")),  # SC static ZZ exp(-i beta Z Z), beta from J, Delta, alpha
     "zy": (2, ("theta",)),            # NV conditional CRy+-(theta) = exp(-i theta/2 Z_c Y_t), Eq. (conditional_rots)
     "idle_t2s": (1, ("dt", "t1", "t2s")),   # passive T1 as depolarising + Gaussian T2* dephasing, Eqs. (depolt1),(depht2s)
+    "bitflip_asym": (1, ("p10", "p01")),     # asymmetric bit flip: |1> -> |0> with p10, |0> -> |1> with p01 (Sec. 6)
 }
 
 
@@ -356,5 +357,6 @@ def _random_params(r: np.random.Generator, name: str) -> Tuple[float, ...]:
         "zz_static": lambda: (u(0.02, 0.2), u(0.2, 1.0), u(-3.0, -2.0), u(-3.0, -2.0)),
         "zy": lambda: (u(0, 2 * math.pi),),
         "idle_t2s": lambda: (u(0.01, 20), u(20, 200), u(10, 100)),
+        "bitflip_asym": lambda: (u(0, 0.2), u(0, 0.2)),
     }
     return table[name]()
