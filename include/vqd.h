@@ -383,6 +383,37 @@ typedef struct {
 int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in, int readout, int cap,
                     vqd_native_op* out, int* nout);
 
+/* Neutral-atom device of Sec. 6 with the parameters of its App. C table (identical atoms at fixed sites;
+ * moves, atom loss and multi-qubit gates are not modelled).  Host arrays owned by the caller.  MHz, us. */
+typedef struct {
+  int32_t n;               /* atoms (1..32) */
+  const double* x;         /* [n] site coordinates (lattice units) */
+  const double* y;         /* [n] */
+  double blockade;         /* CZ(phi) needs the two atoms within this distance */
+  double t2;               /* T2 > 0 */
+  double t_vac;            /* vacuum lifetime > 0; T1 = t_vac / n (collisional loss, Sec. 6) */
+  double p10, p01;         /* asymmetric bit flip of a single rotation by pi: |1> -> |0> and |0> -> |1> */
+  double leak_init;        /* initialisation leakage gamma in [0,1] (operator L of Sec. 6) */
+  double leak_cz_a, leak_cz_b;  /* CZ leakage alpha, beta in [0,1] (Eq. czleak) */
+  double dur_cz;           /* duration of a Rydberg CZ(phi), >= 0 (not tabulated: the caller's choice) */
+  double fid_meas;         /* readout fidelity in [1/2,1] */
+  uint32_t flags;          /* VQD_NA_NO_PASSIVE */
+} vqd_na_device;
+#define VQD_NA_NO_PASSIVE 1u  /* no passive T1/T2 decay */
+
+/* Compile a logical circuit of Raman rotations U(phi, Omega, Delta, t) (VQD_OP_U) and Rydberg CZ(phi)
+ * (VQD_OP_CZPHI) on atom pairs within the blockade radius (others: VQD_EINVAL) for the atoms.  Gates run
+ * one at a time, in program order.  With init != 0 the program starts with leak_init(gamma) on every atom.
+ * U on q (its duration is its own t) is followed by deph1(1 - e^{-t/(2 T2)}) (Sec. 6, with the sign of the
+ * exponent read as decay) and bitflip_asym(p10 s, p01 s), s = Omega_R |t| / pi with
+ * Omega_R = sqrt(Omega^2 + Delta^2) (App. C's angle rule); CZ(phi) on (a, b) lasts dur_cz and is followed
+ * by leak_cz(alpha, beta).  During a gate of length t > 0 every other atom gets idle_depol(t, t_vac / n,
+ * T2).  With readout != 0 every atom gets depol1(3 (1 - fid_meas) / 2), whose misclassification
+ * probability is 1 - fid_meas.  out == NULL only counts; otherwise out has room for cap ops (VQD_EINVAL
+ * if too few). */
+int vqd_na_compile(const vqd_na_device* dev, int nin, const vqd_native_op* in, int init, int readout, int cap,
+                   vqd_native_op* out, int* nout);
+
 /* App. B: severities (p_deph, q_depol) of the standard error deph(p) o depol(q) whose average
  * gate fidelity is fbar, with depolarising fraction x in [0,1]; nq = 1 or 2. */
 int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);

@@ -288,3 +288,55 @@ def ion_compile(dev: Dict, ops: Sequence[NativeOp], readout: bool = False) -> Li
                 out.append(NativeOp("bitflip", (j,), (float(dev["bf_read"]),)))
             idle_others((), float(dev["dur_read"]), j + 1)
     return out
+
+
+# ------------------------------------------------------------------ neutral atoms (Sec. 6, App. C)
+def na_compile(dev: Dict, ops: Sequence[NativeOp], init: bool = False, readout: bool = False) -> List[NativeOp]:
+    """Logical circuit -> native op list of the neutral-atom device (Sec. 6, App. C): static sites, serial gates.
+
+    - Initialisation (optional): the leakage operator L on every atom (the perfect reset before it acts on
+      |0> and changes nothing).
+    - Raman rotation U(phi, Omega, Delta, t), lasting its own t: phase-type error deph(1 - e^{-t/(2 T2)}) (the
+      printed exponent's sign read as a decay), then the asymmetric bit flip scaled by the rotation angle
+      Omega_R t / pi (App. C's angle rule).
+    - Rydberg CZ(phi) on two atoms within the blockade radius, lasting dur_cz: the leakage map K of Eq. (czleak).
+    - During a gate the other atoms decay: T1 = T_vac / N as depolarising (Eq. depolt1), T2 dephasing.
+    - Readout (optional): depolarising noise whose misclassification probability 2p/3 is 1 - F, so p = 3(1 - F)/2.
+    """
+    n = int(dev["n"])
+    passive = not (int(dev.get("flags", 0)) & 1)
+    t1 = float(dev["t_vac"]) / n
+    out: List[NativeOp] = []
+
+    def idle_others(active, t):
+        if passive and t > 0:
+            for j in range(n):
+                if j not in active:
+                    out.append(NativeOp("idle_depol", (j,), (t, t1, float(dev["t2"]))))
+
+    if init:
+        out += [NativeOp("leak_init", (j,), (float(dev["leak_init"]),)) for j in range(n)]
+    for op in ops:
+        if op.name == "u":
+            q = op.qubits[0]
+            phi, om, de, t = op.params
+            t = abs(t)
+            s = math.sqrt(om * om + de * de) * t / math.pi
+            out.append(op)
+            out.append(NativeOp("deph1", (q,), (1 - math.exp(-t / (2 * float(dev["t2"]))),)))
+            if (dev["p10"] > 0 or dev["p01"] > 0) and s > 0:
+                out.append(NativeOp("bitflip_asym", (q,), (float(dev["p10"]) * s, float(dev["p01"]) * s)))
+            idle_others((q,), t)
+        elif op.name == "czphi":
+            a, b = op.qubits
+            (xa, ya), (xb, yb) = dev["sites"][a], dev["sites"][b]
+            if math.hypot(xa - xb, ya - yb) > dev["blockade"]:
+                raise ValueError("CZ(phi) on atoms farther apart than the blockade radius")
+            out.append(op)
+            out.append(NativeOp("leak_cz", (a, b), (float(dev["leak_cz"][0]), float(dev["leak_cz"][1]))))
+            idle_others((a, b), float(dev["dur_cz"]))
+        else:
+            raise ValueError(f"{op.name} is not a neutral-atom native gate")
+    if readout:
+        out += [NativeOp("depol1", (j,), (1.5 * (1 - float(dev["fid_meas"])),)) for j in range(n)]
+    return out

@@ -951,6 +951,63 @@ int vqd_ion_compile(const vqd_ion_device* dev, int nin, const vqd_native_op* in,
   API_END(nullptr)
 }
 
+// Neutral-atom device compiler, Sec. 6 and the neutral-atom table of App. C (static sites; moves, loss
+// and multi-qubit gates left out): serial gates; a Raman rotation is followed by its phase error and the
+// asymmetric bit flip, a Rydberg CZ by the leakage of Eq. czleak; the other atoms decay passively.
+int vqd_na_compile(const vqd_na_device* dev, int nin, const vqd_native_op* in, int init, int readout, int cap,
+                   vqd_native_op* out, int* nout) {
+  API_BEGIN
+  if (!dev || !nout || nin < 0 || (nin > 0 && !in) || (out && cap < 0)) throw Error(VQD_EINVAL, "bad argument");
+  const int n = dev->n;
+  if (n < 1 || n > 32 || !dev->x || !dev->y) throw Error(VQD_EINVAL, "bad device: atom count or sites");
+  if (!(dev->t2 > 0) || !(dev->t_vac > 0) || !(dev->blockade >= 0) || !(dev->dur_cz >= 0))
+    throw Error(VQD_EINVAL, "bad device: T2, vacuum lifetime, blockade radius or CZ duration");
+  auto unit = [](double v) { return v >= 0 && v <= 1; };
+  if (!unit(dev->p10) || !unit(dev->p01) || !unit(dev->leak_init) || !unit(dev->leak_cz_a) || !unit(dev->leak_cz_b))
+    throw Error(VQD_EINVAL, "bad device: a probability outside [0,1]");
+  if (readout && !(dev->fid_meas >= 0.5 && dev->fid_meas <= 1)) throw Error(VQD_EINVAL, "bad device: readout fidelity");
+  const bool passive = !(dev->flags & VQD_NA_NO_PASSIVE);
+  const double pi = 3.14159265358979323846, t1 = dev->t_vac / n;
+  OpSink sink{out, cap};
+  auto idle_others = [&](int a, int b, double t) {
+    if (!passive || t <= 0) return;
+    for (int j = 0; j < n; j++)
+      if (j != a && j != b) sink.emit(VQD_OP_IDLE_DEPOL, j, -1, t, t1, dev->t2);
+  };
+  if (init)
+    for (int j = 0; j < n; j++) sink.emit(VQD_OP_LEAK_INIT, j, -1, dev->leak_init);
+  for (int i = 0; i < nin; i++) {
+    const vqd_native_op& o = in[i];
+    const int ar = native_arity(o.code);
+    if (ar < 1 || o.nq != ar) throw Error(VQD_EINVAL, "bad op at index " + std::to_string(i));
+    for (int j = 0; j < ar; j++)
+      if (o.q[j] < 0 || o.q[j] >= n || (j == 1 && o.q[1] == o.q[0]))
+        throw Error(VQD_EINVAL, "bad qubit at op " + std::to_string(i));
+    if (o.code == VQD_OP_U) {
+      const int q = o.q[0];
+      const double t = std::fabs(o.par[3]);
+      const double sc = std::hypot(o.par[1], o.par[2]) * t / pi;  // rotation angle over pi
+      sink.put(o);
+      sink.emit(VQD_OP_DEPH1, q, -1, 1 - std::exp(-t / (2 * dev->t2)));
+      if ((dev->p10 > 0 || dev->p01 > 0) && sc > 0) sink.emit(VQD_OP_BITFLIP_ASYM, q, -1, dev->p10 * sc, dev->p01 * sc);
+      idle_others(q, -1, t);
+    } else if (o.code == VQD_OP_CZPHI) {
+      const int a = o.q[0], b = o.q[1];
+      if (std::hypot(dev->x[a] - dev->x[b], dev->y[a] - dev->y[b]) > dev->blockade)
+        throw Error(VQD_EINVAL, "CZ(phi) on atoms farther apart than the blockade radius at op " + std::to_string(i));
+      sink.put(o);
+      sink.emit(VQD_OP_LEAK_CZ, a, b, dev->leak_cz_a, dev->leak_cz_b);
+      idle_others(a, b, dev->dur_cz);
+    } else {
+      throw Error(VQD_EINVAL, "op " + std::to_string(i) + " is not a neutral-atom native gate");
+    }
+  }
+  if (readout)
+    for (int j = 0; j < n; j++) sink.emit(VQD_OP_DEPOL1, j, -1, 1.5 * (1 - dev->fid_meas));
+  *nout = sink.cnt;
+  API_END(nullptr)
+}
+
 int vqd_stderr_params(int nq, double fbar, double x, double* p, double* q) {
   API_BEGIN
   if (!p || !q) throw Error(VQD_EINVAL, "NULL output");

@@ -89,6 +89,17 @@ class ion_device(ctypes.Structure):
 VQD_ION_NO_PASSIVE = 1
 
 
+class na_device(ctypes.Structure):
+    """vqd_na_device: neutral-atom device table (identical atoms at fixed sites)."""
+    _fields_ = [("n", ctypes.c_int32), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("blockade", ctypes.c_double),
+                ("t2", ctypes.c_double), ("t_vac", ctypes.c_double), ("p10", ctypes.c_double), ("p01", ctypes.c_double),
+                ("leak_init", ctypes.c_double), ("leak_cz_a", ctypes.c_double), ("leak_cz_b", ctypes.c_double),
+                ("dur_cz", ctypes.c_double), ("fid_meas", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+VQD_NA_NO_PASSIVE = 1
+
+
 class VQDError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libvqd error {code}: {msg}")
@@ -147,6 +158,7 @@ def lib() -> ctypes.CDLL:
             "vqd_si_compile": (I, [P, I, P, I, P, P]),
             "vqd_nv_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_ion_compile": (I, [P, I, P, I, I, P, P]),
+            "vqd_na_compile": (I, [P, I, P, I, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -395,6 +407,24 @@ def vqd_ion_compile(dev: dict, ops, readout: bool = False) -> np.ndarray:
     out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
     _check(lib().vqd_ion_compile(ctypes.byref(d), len(a), _ptr(a), int(bool(readout)), cnt.value, _ptr(out),
                                  ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def vqd_na_compile(dev: dict, ops, init: bool = False, readout: bool = False) -> np.ndarray:
+    """Compile a logical U / CZ(phi) circuit for a neutral-atom device (host only).  ``dev`` holds n, sites
+    (list of (x, y)), blockade, t2, t_vac, p10, p01, leak_init, leak_cz (alpha, beta), dur_cz, fid_meas and
+    optional flags."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    xs = np.ascontiguousarray(np.asarray([s[0] for s in dev["sites"]], dtype=np.float64))
+    ys = np.ascontiguousarray(np.asarray([s[1] for s in dev["sites"]], dtype=np.float64))
+    d = na_device(int(dev["n"]), _ptr(xs), _ptr(ys), float(dev["blockade"]), float(dev["t2"]), float(dev["t_vac"]),
+                  float(dev["p10"]), float(dev["p01"]), float(dev["leak_init"]), float(dev["leak_cz"][0]),
+                  float(dev["leak_cz"][1]), float(dev["dur_cz"]), float(dev["fid_meas"]), int(dev.get("flags", 0)))
+    cnt = ctypes.c_int()
+    args = (int(bool(init)), int(bool(readout)))
+    _check(lib().vqd_na_compile(ctypes.byref(d), len(a), _ptr(a), *args, 0, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=NATIVE_OP_DTYPE)
+    _check(lib().vqd_na_compile(ctypes.byref(d), len(a), _ptr(a), *args, cnt.value, _ptr(out), ctypes.byref(cnt)))
     return out[: cnt.value].copy()
 
 

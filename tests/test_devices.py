@@ -437,3 +437,74 @@ def test_ion_compiled_program_gpu_parity(vqd):
             assert np.abs(vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0)) - want).max() < TOL_F64, runner
         finally:
             vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- neutral atoms (Sec. 6, App. C)
+from oracle.devices import na_compile  # noqa: E402
+from workloads.devices import NA_CLUSTER12, na_cluster_circuit  # noqa: E402
+
+
+def small_na(**kw):
+    dev = {"n": 3, "sites": [(0.0, 0.0), (1.0, 0.0), (5.0, 0.0)], "blockade": 1.0, "t2": 40.0, "t_vac": 300.0, "rabi": 0.1,
+           "p10": 0.01, "p01": 0.02, "leak_init": 0.05, "leak_cz": (0.1, 0.01), "dur_cz": 0.5, "fid_meas": 0.97}
+    dev.update(kw)
+    return dev
+
+
+def test_na_worked_example_by_hand(vqd):
+    """U(pi/2, 0.1, 0, 5) on atom 2 (a pi/2 rotation lasting 5 us), then CZ(phi) on the neighbours (0, 1); T1 = 300/3
+    = 100 us; initialisation leakage first, readout depolarising p = 3(1 - 0.97)/2 last."""
+    dev = small_na()
+    ops = [NativeOp("u", (2,), (math.pi / 2, 0.1, 0.0, 5.0)), NativeOp("czphi", (0, 1), (0.7,))]
+    s = 0.1 * 5.0 / math.pi
+    want = [NativeOp("leak_init", (j,), (0.05,)) for j in range(3)]
+    want += [ops[0], NativeOp("deph1", (2,), (1 - math.exp(-5.0 / 80.0),)),
+             NativeOp("bitflip_asym", (2,), (0.01 * s, 0.02 * s)),
+             NativeOp("idle_depol", (0,), (5.0, 100.0, 40.0)), NativeOp("idle_depol", (1,), (5.0, 100.0, 40.0)),
+             ops[1], NativeOp("leak_cz", (0, 1), (0.1, 0.01)), NativeOp("idle_depol", (2,), (0.5, 100.0, 40.0))]
+    want += [NativeOp("depol1", (j,), (1.5 * 0.03,)) for j in range(3)]
+    same_ops(na_compile(dev, ops, init=True, readout=True), want, 1e-15)
+    same_ops(as_ops(vqd, vqd.vqd_na_compile(dev, ops, init=True, readout=True)), want, 1e-12)
+
+
+def test_na_library_matches_oracle(vqd):
+    for dev in (NA_CLUSTER12, dict(NA_CLUSTER12, flags=1), small_na(sites=[(0.0, 0.0), (1.0, 0.0), (0.5, 0.5)])):
+        ops = na_cluster_circuit(dev, layers=2)
+        for init, readout in ((False, False), (True, True)):
+            same_ops(as_ops(vqd, vqd.vqd_na_compile(dev, ops, init, readout)), na_compile(dev, ops, init, readout), 1e-12)
+
+
+def test_na_leakage_and_readout_closed_forms():
+    """Sec. 6: initialisation leakage leaves tr = (1 - gamma)^n; readout depolarising reads |0> as 1 with
+    probability 1 - F; CZ(phi) on |11> keeps 1 - beta of the trace (Eq. czleak)."""
+    dev = small_na(flags=1, p10=0.0, p01=0.0)
+    rho = evolve.run_program(Program(3, na_compile(dev, [], init=True)))
+    assert abs(measure.trace(rho).real - 0.95 ** 3) < 1e-14
+    rho = evolve.run_program(Program(3, na_compile(dev, [], readout=True)))
+    assert abs(measure.probs(rho, [1])[1] - 0.03) < 1e-14
+    flip = [NativeOp("u", (q,), (0.0, 0.1, 0.0, math.pi / 0.1)) for q in (0, 1)]    # Omega t = pi: |0> -> |1>
+    rho = evolve.run_program(Program(3, na_compile(dev, flip + [NativeOp("czphi", (0, 1), (0.3,))])))
+    assert abs(measure.trace(rho).real - (1 - 0.01)) < 1e-13
+
+
+def test_na_blockade_and_bad_input(vqd):
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_na_compile(small_na(), [NativeOp("czphi", (0, 2), (0.3,))])   # 5 lattice units apart
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_na_compile(small_na(), [NativeOp("cz", (0, 1))])
+    with pytest.raises(ValueError):
+        na_compile(small_na(), [NativeOp("czphi", (0, 2), (0.3,))])
+
+
+@pytest.mark.gpu
+def test_na_compiled_program_gpu_parity(vqd):
+    ops = na_cluster_circuit(NA_CLUSTER12, layers=2)
+    lib_ops = vqd.vqd_na_compile(NA_CLUSTER12, ops, init=True, readout=True)
+    want = evolve.run_program(Program(12, na_compile(NA_CLUSTER12, ops, init=True, readout=True)))
+    for runner in ("plain", "fused"):
+        ctx = vqd.vqd_create(12, vqd.VQD_F64)
+        try:
+            (vqd.vqd_apply_native if runner == "plain" else vqd.vqd_run_program)(ctx, 0, lib_ops)
+            assert np.abs(vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0)) - want).max() < TOL_F64, runner
+        finally:
+            vqd.vqd_destroy(ctx)

@@ -184,3 +184,38 @@ def ion_circuit(dev: Dict, n_gates: int, seed: int = 17) -> List[NativeOp]:
             name = ("rx", "ry", "rz")[int(r.integers(0, 3))]
             ops.append(NativeOp(name, (int(r.integers(0, n)),), (float(r.uniform(-math.pi, math.pi)),)))
     return ops
+
+
+NA_CLUSTER12 = {  # App. C, neutral atoms, 1D cluster-state setting (us, MHz, lattice units)
+    "n": 12,
+    "sites": [(float(i), 0.0) for i in range(12)],
+    "blockade": 1.0,
+    "t2": 100e6,
+    "t_vac": 100e6,
+    "rabi": 0.1,
+    "p10": 0.001,          # p(1 -> 0); the table repeats the label, read as p(1 -> 0) then p(0 -> 1)
+    "p01": 0.03,
+    "leak_init": 0.01,
+    "leak_cz": (0.02, 0.0001),
+    "dur_cz": 0.25,        # not tabulated: a stand-in Rydberg gate time
+    "fid_meas": 0.975,
+}
+
+
+def na_cluster_circuit(dev: Dict, seed: int = 19, layers: int = 1) -> List[NativeOp]:
+    """Linear cluster state in the neutral-atom natives: a pi/2 Raman rotation about y on every atom (phi = pi/2,
+    Delta = 0, Omega t = pi/2), then CZ(pi/2) along the chain (CZ(phi) of Sec. 6 is a CZ up to local phases at
+    phi = pi/2), repeated `layers` times with seeded small detunings."""
+    r = _rng(seed)
+    n = int(dev["n"])
+    om = float(dev["rabi"])
+    ops: List[NativeOp] = []
+    for _ in range(layers):
+        for q in range(n):
+            de = float(r.uniform(-0.01, 0.01))
+            ops.append(NativeOp("u", (q,), (math.pi / 2, om, de, (math.pi / 2) / om)))
+        for q in range(0, n - 1, 2):
+            ops.append(NativeOp("czphi", (q, q + 1), (math.pi / 2,)))
+        for q in range(1, n - 1, 2):
+            ops.append(NativeOp("czphi", (q, q + 1), (math.pi / 2,)))
+    return ops
