@@ -238,7 +238,8 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
  * noise that follows the previous gate on the same qubits (kept right after it).  Each gate goes to the
  * earliest layer after every earlier gate that shares a qubit; a layer lasts as long as its slowest
  * gate.  Output, layer by layer: the layer's gates, each followed by its noise ops, then for every
- * qubit j a passive-noise op of code idle_code (VQD_OP_IDLE or VQD_OP_IDLE_DEPOL) with parameters
+ * qubit j a passive-noise op of code idle_code (VQD_OP_IDLE, VQD_OP_IDLE_DEPOL or VQD_OP_IDLE_T2S, whose third
+ * parameter is then T2*) with parameters
  * (dt, t1[j], t2[j]), dt = layer duration minus the time qubit j was busy in the layer (skipped when
  * dt = 0).  out has room for cap ops; *nout receives the count (VQD_EINVAL if cap is too small). */
 int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int idle_code, const double* t1,

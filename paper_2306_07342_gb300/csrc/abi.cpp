@@ -554,7 +554,8 @@ int vqd_schedule(int n, int nin, const vqd_native_op* in, const double* dur, int
   API_BEGIN
   if (n < 1 || n > 32 || nin < 0 || (nin > 0 && (!in || !dur)) || !t1 || !t2 || !out || !nout || cap < 0)
     throw Error(VQD_EINVAL, "bad argument");
-  if (idle_code != VQD_OP_IDLE && idle_code != VQD_OP_IDLE_DEPOL) throw Error(VQD_EINVAL, "idle_code must be an idle op");
+  if (idle_code != VQD_OP_IDLE && idle_code != VQD_OP_IDLE_DEPOL && idle_code != VQD_OP_IDLE_T2S)
+    throw Error(VQD_EINVAL, "idle_code must be an idle op");
   // gates with their trailing noise ops, each assigned to a layer
   struct G {
     int first, count;  // gate op and its noise ops: in[first .. first+count)

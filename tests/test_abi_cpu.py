@@ -151,7 +151,8 @@ def test_schedule_worked_example_and_oracle(vqd):
             assert g["par"][1] == t1[w[1][0]] and g["par"][2] == t2[w[1][0]]
 
 
-def test_schedule_random_programs_match_oracle(vqd):
+@pytest.mark.parametrize("idle", ["idle_depol", "idle_t2s"])
+def test_schedule_random_programs_match_oracle(vqd, idle):
     from oracle.schedule import schedule
     r = _rng(77)
     n = 5
@@ -169,8 +170,8 @@ def test_schedule_random_programs_match_oracle(vqd):
         ops.append(o)
         d2.append(d)
     t1, t2 = list(r.uniform(20, 100, n)), list(r.uniform(10, 50, n))
-    orc = schedule(n, ops, d2, t1, t2, idle="idle_depol")
-    got = vqd.vqd_schedule(n, ops, d2, t1, t2, idle="idle_depol")
+    orc = schedule(n, ops, d2, t1, t2, idle=idle)
+    got = vqd.vqd_schedule(n, ops, d2, t1, t2, idle=idle)
     assert len(orc) == len(got)
     for o, g in zip(orc, got):
         assert vqd.OP_CODES[g["code"]] == o.name and tuple(g["q"][: g["nq"]]) == o.qubits
