@@ -446,6 +446,17 @@ int vqd_batch_reduce(vqd_t ctx, double* probs, double* trace_re, double* purity)
  * forced outcome. */
 int vqd_measure(vqd_t ctx, int inst, int q, double u, int force, int* outcome, double* prob);
 
+/* Parity measurement of the silicon device (Sec. 7, Eq. m) on qubits qa, qb with collapse.  Outcome 0 is
+ * the odd subspace span{|01>, |10>} (a change of current is detected), outcome 1 the even subspace
+ * span{|00>, |11>}; |ab> means qa = a, qb = b.  With force = -1 the outcome is 0 when u tr(rho) < tr(P_0 rho),
+ * else 1; force = 0 or 1 post-selects.  The state becomes P_m rho P_m / tr(P_m rho); with decay != 0 the
+ * Kraus map K = {|00><00|, |11><11|, |10><10|, |10><01|} of Sec. 7 follows, so that |01> ends in |10>.
+ * Feedback is the caller's: branch on the returned outcome between calls.  Returns the outcome and its
+ * probability (either pointer may be NULL).  Synchronous.  EINVAL for equal or out-of-range qubits or a
+ * zero-probability forced outcome. */
+int vqd_measure_parity(vqd_t ctx, int inst, int qa, int qb, double u, int force, int decay, int* outcome,
+                       double* prob);
+
 /* tr rho (not renormalised: trace-decreasing leakage channels leave it below 1). */
 int vqd_trace(vqd_t ctx, int inst, double* re_out, double* im_out);
 

@@ -107,3 +107,30 @@ def measure_collapse(rho: np.ndarray, q: int, u: float = 0.0, force: int = -1):
     from .evolve import apply_kraus
     out = apply_kraus(rho, (q,), [proj]) / p[m]
     return m, p[m] / tot, out
+
+
+def parity_collapse(rho: np.ndarray, qa: int, qb: int, u: float = 0.0, force: int = -1, decay: bool = True):
+    """Silicon parity measurement of Sec. 7 (Eq. m) on qubits (qa, qb): outcome 0 is the odd subspace
+    span{|01>, |10>}, outcome 1 the even subspace span{|00>, |11>} (|ab>: qa = a, qb = b).  Drawn as 0 when
+    u tr(rho) < tr(P_0 rho) (or forced); the state becomes P_m rho P_m / tr(P_m rho), then, with decay, the
+    Kraus map {|00><00|, |11><11|, |10><10|, |10><01|} of Sec. 7.  Returns (m, probability, new rho)."""
+    from .evolve import apply_kraus
+    p = probs(rho, [qa, qb])                       # index a | b << 1
+    p_odd, p_even = p[1] + p[2], p[0] + p[3]
+    tot = p_odd + p_even
+    m = force if force >= 0 else (0 if u * tot < p_odd else 1)
+    keep = (1, 2) if m == 0 else (0, 3)
+    proj = np.zeros((4, 4), dtype=complex)
+    for r in keep:
+        proj[r, r] = 1.0
+    pm = p_odd if m == 0 else p_even
+    out = apply_kraus(rho, (qa, qb), [proj]) / pm
+    if decay:
+        ket = lambda a, b: a | (b << 1)
+        ks = []
+        for (ra, rb), (ca, cb) in [((0, 0), (0, 0)), ((1, 1), (1, 1)), ((1, 0), (1, 0)), ((1, 0), (0, 1))]:
+            k = np.zeros((4, 4), dtype=complex)
+            k[ket(ra, rb), ket(ca, cb)] = 1.0
+            ks.append(k)
+        out = apply_kraus(out, (qa, qb), ks)
+    return m, pm / tot, out

@@ -1115,6 +1115,58 @@ int vqd_measure(vqd_t c, int inst, int q, double u, int force, int* outcome, dou
   API_END(c)
 }
 
+// Sec. 7, Eq. (m): projective parity measurement of (qa, qb), then optionally the decay map K of |01>
+// into |10>.  Member index of the two-qubit block: r = a | b << 1 (a = qa's bit, b = qb's bit); the odd
+// subspace is r in {1, 2}, the even one r in {0, 3}.
+int vqd_measure_parity(vqd_t c, int inst, int qa, int qb, double u, int force, int decay, int* outcome,
+                       double* prob) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  const int n = c->n[inst];
+  if (qa < 0 || qa >= n || qb < 0 || qb >= n || qa == qb) throw Error(VQD_EINVAL, "measured qubits out of range or equal");
+  if (force < -1 || force > 1) throw Error(VQD_EINVAL, "force must be -1 (draw), 0 or 1");
+  if (force == -1 && !(u >= 0 && u < 1)) throw Error(VQD_EINVAL, "u must be in [0, 1)");
+  const int qs[2] = {qa, qb};
+  timed(c, SC_REDUCE, std::ldexp(1.0, n) * c->esize, 0, 2,
+        [&] { return launch_prob(c->prec, c->ptr(inst), n, 2, qs, c->d_scratch, c->d_out, c->stream); });
+  fetch(c, 4);
+  const double podd = c->h_out[1] + c->h_out[2], peven = c->h_out[0] + c->h_out[3], tot = podd + peven;
+  if (!(tot > 0)) throw Error(VQD_EINVAL, "state has zero trace");
+  const int m = force >= 0 ? force : (u * tot < podd ? 0 : 1);
+  const double pm = m == 0 ? podd : peven;
+  if (!(pm > 0)) throw Error(VQD_EINVAL, "forced outcome has probability zero");
+  auto in_sub = [&](int r) { return m == 0 ? (r == 1 || r == 2) : (r == 0 || r == 3); };
+  Pass p;  // P_m rho P_m / p_m: a real diagonal superoperator, member s = r | c << 2
+  p.kind = KK_ELEM;
+  p.k = 2;
+  p.q[0] = qa;
+  p.q[1] = qb;
+  p.coef.assign(16, 0.0);
+  for (int s = 0; s < 16; s++)
+    if (in_sub(s & 3) && in_sub(s >> 2)) p.coef[s] = 1.0 / pm;
+  timed(c, SC_ELEM, 2.0 * c->bytes(inst) * pass_touched_fraction(p), 0, 1,
+        [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
+  if (decay) {
+    std::vector<cd> K(4 * 16, 0.0);  // row-major 4 x 4, index r = a | b << 1
+    K[0 * 16 + 0 * 4 + 0] = 1.0;     // |00><00|
+    K[1 * 16 + 3 * 4 + 3] = 1.0;     // |11><11|
+    K[2 * 16 + 1 * 4 + 1] = 1.0;     // |10><10|  (a = 1, b = 0)
+    K[3 * 16 + 1 * 4 + 2] = 1.0;     // |10><01|
+    Op op;
+    op.unitary = false;
+    op.k = 2;
+    op.q[0] = qa;
+    op.q[1] = qb;
+    op.m = superop_from_kraus(2, 4, K.data());
+    op.weight = 0.0;
+    apply_op(c, inst, op);
+  }
+  if (outcome) *outcome = m;
+  if (prob) *prob = pm / tot;
+  API_END(c)
+}
+
 int vqd_expect(vqd_t c, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out) {
   API_BEGIN
   need_ctx(c);

@@ -153,6 +153,7 @@ def lib() -> ctypes.CDLL:
             "vqd_set_tile_shape": (I, [P, I, I]),
             "vqd_measure": (I, [P, I, I, D, I, P, P]),
             "vqd_batch_reduce": (I, [P, P, P, P]),
+            "vqd_measure_parity": (I, [P, I, I, I, D, I, I, P, P]),
             "vqd_schedule": (I, [I, I, P, P, I, P, P, I, P, P]),
             "vqd_sc_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_si_compile": (I, [P, I, P, I, P, P]),
@@ -473,6 +474,14 @@ def vqd_batch_reduce(ctx, ns):
         out.append(probs[o:o + 2 ** n])
         o += 2 ** n
     return out, tr, pu
+
+
+def vqd_measure_parity(ctx, inst: int, qa: int, qb: int, u: float = 0.0, force: int = -1, decay: bool = True):
+    """Parity measurement of (qa, qb) with collapse (Sec. 7): outcome 0 = odd, 1 = even; returns (outcome, prob)."""
+    m, p = ctypes.c_int(), ctypes.c_double()
+    _check(lib().vqd_measure_parity(ctx, inst, qa, qb, float(u), int(force), int(bool(decay)), ctypes.byref(m),
+                                    ctypes.byref(p)), ctx)
+    return m.value, p.value
 
 
 def vqd_measure(ctx, inst: int, q: int, u: float = 0.0, force: int = -1):

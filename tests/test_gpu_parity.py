@@ -247,6 +247,24 @@ def test_diagonal_passes_touch_only_changed_amplitudes(vqd, p):
         vqd.vqd_destroy(ctx)
 
 
+@pytest.mark.parametrize("p", PRECS)
+def test_parity_measurement_matches_oracle(vqd, p):
+    """Sec. 7 parity readout on a random 5-qubit state: drawn and forced outcomes, with and without the decay map,
+    against the oracle (outcome, probability, collapsed state)."""
+    rng = np.random.default_rng(91)
+    rho = rand_state(5, rng)
+    for qa, qb, u, force, decay in ((1, 3, 0.37, -1, True), (4, 0, 0.81, -1, False), (2, 1, 0.0, 0, True),
+                                    (2, 1, 0.0, 1, True)):
+        mw, pw, want = measure.parity_collapse(rho, qa, qb, u, force, decay)
+        ctx = make_ctx(vqd, 5, p, rho)
+        try:
+            m, pm = vqd.vqd_measure_parity(ctx, 0, qa, qb, u, force, decay)
+            assert m == mw and abs(pm - pw) < (1e-13 if p != "f32" else 1e-6)
+            assert np.abs(gpu_state(vqd, ctx) - want).max() < (1e-12 if p != "f32" else 1e-5)
+        finally:
+            vqd.vqd_destroy(ctx)
+
+
 # ---------------------------------------------------------------- reductions
 @pytest.mark.parametrize("p", PRECS)
 def test_reductions(vqd, p):

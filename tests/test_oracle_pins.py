@@ -430,6 +430,30 @@ def test_bitflip_asym_closed_forms(p10, p01):
     assert abs(measure.trace(rho) - 1) < 1e-14
 
 
+def test_parity_measurement_closed_forms():
+    """Sec. 7: the Bell state (|00> + |11>)/sqrt 2 has even parity with certainty and the projection leaves it as it is;
+    (|01> + |10>)/sqrt 2 is odd with certainty, and the decay map K leaves the pure |10> (the deterministic
+    initialisation the section describes); |++> is odd or even with probability 1/2 each."""
+    bell = np.zeros(8, dtype=complex)
+    bell[0] = bell[0b101] = 1 / math.sqrt(2)                # |q0 q2> in {00, 11}, q1 = 0
+    bell_rho = np.outer(bell, bell.conj())
+    m, pm, out = measure.parity_collapse(bell_rho, 0, 2, u=0.3, decay=False)
+    assert m == 1 and abs(pm - 1) < 1e-14 and np.abs(out - bell_rho).max() < 1e-14
+    # K as printed lists |00><00| and |11><11| as separate operators, so it also dephases |00> against |11>
+    m, pm, out = measure.parity_collapse(bell_rho, 0, 2, u=0.3)
+    assert np.abs(out - np.diag(np.diag(bell_rho))).max() < 1e-14
+    psi = np.zeros(8, dtype=complex)
+    psi[0b100] = psi[0b001] = 1 / math.sqrt(2)              # (|01> + |10>)/sqrt 2 on (q0, q2)
+    m, pm, out = measure.parity_collapse(np.outer(psi, psi.conj()), 0, 2, u=0.99)
+    want = np.zeros((8, 8))
+    want[0b001, 0b001] = 1.0                                 # q0 = 1, q2 = 0: |10>
+    assert m == 0 and abs(pm - 1) < 1e-14 and np.abs(out - want).max() < 1e-14
+    plus = np.full(4, 0.5, dtype=complex)
+    for u, m_want in ((0.2, 0), (0.7, 1)):
+        m, pm, out = measure.parity_collapse(np.outer(plus, plus.conj()), 0, 1, u=u, decay=False)
+        assert m == m_want and abs(pm - 0.5) < 1e-14 and abs(np.trace(out).real - 1) < 1e-14
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4
