@@ -265,6 +265,61 @@ def test_parity_measurement_matches_oracle(vqd, p):
             vqd.vqd_destroy(ctx)
 
 
+def qnd_initialise(meas, x_gate, crot, draws):
+    """Sec. 7's QND initialisation of Q1, Q2, Q3 (Eq. initqdots) with classical feedback, driven through callbacks:
+    meas(u) is the parity readout of (Q1, Q2) with decay, returning the outcome ("0" odd, "1" even); x_gate(q)
+    flips qubit q; crot() is the controlled-X from Q3 to Q2.  Two rounds: readout, X on Q1 if even, readout
+    (now |10> on Q1 Q2), CROT, readout (= Q3), X on Q3 if it read 1; the second round re-prepares Q1 Q2."""
+    outcomes = []
+    for _ in range(2):
+        p1 = meas(next(draws))
+        if p1 == 1:
+            x_gate(0)
+        meas(next(draws))
+        crot()
+        p3 = meas(next(draws))
+        outcomes.append((p1, p3))
+        if p3 == 1:
+            x_gate(2)
+    return outcomes
+
+
+def test_qnd_initialisation_with_feedback(vqd):
+    """From a random 3-qubit state, the feedback protocol leaves |Q1 Q2 Q3> = |100> whatever the draws, on the GPU
+    and in the oracle, with the same outcomes."""
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    CX = np.eye(4, dtype=complex)[[0, 3, 2, 1]]          # control = first target (low bit), target = second
+    for seed in range(3):
+        rng = np.random.default_rng(500 + seed)
+        rho0 = rand_state(3, rng)
+        u = list(rng.uniform(size=6))
+        ctx = make_ctx(vqd, 3, "f64", rho0)
+        try:
+            got = qnd_initialise(lambda x: vqd.vqd_measure_parity(ctx, 0, 0, 1, x, -1, True)[0],
+                                 lambda q: vqd.vqd_apply_unitary(ctx, 0, [q], X),
+                                 lambda: vqd.vqd_apply_unitary(ctx, 0, [2, 1], CX), iter(u))
+            state = {"rho": rho0}
+
+            def o_meas(x):
+                m, _, state["rho"] = measure.parity_collapse(state["rho"], 0, 1, x, -1, True)
+                return m
+
+            def o_x(q):
+                state["rho"] = evolve.apply_unitary(state["rho"], (q,), X)
+
+            def o_crot():
+                state["rho"] = evolve.apply_unitary(state["rho"], (2, 1), CX)
+
+            want = qnd_initialise(o_meas, o_x, o_crot, iter(u))
+            assert got == want
+            final = np.zeros((8, 8))
+            final[0b001, 0b001] = 1.0                        # Q1 = q0 = 1, Q2 = Q3 = 0
+            assert np.abs(state["rho"] - final).max() < 1e-12
+            assert np.abs(gpu_state(vqd, ctx) - final).max() < 1e-12
+        finally:
+            vqd.vqd_destroy(ctx)
+
+
 # ---------------------------------------------------------------- reductions
 @pytest.mark.parametrize("p", PRECS)
 def test_reductions(vqd, p):

@@ -454,6 +454,30 @@ def test_parity_measurement_closed_forms():
         assert m == m_want and abs(pm - 0.5) < 1e-14 and abs(np.trace(out).real - 1) < 1e-14
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_qnd_initialisation_is_deterministic(seed):
+    """Sec. 7 (Eq. initqdots): parity readouts of (Q1, Q2) with the decay map, X on Q1 after an even outcome,
+    CROT from Q3 to Q2 and X on Q3 after reading it 1, repeated once, leave |Q1 Q2 Q3> = |100> from any state."""
+    from ._lib import rand_state
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    CX = np.eye(4, dtype=complex)[[0, 3, 2, 1]]
+    rng = np.random.default_rng(700 + seed)
+    rho = rand_state(3, rng)
+    u = iter(rng.uniform(size=6))
+    for _ in range(2):
+        p1, _, rho = measure.parity_collapse(rho, 0, 1, next(u))
+        if p1 == 1:
+            rho = evolve.apply_unitary(rho, (0,), X)
+        _, _, rho = measure.parity_collapse(rho, 0, 1, next(u))
+        rho = evolve.apply_unitary(rho, (2, 1), CX)
+        p3, _, rho = measure.parity_collapse(rho, 0, 1, next(u))
+        if p3 == 1:
+            rho = evolve.apply_unitary(rho, (2,), X)
+    want = np.zeros((8, 8))
+    want[0b001, 0b001] = 1.0
+    assert np.abs(rho - want).max() < 1e-13
+
+
 # ---------------------------------------------------------------- unitary circuits, graph states
 def test_unitary_circuit_matches_statevector():
     n = 4
