@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cols", type=int, default=7)
     ap.add_argument("--depth", type=int, default=60)
     ap.add_argument("--batch-count", type=int, default=1024, help="instances of the batched neutral-atom workload")
+    ap.add_argument("--fp64-diag", action="store_true",
+                    help="time FP64 elementwise passes (real full, dephasing, Rz) on a 14-qubit state and exit")
     ap.add_argument("--precision", default=None, choices=["sc_grid14", "ion15", "spin16"],
                     help="instead of timing: error of the complex64 paths against the FP64 path on one workload")
     ap.add_argument("--prefix", type=int, default=0, help="--precision: only the first N native ops (0 = all)")
@@ -453,8 +455,47 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fp64_diag():
+    """FP64 elementwise passes on a 14-qubit complex128 state: a real diagonal superoperator that changes every
+    amplitude, a dephasing and an Rz (both leave half of the amplitudes untouched); 20 timed passes each after 3
+    warm-up passes, CUDA events through the library's launch accounting."""
+    import numpy as np
+    import torch
+    from paper_2306_07342_gb300 import build as _b
+    _b.build()
+    from paper_2306_07342_gb300 import vqd
+    from workloads.circuits import NativeOp
+    n = 14
+    ctx = vqd.vqd_create(n, vqd.VQD_F64, torch.cuda.current_stream().cuda_stream)
+    real = np.diag([0.9, 0.8, 0.7, 0.6]).astype(complex)
+    cases = {"real_full": lambda: vqd.vqd_apply_superop(ctx, 0, [7], real),
+             "deph_half": lambda: vqd.vqd_apply_native(ctx, 0, [NativeOp("deph1", (7,), (0.1,))]),
+             "rz_complex_half": lambda: vqd.vqd_apply_native(ctx, 0, [NativeOp("rz", (7,), (0.3,))])}
+    out = {}
+    try:
+        for name, f in cases.items():
+            for _ in range(3):
+                f()
+            torch.cuda.synchronize()
+            vqd.vqd_profile(ctx, 2)
+            vqd.vqd_profile_reset(ctx)
+            for _ in range(20):
+                f()
+            torch.cuda.synchronize()
+            st = vqd.vqd_profile_read(ctx)["elem"]
+            vqd.vqd_profile(ctx, 0)
+            ms = st["total_ms"] / st["launches"]
+            out[name] = {"avg_ms": ms, "alg_GBps": st["alg_bytes"] / st["launches"] / (ms * 1e-3) / 1e9}
+    finally:
+        vqd.vqd_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.fp64_diag:
+        run_fp64_diag()
+        return
     if args.precision:
         run_precision(args)
         return
