@@ -9,11 +9,17 @@ Modules
 -------
 ``compile``  device compiler: native operation -> unitary or Kraus set (Sec. 3, 4-8, App. B).
 ``evolve``   state initialisation and the literal update rho <- sum_k K rho K^dagger.
-``measure``  probabilities, Pauli expectation values, trace, purity.
+``measure``  probabilities, Pauli expectation values, trace, purity, trace distance, Uhlmann
+             fidelity, projective and parity measurement with collapse (Secs. 6, 7).
 ``brute``    independent full-space constructions (Kronecker chains, 4^n superoperators)
              used only to pin the oracle itself.
+``trajectories``  statevector trajectories with their own counter-based Philox draws (Sec. 2).
+``schedule`` ASAP scheduling with passive idle noise (Sec. 2).
+``devices``  the five device-family compilers (Secs. 4-8, App. C).
 
-Parity status: every function here is pinned by tests in ``tests/test_oracle_pins.py``
-except the readings listed as "parity unpinned" in their docstrings (none at present).
+Parity status: every function here is pinned by tests in ``tests/test_oracle_pins.py``,
+``tests/test_devices.py``, ``tests/test_trajectories.py`` and ``tests/test_abi_cpu.py``
+(closed forms, worked examples, brute force), except the readings listed as "parity unpinned"
+in their docstrings (none at present).
 """
 from . import compile, evolve, measure, brute  # noqa: F401
