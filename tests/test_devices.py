@@ -511,3 +511,34 @@ def test_na_compiled_program_gpu_parity(vqd):
             assert np.abs(vqd.rho_from_flat(vqd.vqd_get_state(ctx, 0)) - want).max() < TOL_F64, runner
         finally:
             vqd.vqd_destroy(ctx)
+
+
+# ---------------------------------------------------------------- host contract shared by the compilers
+def test_compilers_refuse_null_device_and_short_buffers(vqd):
+    """Every compiler refuses a NULL device with VQD_EINVAL.  The compilers share one output sink, so the
+    capacity check is exercised through one of them: a buffer one op shorter than the compiled program is refused,
+    and the exact size is accepted and filled with the same ops as the counting run."""
+    import ctypes
+    a = vqd.native_ops(si_circuit(SI6, 20))
+    cnt = ctypes.c_int()
+    lib = vqd.lib()
+    calls = {"sc": lambda: lib.vqd_sc_compile(None, len(a), vqd._ptr(a), 0, 0, None, ctypes.byref(cnt)),
+             "si": lambda: lib.vqd_si_compile(None, len(a), vqd._ptr(a), 0, None, ctypes.byref(cnt)),
+             "nv": lambda: lib.vqd_nv_compile(None, len(a), vqd._ptr(a), 0, 0, None, ctypes.byref(cnt)),
+             "ion": lambda: lib.vqd_ion_compile(None, len(a), vqd._ptr(a), 0, 0, None, ctypes.byref(cnt)),
+             "na": lambda: lib.vqd_na_compile(None, len(a), vqd._ptr(a), 0, 0, 0, None, ctypes.byref(cnt))}
+    for name, call in calls.items():
+        assert call() == vqd.VQD_EINVAL, name
+    keep = {k: np.ascontiguousarray(np.asarray(SI6[k], np.float64).reshape(-1))
+            for k in ("t1", "t2", "freq", "rabi", "fid_1q", "freq_cz", "fid_cz", "xtalk_on", "xtalk_off")}
+    d = vqd.si_device(6, vqd._ptr(keep["t1"]), vqd._ptr(keep["t2"]), vqd._ptr(keep["freq"]), vqd._ptr(keep["rabi"]),
+                      vqd._ptr(keep["fid_1q"]), float(SI6["x_1q"]), vqd._ptr(keep["freq_cz"]), vqd._ptr(keep["fid_cz"]),
+                      float(SI6["x_cz"]), vqd._ptr(keep["xtalk_on"]), vqd._ptr(keep["xtalk_off"]), 0)
+    assert lib.vqd_si_compile(ctypes.byref(d), len(a), vqd._ptr(a), 0, None, ctypes.byref(cnt)) == vqd.VQD_OK
+    need = cnt.value
+    out = np.zeros(need, dtype=vqd.NATIVE_OP_DTYPE)
+    assert lib.vqd_si_compile(ctypes.byref(d), len(a), vqd._ptr(a), need - 1, vqd._ptr(out), ctypes.byref(cnt)) \
+        == vqd.VQD_EINVAL
+    assert lib.vqd_si_compile(ctypes.byref(d), len(a), vqd._ptr(a), need, vqd._ptr(out), ctypes.byref(cnt)) == vqd.VQD_OK
+    assert cnt.value == need
+    same_ops(as_ops(vqd, out), as_ops(vqd, vqd.vqd_si_compile(SI6, si_circuit(SI6, 20))), 0.0)
