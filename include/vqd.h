@@ -145,7 +145,8 @@ typedef struct {
 size_t vqd_state_bytes(int n, int prec);
 
 /* One n-qubit state (1 <= n <= VQD_MAX_QUBITS) in library-allocated device memory, initialised
- * to |0..0><0..0|.  stream is a cudaStream_t (NULL = legacy default stream).  The library owns
+ * to |0..0><0..0|: the density matrix on which Sec. 2 simulates the device's noisy channel (the
+ * representation that captures noise completely, at quadratic cost over the statevector).  stream is a cudaStream_t (NULL = legacy default stream).  The library owns
  * the memory; vqd_destroy frees it. */
 int vqd_create(int n, int prec, void* stream, vqd_t* out);
 
@@ -177,7 +178,9 @@ int vqd_init_product_diag(vqd_t ctx, int inst, const double* excited);
  * Applying operators (asynchronous; one pass over the state per call)
  * ---------------------------------------------------------------------------------------- */
 
-/* rho <- U rho U^dagger, U is 2^k x 2^k (k = 1 or 2) on distinct targets.  ENOTCP if U is not
+/* rho <- U rho U^dagger, U is 2^k x 2^k (k = 1 or 2) on distinct targets: one unitary operator of the
+ * channel a device specification makes from a circuit (Sec. 2); the native gates of Sec. 4-8 are
+ * such unitaries.  ENOTCP if U is not
  * unitary within 1e-10 (unless VQD_NO_CHECK is set with vqd_set_flags). */
 int vqd_apply_unitary(vqd_t ctx, int inst, int k, const int* targets, const vqd_c128* U);
 
@@ -187,7 +190,8 @@ int vqd_apply_unitary(vqd_t ctx, int inst, int k, const int* targets, const vqd_
 int vqd_apply_kraus(vqd_t ctx, int inst, int k, const int* targets, int nK, const vqd_c128* K);
 
 /* vec-group <- S vec-group with the 4^k x 4^k superoperator S (index convention above);
- * no positivity check. */
+ * no positivity check.  S is the matrix form of a general Kraus map of Sec. 2 acting on the density
+ * matrix, S = sum_j conj(K_j) (x) K_j, so any channel of Sec. 3 can be passed in this form. */
 int vqd_apply_superop(vqd_t ctx, int inst, int k, const int* targets, const vqd_c128* S);
 
 /* Compile each native op with the device compiler and apply it with one pass over the state
@@ -201,9 +205,14 @@ int vqd_apply_native(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, un
 #define VQD_MAX_FUSE 6
 int vqd_run_program(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, int fuse_qubits, unsigned flags);
 
-/* Batched path: instance i of a batch context runs ops[offsets[i] .. offsets[i+1]) (native ops),
- * all instances in ONE persistent kernel launch (each CTA takes whole instances from a queue,
- * largest first).  offsets has count+1 entries. */
+/* Batched path: instance i of a batch context runs ops[offsets[i] .. offsets[i+1]) (native ops)
+ * through the fused path.  Every instance's program is planned into stages; stage w of every instance
+ * forms wave w, one persistent-kernel launch whose CTAs take (instance, stage, chunk of tiles) items
+ * from an atomic queue, largest instances first, so that no CTA waits for another.  The waves of a
+ * batch are captured into a CUDA graph on the context's stream (when it can capture) and the graph is
+ * replayed when the same batch runs again.  offsets has count+1 entries.  The paper runs one device
+ * at a time; batching many instances (parameter sweeps such as the noise-severity scans of Sec. 5) is
+ * this library's addition. */
 int vqd_run_batch(vqd_t ctx, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags);
 
 /* ------------------------------------------------------------------------------------------
@@ -423,13 +432,17 @@ int vqd_stderr_params(int nq, double fbar, double x, double* p_deph, double* q_d
  * Reductions (synchronous; FP64 accumulation, fixed summation order)
  * ---------------------------------------------------------------------------------------- */
 
-/* Marginal Z-basis probabilities of qubits[0..m-1] (distinct; m <= n, 2^m outputs):
+/* Marginal Z-basis probabilities of qubits[0..m-1] (distinct; m <= n, 2^m outputs), the outcome
+ * distribution of a projective measurement in the computational basis (Sec. 3.6 readout, and the
+ * populations reported for the Bell states of Sec. 7):
  * out[v] = sum of Re rho[x][x] over basis states x whose bits on qubits spell v (qubits[0]
  * = least significant bit of v). */
 int vqd_prob(vqd_t ctx, int inst, int m, const int* qubits, double* out);
 
 /* *out = Re sum_t coeffs[t] tr(P_t rho); paulis is nterms x n bytes, paulis[t*n + q] in
- * {0=I, 1=X, 2=Y, 3=Z} is the factor on qubit q. */
+ * {0=I, 1=X, 2=Y, 3=Z} is the factor on qubit q.  The expected value of a Pauli sum: the stabilisers
+ * and logical operators of Sec. 6.4, the Hamiltonian terms of the VQE of Sec. 8.4, and the quantity
+ * SampleExpecPauliString estimates by trajectories in Sec. 2. */
 int vqd_expect(vqd_t ctx, int inst, int nterms, const uint8_t* paulis, const double* coeffs, double* out);
 
 /* Reductions of every instance of a batch context in one batched launch (one CTA per chunk of 2^20
@@ -457,10 +470,13 @@ int vqd_measure(vqd_t ctx, int inst, int q, double u, int force, int* outcome, d
 int vqd_measure_parity(vqd_t ctx, int inst, int qa, int qb, double u, int force, int decay, int* outcome,
                        double* prob);
 
-/* tr rho (not renormalised: trace-decreasing leakage channels leave it below 1). */
+/* tr rho (not renormalised: the trace-decreasing leakage and loss maps of Sec. 3.7 and the CPTN
+ * map of Sec. 6.3 leave it below 1). */
 int vqd_trace(vqd_t ctx, int inst, double* re_out, double* im_out);
 
-/* tr(rho^dagger rho) = sum |rho_ij|^2 (equals tr rho^2 for Hermitian rho). */
+/* tr(rho^dagger rho) = sum |rho_ij|^2 (equals tr rho^2 for Hermitian rho).  The paper prints no purity;
+ * it is the mixedness of the density matrix of Sec. 2, 1 for the pure output of a noiseless circuit and
+ * lowered by every mixing channel of Sec. 3, so it tracks how much noise a program has applied. */
 int vqd_purity(vqd_t ctx, int inst, double* out);
 
 /* Copy instance inst to / from host, FP64 complex, layout above (4^n entries). */
@@ -510,10 +526,14 @@ int vqd_traj_expect(int n, int prec, int nops, const vqd_native_op* ops, unsigne
  *   dev_out    DEVICE array of 2^m doubles, written on `stream` (a cudaStream_t; NULL = legacy
  *              default stream).  The call is asynchronous: synchronise the stream before reading.
  *
- * Returns VQD_OK, VQD_EINVAL (bad argument, or m above VQD_PROB_STATIC_MAX_M: the static scratch
- * holds at most 2^14 partial sums) or VQD_EDEVICE; the message is in vqd_last_error(NULL).
+ * Returns VQD_OK, VQD_EINVAL (bad argument; dev_state not aligned to its amplitude size, 8 bytes for
+ * VQD_F32 and 16 otherwise, or dev_out not 8-byte aligned; or m above VQD_PROB_STATIC_MAX_M: the static
+ * scratch holds at most 2^14 partial sums) or VQD_EDEVICE; the message is in vqd_last_error(NULL).
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current) and keeps it; make that first call before any stream capture.  All calls
+ * that device current) and keeps it, keyed by the device ordinal; make that first call before any
+ * stream capture.  The kept address belongs to the device's primary context, the one the CUDA runtime
+ * uses: call it only with that context current, and not after cudaDeviceReset in the same process
+ * (the reset destroys the context the address belongs to).  All calls
  * share the one array and each call overwrites what the previous one left there: calls that
  * overlap on the GPU (other streams, or other host threads) race, so serialise them.
  * ---------------------------------------------------------------------------------------- */

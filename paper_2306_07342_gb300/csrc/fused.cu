@@ -126,7 +126,9 @@ static Op compose(const Op& first, const Op& second) {
 // per amplitude with coefficients in registers, against 16 MACs and 16 coefficient loads for the dense
 // form.  S[so][si] = A[ao][ai] B[bo][bi] with s = r0 | r1 << 1 | c0 << 2 | c1 << 3, a = r0 | c0 << 1 and
 // b = r1 | c1 << 1, so S realigned as M[(ao, ai)][(bo, bi)] has rank one; the factors are one column and
-// one row of M through its largest entry, accepted when they reproduce every entry to 1e-13 of it.
+// one row of M through its largest entry, accepted when they reproduce every entry to 1e-15 of it (a
+// few FP64 roundings of an exact product, as the kron of two one-qubit channels gives), so that a
+// slightly entangling channel is never replaced by an approximation.
 static bool split_product(const Op& op, Op& a, Op& b) {
   if (op.k != 2 || op.unitary || is_diag(op)) return false;
   auto a_of = [](int s) { return (s & 1) | (((s >> 2) & 1) << 1); };
@@ -147,7 +149,7 @@ static bool split_product(const Op& op, Op& a, Op& b) {
   for (int y = 0; y < 16; y++) B[y] = M[pi * 16 + y] / M[pi * 16 + pj];
   for (int x = 0; x < 16; x++)
     for (int y = 0; y < 16; y++)
-      if (std::abs(M[x * 16 + y] - A[x] * B[y]) > 1e-13 * top) return false;
+      if (std::abs(M[x * 16 + y] - A[x] * B[y]) > 1e-15 * top) return false;
   a = Op();
   a.unitary = false;
   a.k = 1;
@@ -221,7 +223,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
     if (is_diag(op)) {  // factor of member t = r | c << 1
       for (int t = 0; t < 4; t++) {
         const int r = t & 1, c = t >> 1;
-        out.push_back(op.unitary ? op.m[r * 2 + r] * std::conj(op.m[c * 2 + c]) : op.m[t * 5]);
+        out.push_back(op.unitary ? (r == c ? cd(1.0) : op.m[r * 2 + r] * std::conj(op.m[c * 2 + c])) : op.m[t * 5]);
       }
       return on_b ? BK_DIAG_B : BK_DIAG_A;
     }
@@ -233,7 +235,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
   if (is_diag(op)) {  // factor of member t = r | c << 2
     for (int t = 0; t < 16; t++) {
       const int r = t & 3, c = t >> 2;
-      out.push_back(op.unitary ? m[r * 4 + r] * std::conj(m[c * 4 + c]) : m[t * 17]);
+      out.push_back(op.unitary ? (r == c ? cd(1.0) : m[r * 4 + r] * std::conj(m[c * 4 + c])) : m[t * 17]);
     }
     return BK_DIAG2;
   }

@@ -787,6 +787,12 @@ extern "C" int vqd_prob_static(const void* dev_state, int n, int prec, int m, co
       return report_static_error(VQD_EINVAL, "vqd_prob_static: measured qubit out of range or repeated");
     used |= 1u << qubits[j];
   }
+  // The kernels read whole amplitudes (8 bytes for complex64, 16 for complex128 and float-float) and
+  // write doubles: a misaligned address would fault on the GPU, so it is refused here.
+  const uintptr_t align = prec == VQD_F32 ? 8 : 16;
+  if ((uintptr_t)dev_state % align != 0 || (uintptr_t)dev_out % 8 != 0)
+    return report_static_error(VQD_EINVAL,
+                               "vqd_prob_static: dev_state must be 8-byte (VQD_F32) or 16-byte aligned and dev_out 8-byte aligned");
   double* scratch = nullptr;
   cudaError_t e = static_scratch(&scratch);
   if (e == cudaSuccess) {

@@ -11,13 +11,12 @@
 
 namespace vqd {
 
-// Launch one plain-path pass over an n-qubit state (complex64 if prec == VQD_F32, else complex128).
-// A diagonal factor within a few ulps of 1: the entries |d_r|^2 of a diagonal unitary's superoperator
-// are exactly 1 but arrive rounded from their FP64 product.  Elementwise passes leave such amplitudes
-// untouched (factor exactly 1).
-inline bool is_unit_factor(const std::complex<double>& c) {
-  return std::abs(c.real() - 1.0) <= 1e-15 && std::abs(c.imag()) <= 1e-15;
-}
+// A diagonal factor equal to 1: elementwise passes (plain and fused) leave the amplitudes with this
+// factor untouched.  The comparison is exact.  The device compiler and the fused composer write the
+// factors |U_rr|^2 of diagonal unitaries as exactly 1 (see superop_from_unitary), so a phase or a
+// dephasing skips the members whose row and column index agree; a factor of a caller's superoperator
+// is skipped only when it is exactly 1.
+inline bool is_unit_factor(const std::complex<double>& c) { return c.real() == 1.0 && c.imag() == 0.0; }
 // Fraction of the state's amplitudes a plain pass reads and writes: elementwise passes skip the
 // amplitudes whose factor is 1; every other pass touches all of them.
 double pass_touched_fraction(const Pass& p);

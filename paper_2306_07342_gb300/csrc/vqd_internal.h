@@ -32,7 +32,8 @@ struct Op {
 Op compile_native(const vqd_native_op& op, unsigned flags);
 void stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);
 std::vector<cd> superop_from_kraus(int k, int nK, const cd* K);   // sum conj(K) (x) K
-std::vector<cd> superop_from_unitary(int k, const cd* U);
+std::vector<cd> superop_from_unitary(int k, const cd* U);            // |U_rr|^2 of a diagonal U set to 1
+bool is_diagonal_matrix(int d, const cd* M);
 void check_unitary(int k, const cd* U);                           // throws VQD_ENOTCP
 void check_cptn(int k, int nK, const cd* K);                      // throws VQD_ENOTCP
 int native_arity(int code);

@@ -188,3 +188,23 @@ def test_fused_plan_splits_tensor_product_channels(vqd):
     info = vqd.vqd_plan_info(4, vqd.VQD_F32, corr, fuse_qubits=4)
     assert info["sup2"] == 1 and info["sup1"] == 0
 
+
+
+def test_fused_plan_keeps_slightly_correlated_channels_dense(vqd):
+    """A two-qubit channel that is a product only up to 5e-14 (depol2 with p = 2e-13) stays one channel: the
+    planner's product test accepts only a few FP64 roundings of an exact product, so no channel is replaced
+    by an approximation above FP64 rounding."""
+    info = vqd.vqd_plan_info(4, vqd.VQD_F64, [NativeOp("depol2", (0, 2), (2e-13,))], fuse_qubits=4)
+    assert info["sup2"] == 1 and info["sup1"] == 0
+
+
+@pytest.mark.parametrize("prec_name,state_addr,out_addr", [("f64", 0x10008, 0x20000), ("split", 0x10004, 0x20000),
+                                                           ("f32", 0x10004, 0x20000), ("f32", 0x10008, 0x20004)])
+def test_prob_static_refuses_misaligned_addresses(vqd, prec_name, state_addr, out_addr):
+    """Misaligned device addresses are refused with VQD_EINVAL before any CUDA call (these fake addresses
+    never reach a GPU), instead of faulting in the kernel."""
+    prec = {"f64": vqd.VQD_F64, "f32": vqd.VQD_F32, "split": vqd.VQD_F32_SPLIT}[prec_name]
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_prob_static(state_addr, 4, prec, [0, 1], out_addr)
+    assert e.value.code == vqd.VQD_EINVAL and "aligned" in str(e.value)
+

@@ -1,5 +1,6 @@
 """Monte-Carlo trajectories (Sec. 2): oracle pins on CPU, GPU parity (one by one and in the mean)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -24,6 +25,19 @@ def hamiltonian(n, rng, nterms=6):
 
 
 # ---------------------------------------------------------------- CPU pins of the oracle
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def test_philox_known_answer_vectors():
+    """The oracle's Philox4x32-10 reproduces the generator's published known-answer vectors: a swapped
+    multiplier, key schedule constant or output word changes every one of them."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if ln.strip() and ln[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        assert otj.philox4x32_10(tuple(w[0:4]), tuple(w[4:6])) == tuple(w[6:10])
+
+
 def test_philox_uniform_draws_are_uniform_and_distinct():
     u = np.array([otj.uniform(12345, op, t) for op in range(40) for t in range(250)])
     assert u.min() >= 0.0 and u.max() < 1.0
