@@ -9,6 +9,8 @@ Modules
 -------
 ``compile``  device compiler: native operation -> unitary or Kraus set (Sec. 3, 4-8, App. B).
 ``evolve``   state initialisation and the literal update rho <- sum_k K rho K^dagger.
+``cloop``    the same update as plain FP64 C loops (``c/kraus_loop.c``, gcc + OpenMP), for full-size runs
+             and for the timed CPU baseline.
 ``measure``  probabilities, Pauli expectation values, trace, purity, trace distance, Uhlmann
              fidelity, projective and parity measurement with collapse (Secs. 6, 7).
 ``brute``    independent full-space constructions (Kronecker chains, 4^n superoperators)

@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import evolve, measure
+from oracle import cloop, evolve, measure
 from oracle import compile as oc
 from workloads import config1_chain6, config2_sc_grid, config3_ion_alltoall, config5_spin_chain
 from workloads.circuits import NativeOp, OP_NAMES, Program, random_program
@@ -342,19 +342,30 @@ def test_reductions(vqd, p):
 
 
 # ---------------------------------------------------------------- batched persistent path
-@pytest.mark.parametrize("p,fuse", [("f64", 0), ("f32", 0), ("f32", 3), ("split", 0)])
-def test_batch_matches_per_instance_oracle(vqd, p, fuse):
-    """Uneven instances in one batched run: single-tile instances, and (n = 9, 10) multi-stage ones
-    whose stages span several waves and tile chunks."""
+@pytest.fixture(scope="module")
+def batch_programs():
+    """Uneven instances of the neutral-atom batch workload and their oracle states (computed once): single-tile
+    instances (n = 3..8), multi-stage ones (n = 9, 10) and the largest sizes of the batch configuration (n = 11,
+    12; one layer each, the oracle's cost growing as 4^n per op)."""
     from workloads import config4_neutral_batch
     progs = config4_neutral_batch(seed=8, count=10, n_lo=3, n_hi=8, depth=3)
     progs += config4_neutral_batch(seed=9, count=2, n_lo=9, n_hi=10, depth=2)
+    progs += [config4_neutral_batch(seed=10 + m, count=1, n_lo=m, n_hi=m, depth=1)[0] for m in (11, 12)]
+    assert [q.n for q in progs[-2:]] == [11, 12]
+    return progs, [cloop.run_program(q) for q in progs]
+
+
+@pytest.mark.parametrize("p,fuse", [("f64", 0), ("f32", 0), ("f32", 3), ("split", 0)])
+def test_batch_matches_per_instance_oracle(vqd, p, fuse, batch_programs):
+    """Uneven instances in one batched run, up to the batch configuration's largest size (n = 12), whose
+    stages span several waves and tile chunks, each against the oracle."""
+    progs, wants = batch_programs
     ctx = vqd.vqd_create_batch([q.n for q in progs], prec_code(vqd, p))
     try:
         vqd.vqd_run_batch(ctx, [q.ops for q in progs], fuse)
         probs, trs, purs = vqd.vqd_batch_reduce(ctx, [q.n for q in progs])
         for i, prog in enumerate(progs):
-            want = evolve.run_program(prog)
+            want = wants[i]
             got = gpu_state(vqd, ctx, i)
             t = tol(p, len(prog.ops))
             assert np.abs(got - want).max() < t, i

@@ -582,3 +582,44 @@ def test_measure_collapse_bell_and_product_states():
     m, pm, out = measure.measure_collapse(rho, 1, force=1)
     assert abs(pm - 0.6) < 1e-15
     assert np.abs(out - np.kron(np.diag([0, 1]), a)).max() < 1e-15
+
+
+# ---------------------------------------------------------------- the C-loop evaluation of the same update
+@pytest.mark.parametrize("n,targets,nk", [(2, (1,), 3), (3, (0, 2), 4), (4, (3, 0), 5), (4, (2,), 2), (4, (3, 0, 1), 3),
+                                          (5, (1, 4, 2, 0), 2)])
+def test_c_loop_matches_brute_superoperator(n, targets, nk):
+    """The loop form (oracle/c/kraus_loop.c) of sum_j K_j rho K_j^dagger against the 4^n x 4^n Kronecker
+    superoperator, for one to four target qubits in any order."""
+    from oracle import cloop
+    rng = np.random.default_rng(300 + n + nk)
+    ks = rand_kraus(2 ** len(targets), nk, rng)
+    rho = rand_state(n, rng)
+    S = brute.superop([brute.full_operator(K, targets, n) for K in ks])
+    want = brute.unvec(S @ brute.vec(rho))
+    got = cloop.apply_kraus(np.ascontiguousarray(rho), targets, ks)
+    assert np.abs(got - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("seed,n", [(51, 3), (52, 5), (53, 7)])
+def test_c_loop_and_tensor_oracle_agree_on_random_programs(seed, n):
+    """Every native op kind, evaluated by the C loops and by the tensor contractions: the same result up to
+    the rounding of the summation order, whatever the thread count."""
+    from oracle import cloop
+    prog = random_program(seed, n, 150)
+    want = evolve.run_program(prog)
+    for threads in (1, 3):
+        got = cloop.run_program(prog, threads=threads)
+        assert np.abs(got - want).max() < 1e-13
+    cloop.set_threads(cloop.max_threads())
+
+
+@pytest.mark.parametrize("p", [0.05, 0.7])
+def test_c_loop_bell_state_fidelities(p):
+    """The depolarised Bell-state fidelities (closed forms from Eqs. depol1/depol2) through the C loops."""
+    from oracle import cloop
+    psi = bell()
+    f = lambda r: measure.fidelity_pure(r, psi)
+    rho = np.ascontiguousarray(np.outer(psi, psi.conj()))
+    assert abs(f(cloop.apply_kraus(rho.copy(), (0, 1), oc.depol2(p))) - (1 - 4 * p / 5)) < 1e-14
+    both = cloop.apply_kraus(cloop.apply_kraus(rho.copy(), (0,), oc.depol1(p)), (1,), oc.depol1(p))
+    assert abs(f(both) - ((1 - p) ** 2 + p * p / 3)) < 1e-14
