@@ -166,13 +166,59 @@ static bool split_product(const Op& op, Op& a, Op& b) {
 }
 
 // ---------------------------------------------------------------- composition inside a stage
+// Arithmetic of one coefficient in a sweep that follows the coefficients' structure (zero: nothing;
+// one: an add; real or imaginary: two real multiply-adds; complex: four), in real multiply-adds.
+static double coef_cost(const cd& c) {
+  if (c == 0.0) return 0.0;
+  if (c == 1.0) return 1.0;
+  if (c.imag() == 0.0 || c.real() == 0.0) return 2.0;
+  return 4.0;
+}
+
+// Cost per amplitude of one sweep of an operator (k <= 2) whose arithmetic follows the structure of its
+// coefficients, in real multiply-adds: a diagonal scales each member whose factor is not 1; a one-qubit
+// operator is its 4 x 4 superoperator on the 4 members of a group; a two-qubit unitary is U A U^dagger
+// on the 4 x 4 block A (each entry of U is used 8 times per 16 members); a two-qubit channel is its
+// 16 x 16 superoperator, whose coefficients are read from shared memory for every group.  `branch` is
+// the cost of examining one coefficient's structure (once per term and group).
+static double sweep_cost(const Op& op, double branch) {
+  const int d = 1 << op.k, D = d * d;
+  double c = 0.0;
+  if (is_diag(op)) {
+    for (int s = 0; s < D; s++) {
+      const int r = s & (d - 1), cc = s >> op.k;
+      const cd f = op.unitary ? (r == cc ? cd(1.0) : op.m[r * d + r] * std::conj(op.m[cc * d + cc])) : op.m[(size_t)s * D + s];
+      c += f == 1.0 ? 0.0 : (f == 0.0 ? 1.0 : coef_cost(f)) + branch;
+    }
+    return c / D;
+  }
+  if (op.k == 2 && op.unitary) {
+    for (const cd& u : op.m) c += coef_cost(u) + branch;
+    return 8.0 * c / D;
+  }
+  const std::vector<cd> S = op.unitary ? superop_from_unitary(op.k, op.m.data()) : op.m;
+  for (const cd& x : S) c += coef_cost(x) + (x == 0.0 ? branch : 2.0 * branch);
+  return c / D;
+}
+
 // The stage's operators are merged into composites on at most two qubits, in FP64.  Open
 // composites are kept on pairwise disjoint qubit sets; an operator merges with the composites it
 // touches when their qubits and its own number at most two, otherwise it first emits them, so
-// every qubit sees its operators in program order.  A merge that would build a dense two-qubit
-// superoperator out of cheaper pieces is refused: applied in shared memory it costs 16 complex
-// MACs and 16 coefficient loads per amplitude, more than the pieces.
-static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vector<int>& idx) {
+// every qubit sees its operators in program order.
+// Complex64 (FP32 arithmetic, where multiply-adds are cheap and every sweep costs shared-memory
+// traffic and addressing): a merge is refused only when it would build a dense two-qubit
+// superoperator out of cheaper pieces (16 complex MACs and 16 coefficient loads per amplitude).
+// FP64 and float-float (where arithmetic dominates: FP64 runs at 1/58 of the FP32 rate on this GPU,
+// and a float-float multiply-add takes about 15 FP32 instructions): the sweeps follow the
+// coefficients' zero/one/real/imaginary structure, and a merge is taken only when the composite's
+// structured arithmetic does not exceed that of its pieces plus the cost of the sweep it saves.
+static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vector<int>& idx, int prec) {
+  const bool structured = prec != VQD_F32;
+  // in real multiply-adds of the precision: a float-float one is about 15 FP32 instructions, an FP64 one
+  // occupies the FP64 pipe for about as long as 30 FP32 instructions; a sweep's shared-memory traffic and
+  // addressing take about 5 FP32 instructions per amplitude, a coefficient test about 2
+  const double sweep_saved = prec == VQD_F64 ? 0.15 : 0.3;
+  const double branch = prec == VQD_F64 ? 0.07 : 0.13;
   std::vector<Op> out, open;
   for (int i : idx) {
     const Op& op = ops[i];
@@ -195,12 +241,15 @@ static std::vector<Op> compose_stage(const std::vector<Op>& ops, const std::vect
     if (nu <= 2 && !hit.empty()) {
       Op c = open[hit[0]];
       bool dense_in = is_dense2(c) || is_dense2(op);
+      double parts = structured ? sweep_cost(c, branch) + sweep_cost(op, branch) : 0.0;
       for (size_t h = 1; h < hit.size(); h++) {
         dense_in = dense_in || is_dense2(open[hit[h]]);
+        if (structured) parts += sweep_cost(open[hit[h]], branch) + sweep_saved;
         c = compose(c, open[hit[h]]);  // disjoint composites commute
       }
       c = compose(c, op);
-      if (!(is_dense2(c) && !dense_in)) {
+      const bool take = structured ? sweep_cost(c, branch) <= parts + sweep_saved : !(is_dense2(c) && !dense_in);
+      if (take) {
         for (int h = (int)hit.size() - 1; h >= 0; h--) open.erase(open.begin() + hit[h]);
         open.push_back(std::move(c));
         merged = true;
@@ -244,16 +293,16 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
 }
 
 static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::vector<int>& idx, uint32_t qmask,
-                        int n, int L, bool whole) {
+                        int n, int L, bool whole, int prec) {
   // Blocks, members and their coefficients first: a stage whose coefficients overflow the shared
   // memory budget is split in two (each half is a valid stage on the same tile).
-  const std::vector<Op> comp = compose_stage(ops, idx);
+  const std::vector<Op> comp = compose_stage(ops, idx, prec);
   size_t ncoef = 0;
   for (const Op& o : comp) ncoef += is_diag(o) ? (o.k == 1 ? 4 : 16) : (o.k == 1 ? 16 : (o.unitary ? 16 : 256));
   if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap) && idx.size() > 1) {
     std::vector<int> a(idx.begin(), idx.begin() + idx.size() / 2), b(idx.begin() + idx.size() / 2, idx.end());
-    build_stage(plan, ops, a, qmask, n, L, whole);
-    build_stage(plan, ops, b, qmask, n, L, whole);
+    build_stage(plan, ops, a, qmask, n, L, whole, prec);
+    build_stage(plan, ops, b, qmask, n, L, whole, prec);
     return;
   }
   StageDesc sd;
@@ -305,6 +354,7 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
     tb.op_end = (int)plan.ops.size();
     plan.blocks.push_back(tb);
   }
+  while (plan.flag.size() < plan.coef.size()) plan.flag.push_back((uint8_t)flag_of(plan.coef[plan.flag.size()]));
   sd.block_end = (int)plan.blocks.size();
   sd.coef_end = (int)plan.coef.size();
   sd.op_end = (int)plan.ops.size();
@@ -338,7 +388,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
   if (2 * n <= budget) {  // the whole state is one tile: one stage holds every operator
     std::vector<int> all(ops.size());
     for (size_t i = 0; i < ops.size(); i++) all[i] = (int)i;
-    build_stage(plan, ops, all, (1u << n) - 1, n, L, true);
+    build_stage(plan, ops, all, (1u << n) - 1, n, L, true, prec);
     return plan;
   }
   const uint32_t full = (1u << n) - 1;
@@ -373,7 +423,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
         break;
       }
     }
-    build_stage(plan, ops, stage, q, n, L, false);
+    build_stage(plan, ops, stage, q, n, L, false, prec);
     std::vector<int> next;
     next.reserve(deferred.size() + remaining.size() - i);
     next.insert(next.end(), deferred.begin(), deferred.end());
@@ -412,6 +462,7 @@ BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int
     }
     bp.all.ops.insert(bp.all.ops.end(), p.ops.begin(), p.ops.end());
     bp.all.coef.insert(bp.all.coef.end(), p.coef.begin(), p.coef.end());
+    bp.all.flag.insert(bp.all.flag.end(), p.flag.begin(), p.flag.end());
     bp.all.max_bits = std::max(bp.all.max_bits, p.max_bits);
     bi.stage_end = (int)bp.all.stages.size();
     bi.cost = std::ldexp(1.0, 2 * n[i]) * std::max<size_t>(1, p.stages.size());
@@ -568,18 +619,41 @@ __device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Structured arithmetic (coefficient flags, see compose_stage) for FP64 and float-float; complex64
+// keeps straight-line FMAs.
+template <class T> struct Structured { static constexpr bool value = true; };
+template <> struct Structured<float> { static constexpr bool value = false; };
+
+template <class T>
+__device__ __forceinline__ void mac_s(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
+  if (Structured<T>::value) cmac_flag<T>(acc, c, fl, x);
+  else cmac<T>(acc, c, x);
+}
+template <class T>
+__device__ __forceinline__ cx<T> scale_s(cx<T> x, const cx<T>& f, int fl) {
+  if (Structured<T>::value) {
+    cscale_flag<T>(x, f, fl);
+    return x;
+  }
+  return cmul<T>(x, f);
+}
+
 // ---- one operator, one sweep over the tile.  Each kind has its own loop with the operator's
 // coefficients in registers (loaded once per sweep from shared memory); member s of a group is
 // r | c << k over the operator's tile bits.  The XOR swizzle is linear: sw(base | off) =
 // sw(base) ^ sw(off), so a member address costs one XOR.
 template <class T, bool DIAG>
 __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
-                                       const cx<T>* __restrict__ c, uint32_t skip) {
+                                       const cx<T>* __restrict__ c, const uint8_t* __restrict__ fl, uint32_t skip) {
   const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
   const uint32_t ng = 1u << (nbits - 2);
   cx<T> S[DIAG ? 4 : 16];
+  int F[DIAG ? 4 : 16];
 #pragma unroll
-  for (int i = 0; i < (DIAG ? 4 : 16); i++) S[i] = c[i];
+  for (int i = 0; i < (DIAG ? 4 : 16); i++) {
+    S[i] = c[i];
+    F[i] = Structured<T>::value ? (int)fl[i] : FL_CPLX;
+  }
   const Inserter<2> ins(B.lsorted);
   #pragma unroll 2
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
@@ -592,7 +666,7 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
         if (!(skip >> t & 1u)) x[t] = sm[a[t]];
 #pragma unroll
       for (int t = 0; t < 4; t++)
-        if (!(skip >> t & 1u)) sm[a[t]] = cmul<T>(x[t], S[t]);
+        if (!(skip >> t & 1u)) sm[a[t]] = scale_s<T>(x[t], S[t], F[t]);
     } else {
 #pragma unroll
       for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
@@ -601,7 +675,7 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
         cx<T> y;
         y.x = 0; y.y = 0;
 #pragma unroll
-        for (int u = 0; u < 4; u++) cmac<T>(y, S[t * 4 + u], x[u]);
+        for (int u = 0; u < 4; u++) mac_s<T>(y, S[t * 4 + u], F[t * 4 + u], x[u]);
         sm[a[t]] = y;
       }
     }
@@ -611,7 +685,7 @@ __device__ __forceinline__ void sweep1(cx<T>* __restrict__ sm, int nbits, const 
 // kind: BK_DIAG2, BK_UNI2 (U A U^dagger on the 4x4 block A[r][c] = member r | c << 2) or BK_SUP2
 template <class T, int KIND>
 __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const TileBlock& B,
-                                       const cx<T>* __restrict__ c, uint32_t skip) {
+                                       const cx<T>* __restrict__ c, const uint8_t* __restrict__ fl, uint32_t skip) {
   uint32_t soff[16];
 #pragma unroll
   for (int s = 0; s < 16; s++) {
@@ -623,9 +697,13 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
   }
   const uint32_t ng = 1u << (nbits - 4);
   cx<T> u[KIND == BK_SUP2 ? 1 : 16];
+  int F[KIND == BK_SUP2 ? 1 : 16];
   if (KIND != BK_SUP2) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) u[i] = c[i];
+    for (int i = 0; i < 16; i++) {
+      u[i] = c[i];
+      F[i] = Structured<T>::value ? (int)fl[i] : FL_CPLX;
+    }
   }
   const Inserter<4> ins(B.lsorted);
   if constexpr (KIND == BK_DIAG2) {  // members with factor 1 are left as they are
@@ -634,7 +712,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
       const uint32_t b = sw<T>(ins(g));
 #pragma unroll
       for (int s = 0; s < 16; s++)
-        if (!(skip >> s & 1u)) sm[b ^ soff[s]] = cmul<T>(sm[b ^ soff[s]], u[s]);
+        if (!(skip >> s & 1u)) sm[b ^ soff[s]] = scale_s<T>(sm[b ^ soff[s]], u[s], F[s]);
     }
   } else {
   #pragma unroll 1
@@ -651,7 +729,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
         for (int r = 0; r < 4; r++) {
           t[r].x = 0; t[r].y = 0;
 #pragma unroll
-          for (int m = 0; m < 4; m++) cmac<T>(t[r], u[r * 4 + m], x[m | (cc << 2)]);
+          for (int m = 0; m < 4; m++) mac_s<T>(t[r], u[r * 4 + m], F[r * 4 + m], x[m | (cc << 2)]);
         }
 #pragma unroll
         for (int r = 0; r < 4; r++) x[r | (cc << 2)] = t[r];
@@ -666,7 +744,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
           for (int m = 0; m < 4; m++) {
             cx<T> uc = u[cc * 4 + m];
             uc.y = -uc.y;
-            cmac<T>(t[cc], uc, x[r | (m << 2)]);
+            mac_s<T>(t[cc], uc, F[cc * 4 + m], x[r | (m << 2)]);
           }
         }
 #pragma unroll
@@ -678,7 +756,7 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
         cx<T> y;
         y.x = 0; y.y = 0;
 #pragma unroll
-        for (int j = 0; j < 16; j++) cmac<T>(y, c[i * 16 + j], x[j]);
+        for (int j = 0; j < 16; j++) mac_s<T>(y, c[i * 16 + j], Structured<T>::value ? (int)fl[i * 16 + j] : FL_CPLX, x[j]);
         uint32_t o = 0;
 #pragma unroll
         for (int j = 0; j < 4; j++)
@@ -692,29 +770,35 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
 
 // Apply the stage's operators (one block each) to the tile, one sweep per operator.
 template <class T>
-__device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm, int nbits,
+__device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
+                                            const uint8_t* __restrict__ fsm, int nbits,
                                             const TileBlock* __restrict__ blocks, int bb, int be,
                                             const BlockOp* __restrict__ sops, int op0) {
   for (int b = bb; b < be; b++) {
     const TileBlock B = blocks[b];
     const BlockOp bo = sops[B.op_begin - op0];
     const cx<T>* c = csm + bo.coef;
+    const uint8_t* f = fsm + bo.coef;
     switch (bo.kind) {
-      case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c, bo.skip); break;
-      case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c, 0u); break;
-      case BK_DIAG2: sweep2<T, BK_DIAG2>(sm, nbits, B, c, bo.skip); break;
-      case BK_UNI2: sweep2<T, BK_UNI2>(sm, nbits, B, c, 0u); break;
-      default: sweep2<T, BK_SUP2>(sm, nbits, B, c, 0u); break;
+      case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c, f, bo.skip); break;
+      case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c, f, 0u); break;
+      case BK_DIAG2: sweep2<T, BK_DIAG2>(sm, nbits, B, c, f, bo.skip); break;
+      case BK_UNI2: sweep2<T, BK_UNI2>(sm, nbits, B, c, f, 0u); break;
+      default: sweep2<T, BK_SUP2>(sm, nbits, B, c, f, 0u); break;
     }
     __syncthreads();
   }
 }
 
 template <class T>
-__device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>* __restrict__ coef, int cb, int ce,
+__device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>* __restrict__ coef,
+                                            uint8_t* __restrict__ fsm, const uint8_t* __restrict__ flag, int cb, int ce,
                                             BlockOp* __restrict__ sops, const BlockOp* __restrict__ bops, int ob,
                                             int oe) {
-  for (int i = threadIdx.x; i < ce - cb; i += kThreads) csm[i] = coef[cb + i];
+  for (int i = threadIdx.x; i < ce - cb; i += kThreads) {
+    csm[i] = coef[cb + i];
+    fsm[i] = flag[cb + i];
+  }
   for (int i = threadIdx.x; i < oe - ob; i += kThreads) sops[i] = bops[ob + i];
 }
 
@@ -722,7 +806,8 @@ template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __restrict__ st, const StageDesc S,
                                                                        const TileBlock* __restrict__ blocks,
                                                                        const BlockOp* __restrict__ bops,
-                                                                       const cx<T>* __restrict__ coef) {
+                                                                       const cx<T>* __restrict__ coef,
+                                                                       const uint8_t* __restrict__ flag) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* csm = reinterpret_cast<cx<T>*>(smraw);
   cx<T>* sm = csm + kCoefCap;
@@ -732,14 +817,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __
   if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
   const int nbits = S.nbits, nrest = S.nrest, bb = S.block_begin, be = S.block_end;
   BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << nbits));
-  stage_coefs<T>(csm, coef, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
+  uint8_t* fsm = reinterpret_cast<uint8_t*>(sops + kOpCap);
+  stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
   __syncthreads();
   const uint64_t ntiles = 1ull << nrest;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = deposit(t, s_rest, nrest);
     tile_load_async<T>(st, sm, base, s_bits, nbits);
     __syncthreads();
-    tile_blocks<T>(sm, csm, nbits, blocks, bb, be, sops, S.op_begin);
+    tile_blocks<T>(sm, csm, fsm, nbits, blocks, bb, be, sops, S.op_begin);
     tile_io<T, false>(st, sm, base, s_bits, nbits);
     __syncthreads();
   }
@@ -755,12 +841,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __r
                                                                       const TileBlock* __restrict__ blocks,
                                                                       const BlockOp* __restrict__ bops,
                                                                       const cx<T>* __restrict__ coef,
+                                                                      const uint8_t* __restrict__ flag,
                                                                       const WaveItem* __restrict__ items, int nitems,
                                                                       int* __restrict__ counter, int max_bits) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* csm = reinterpret_cast<cx<T>*>(smraw);
   cx<T>* sm = csm + kCoefCap;
   BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << max_bits));
+  uint8_t* fsm = reinterpret_cast<uint8_t*>(sops + kOpCap);
   __shared__ int item;
   __shared__ int s_bits[kMaxTileBits];
   __shared__ int s_rest[2 * VQD_MAX_QUBITS];
@@ -776,7 +864,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __r
     if (W.stage != cur) {
       if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = S.bits[threadIdx.x];
       if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
-      stage_coefs<T>(csm, coef, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
+      stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
       __syncthreads();
       cur = W.stage;
     }
@@ -786,7 +874,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __r
       const uint64_t base = deposit(t, s_rest, nrest);
       tile_load_async<T>(st, sm, base, s_bits, nbits);
       __syncthreads();
-      tile_blocks<T>(sm, csm, nbits, blocks, S.block_begin, S.block_end, sops, op0);
+      tile_blocks<T>(sm, csm, fsm, nbits, blocks, S.block_begin, S.block_end, sops, op0);
       tile_io<T, false>(st, sm, base, s_bits, nbits);
       __syncthreads();
     }
@@ -819,7 +907,7 @@ static void check(cudaError_t e, const char* what) {
 }
 
 void fused_cache_free(FusedCache& c) {
-  for (void* p : {c.d_blocks, c.d_ops, c.d_coef, c.d_stages, c.d_inst, c.d_items, (void*)c.d_counter})
+  for (void* p : {c.d_blocks, c.d_ops, c.d_coef, c.d_flag, c.d_stages, c.d_inst, c.d_items, (void*)c.d_counter})
     if (p) cudaFree(p);
   c = FusedCache();
 }
@@ -836,6 +924,7 @@ static void upload_common(FusedCache& c, const FusedPlan& p, cudaStream_t s) {
   grow(&c.d_blocks, &c.blocks_cap, std::max<size_t>(1, p.blocks.size()) * sizeof(TileBlock));
   grow(&c.d_ops, &c.ops_cap, std::max<size_t>(1, p.ops.size()) * sizeof(BlockOp));
   grow(&c.d_coef, &c.coef_cap, std::max<size_t>(1, cf.size()) * sizeof(cx<T>));
+  grow(&c.d_flag, &c.flag_cap, std::max<size_t>(1, p.flag.size()));
   grow(&c.d_stages, &c.stages_cap, std::max<size_t>(1, p.stages.size()) * sizeof(StageDesc));
   if (!p.blocks.empty())
     check(cudaMemcpyAsync(c.d_blocks, p.blocks.data(), p.blocks.size() * sizeof(TileBlock), cudaMemcpyHostToDevice, s),
@@ -844,6 +933,8 @@ static void upload_common(FusedCache& c, const FusedPlan& p, cudaStream_t s) {
     check(cudaMemcpyAsync(c.d_ops, p.ops.data(), p.ops.size() * sizeof(BlockOp), cudaMemcpyHostToDevice, s), "upload ops");
   if (!cf.empty())
     check(cudaMemcpyAsync(c.d_coef, cf.data(), cf.size() * sizeof(cx<T>), cudaMemcpyHostToDevice, s), "upload coefficients");
+  if (!p.flag.empty())
+    check(cudaMemcpyAsync(c.d_flag, p.flag.data(), p.flag.size(), cudaMemcpyHostToDevice, s), "upload coefficient flags");
   if (!p.stages.empty())
     check(cudaMemcpyAsync(c.d_stages, p.stages.data(), p.stages.size() * sizeof(StageDesc), cudaMemcpyHostToDevice, s),
           "upload stages");
@@ -866,7 +957,7 @@ static unsigned persistent_grid(K kernel, size_t smem, uint64_t work) {
 
 template <class T>
 static size_t stage_smem(int nbits) {
-  return ((size_t)kCoefCap + ((size_t)1 << nbits)) * sizeof(cx<T>) + (size_t)kOpCap * sizeof(BlockOp);
+  return ((size_t)kCoefCap + ((size_t)1 << nbits)) * sizeof(cx<T>) + (size_t)kOpCap * sizeof(BlockOp) + (size_t)kCoefCap;
 }
 
 template <class T>
@@ -877,7 +968,7 @@ static cudaError_t stage_t(FusedCache& c, const FusedPlan& p, int stage, void* s
   if (e != cudaSuccess) return e;
   unsigned grid = persistent_grid(k_stage<T>, smem, 1ull << S.nrest);
   k_stage<T><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops,
-                                     (const cx<T>*)c.d_coef);
+                                     (const cx<T>*)c.d_coef, (const uint8_t*)c.d_flag);
   return cudaGetLastError();
 }
 
@@ -916,7 +1007,7 @@ static cudaError_t batch_t(FusedCache& c, const BatchPlan& p, void* base, cudaSt
     unsigned grid = persistent_grid(k_wave<T>, smem, (uint64_t)cnt);
     k_wave<T><<<grid, 256, smem, s>>>((cx<T>*)base, (const BatchInst*)c.d_inst, (const StageDesc*)c.d_stages,
                                       (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops, (const cx<T>*)c.d_coef,
-                                      (const WaveItem*)c.d_items + b, cnt, c.d_counter + w, mb);
+                                      (const uint8_t*)c.d_flag, (const WaveItem*)c.d_items + b, cnt, c.d_counter + w, mb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

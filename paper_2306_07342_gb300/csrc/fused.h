@@ -48,6 +48,7 @@ struct FusedPlan {
   std::vector<TileBlock> blocks;
   std::vector<BlockOp> ops;
   std::vector<cd> coef;
+  std::vector<uint8_t> flag;  // structure of each coefficient (FL_* of numeric.h), used by FP64 and float-float
   int max_bits = 0;
 };
 
@@ -93,6 +94,8 @@ struct FusedCache {
   size_t ops_cap = 0;
   void* d_coef = nullptr;
   size_t coef_cap = 0;
+  void* d_flag = nullptr;
+  size_t flag_cap = 0;
   void* d_stages = nullptr;
   size_t stages_cap = 0;
   void* d_inst = nullptr;

@@ -25,20 +25,6 @@
 namespace vqd {
 namespace dev {
 
-enum { FL_ZERO = 0, FL_ONE = 1, FL_REAL = 2, FL_IMAG = 3, FL_CPLX = 4 };
-
-template <class T>
-__device__ __forceinline__ void cmac_flag(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
-  if (fl == FL_ZERO) return;
-  if (fl == FL_ONE) { acc.x += x.x; acc.y += x.y; return; }
-  if (fl == FL_REAL) { acc.x = fma(c.x, x.x, acc.x); acc.y = fma(c.x, x.y, acc.y); return; }
-  if (fl == FL_IMAG) { acc.x = fma(-c.y, x.y, acc.x); acc.y = fma(c.y, x.x, acc.y); return; }
-  acc.x = fma(c.x, x.x, acc.x);
-  acc.x = fma(-c.y, x.y, acc.x);
-  acc.y = fma(c.x, x.y, acc.y);
-  acc.y = fma(c.y, x.x, acc.y);
-}
-
 template <class T>
 __device__ __forceinline__ void cmac(cx<T>& acc, const cx<T>& c, const cx<T>& x) {
   acc.x = fma(c.x, x.x, acc.x);
@@ -391,13 +377,6 @@ static unsigned grid_for(K kernel, uint64_t work, int block = 256) {
   return (unsigned)std::max<uint64_t>(1, std::min(full, need));
 }
 
-static int flag_of(cd c) {
-  if (c == 0.0) return FL_ZERO;
-  if (c == 1.0) return FL_ONE;
-  if (c.imag() == 0.0) return FL_REAL;
-  if (c.real() == 0.0) return FL_IMAG;
-  return FL_CPLX;
-}
 
 template <class T>
 static cx<T> to_cx(cd c) {

@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <complex>
+
 namespace vqd {
 namespace dev {
 
@@ -72,11 +74,51 @@ struct __align__(16) cdf {
   df x, y;
 };
 
+// Structure of an operator coefficient, uniform across a launch (or a sweep): the structured kernels
+// branch on it so that a zero costs nothing, a one an add, and a real or imaginary coefficient two real
+// multiply-adds instead of four.
+enum { FL_ZERO = 0, FL_ONE = 1, FL_REAL = 2, FL_IMAG = 3, FL_CPLX = 4 };
+
 template <class T> struct V2;
 template <> struct V2<float> { using t = float2; };
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<df> { using t = cdf; };
 template <class T> using cx = typename V2<T>::t;
 
+// acc += c x for a coefficient of structure fl
+template <class T>
+__device__ __forceinline__ void cmac_flag(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
+  if (fl == FL_ZERO) return;
+  if (fl == FL_ONE) { acc.x += x.x; acc.y += x.y; return; }
+  if (fl == FL_REAL) { acc.x = fma(c.x, x.x, acc.x); acc.y = fma(c.x, x.y, acc.y); return; }
+  if (fl == FL_IMAG) { acc.x = fma(-c.y, x.y, acc.x); acc.y = fma(c.y, x.x, acc.y); return; }
+  acc.x = fma(c.x, x.x, acc.x);
+  acc.x = fma(-c.y, x.y, acc.x);
+  acc.y = fma(c.x, x.y, acc.y);
+  acc.y = fma(c.y, x.x, acc.y);
+}
+
+// x <- f x for a diagonal factor of structure fl (FL_ONE leaves x as it is)
+template <class T>
+__device__ __forceinline__ void cscale_flag(cx<T>& x, const cx<T>& f, int fl) {
+  if (fl == FL_ONE) return;
+  if (fl == FL_ZERO) { x.x = T(0.0f); x.y = T(0.0f); return; }
+  if (fl == FL_REAL) { x.x = x.x * f.x; x.y = x.y * f.x; return; }
+  if (fl == FL_IMAG) { const T re = -(x.y * f.y); x.y = x.x * f.y; x.x = re; return; }
+  const T re = fma(x.x, f.x, -(x.y * f.y));
+  x.y = fma(x.x, f.y, x.y * f.x);
+  x.x = re;
+}
+
 }  // namespace dev
+
+// Host-side structure of a coefficient (FL_*), for the structured kernels.
+inline int flag_of(const std::complex<double>& c) {
+  if (c == 0.0) return dev::FL_ZERO;
+  if (c == 1.0) return dev::FL_ONE;
+  if (c.imag() == 0.0) return dev::FL_REAL;
+  if (c.real() == 0.0) return dev::FL_IMAG;
+  return dev::FL_CPLX;
+}
+
 }  // namespace vqd

@@ -66,7 +66,8 @@ def test_grid14_first_layer_full_size_vs_oracle(vqd, grid14_first_layer, p, path
         err = max(err, float(np.abs(got[r0:r0 + 1024] - want[r0:r0 + 1024]).max()))
     assert err < tol, (p, path, err)
     assert abs(tr - np.trace(want)) < tol
-    assert abs(pur - float(np.sum(np.abs(want) ** 2))) < 1e-9
+    # purity sums 2^28 squared moduli: complex64 rounding (relative 2^-24 per amplitude) moves it by ~1e-7
+    assert abs(pur - float(np.sum(np.abs(want) ** 2))) < (1e-5 if p == "f32" else 1e-11)
 
 
 @pytest.fixture(scope="module")
