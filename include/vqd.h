@@ -215,6 +215,29 @@ int vqd_run_program(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, int
  * this library's addition. */
 int vqd_run_batch(vqd_t ctx, const int64_t* offsets, const vqd_native_op* ops, int fuse_qubits, unsigned flags);
 
+/* Tensor-core form of the fused path (Sec. 2's general Kraus map in its superoperator form, applied as a
+ * dense matrix product).  The program's native ops are grouped, in program order with a commuting
+ * lookahead (operators that share a qubit keep their order), into blocks on at most k qubits (k = 4, 5 or
+ * 6; a block with fewer qubits is padded with identity qubits).  Each block is composed on the GPU in
+ * FP64 into one 4^k x 4^k superoperator S, which is split into limbs and applied to every group of 4^k
+ * amplitudes as a real GEMM on the tensor cores (tcgen05.mma with TMEM accumulators, TMA tile loads),
+ * accumulating in FP32:
+ *   VQD_TC_3XTF32: operands split as hi + lo TF32 parts, products lo*hi + hi*lo + hi*hi;
+ *   VQD_TC_BF16X3: operands split into three BF16 parts, the six products of combined order <= 4.
+ * Complex64 contexts only (VQD_ENOTSUP otherwise); needs n >= k.  The state is written out of place to a
+ * second buffer of the context's state size (allocated on first use) and copied back at the end when an
+ * odd number of blocks ran, so vqd_state_ptr stays valid.  The call synchronises the stream at the end
+ * and returns VQD_EDEVICE if a kernel wait expired.  Results agree with vqd_run_program up to the FP32
+ * rounding of the split products. */
+#define VQD_TC_3XTF32 0
+#define VQD_TC_BF16X3 1
+int vqd_run_program_tc(vqd_t ctx, int inst, int nops, const vqd_native_op* ops, int k, int scheme, unsigned flags);
+
+/* Blocks of the tensor-core form for an n-qubit program, without running it (host only):
+ * info[0] = blocks (one GEMM pass over the state each), info[1] = original operators,
+ * info[2] = the largest number of operators in one block. */
+int vqd_tc_plan_info(int n, int nops, const vqd_native_op* ops, int k, unsigned flags, int64_t* info);
+
 /* ------------------------------------------------------------------------------------------
  * Device compiler (host only, no GPU needed)
  * ---------------------------------------------------------------------------------------- */

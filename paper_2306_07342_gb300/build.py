@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvqd.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["kernels.cu", "fused.cu", "trajectories.cu", "devcomp.cpp", "abi.cpp"]
-HEADERS = ["kernels.h", "fused.h", "vqd_internal.h"]
+SOURCES = ["kernels.cu", "fused.cu", "tcgemm.cu", "trajectories.cu", "devcomp.cpp", "abi.cpp"]
+HEADERS = ["kernels.h", "fused.h", "tcgemm.h", "numeric.h", "vqd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -13,6 +13,7 @@
 
 #include "fused.h"
 #include "kernels.h"
+#include "tcgemm.h"
 #include "vqd_internal.h"
 
 using namespace vqd;
@@ -24,8 +25,10 @@ thread_local std::string g_err;
 struct KClass {
   const char* name;
 };
-enum StatClass { SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2, SC_FUSED, SC_BATCH, SC_REDUCE, SC_INIT, SC_COUNT };
-const char* kStatNames[SC_COUNT] = {"elem", "sup1", "uni2", "sup2", "fused_stage", "batch", "reduce", "init"};
+enum StatClass { SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2, SC_FUSED, SC_BATCH, SC_REDUCE, SC_INIT, SC_TC_COMPOSE, SC_TC_GEMM,
+                 SC_COUNT };
+const char* kStatNames[SC_COUNT] = {"elem",   "sup1", "uni2",       "sup2",   "fused_stage",
+                                    "batch",  "reduce", "init", "tc_compose", "tc_gemm"};
 
 struct Stat {
   int64_t launches = 0;
@@ -70,6 +73,14 @@ struct vqd_ctx {
   std::vector<size_t> batch_nops;
   int64_t batch_waves = 0;
   TileShape shape;           // tile shape of the fused and batched paths (defaults per precision)
+  // Tensor-core path: second state buffer (out-of-place GEMMs), composition buffer, tiled limbs, error flag.
+  void* tc_alt = nullptr;
+  size_t tc_alt_cap = 0;
+  void* tc_S = nullptr;
+  size_t tc_S_cap = 0;
+  void* tc_R = nullptr;
+  size_t tc_R_cap = 0;
+  int* tc_err = nullptr;
 
   char* ptr(int inst) { return base + off[inst]; }
   size_t bytes(int inst) const { return vqd_state_bytes(n[inst], prec); }
@@ -182,6 +193,8 @@ static void free_ctx(vqd_ctx* c) {
   fused_cache_free(c->fused);
   if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
   fused_cache_free(c->batch);
+  for (void* q : {c->tc_alt, c->tc_S, c->tc_R, (void*)c->tc_err})
+    if (q) cudaFree(q);
   if (c->owns && c->base) cudaFree(c->base);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_out) cudaFree(c->d_out);
@@ -501,6 +514,98 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
   } else {
     account(c->batch_waves, [&] { return launch_batch(c->batch, plan, c->prec, c->base, c->stream); });
   }
+  API_END(c)
+}
+
+// ---------------------------------------------------------------- tensor-core form of the fused path
+static void grow_dev(void** p, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap) return;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cuda_check(cudaMalloc(p, need), what);
+  *cap = need;
+}
+
+// Compile a native list for an n-qubit program without a context (host-only planning calls).
+static std::vector<Op> compile_for(int n, int nops, const vqd_native_op* ops, unsigned flags) {
+  if (n < 1 || n > VQD_MAX_QUBITS || nops < 0 || (nops > 0 && !ops)) throw Error(VQD_EINVAL, "bad argument");
+  std::vector<Op> list;
+  list.reserve(nops);
+  for (int i = 0; i < nops; i++) {
+    int ar = native_arity(ops[i].code);
+    if (ar < 1) throw Error(VQD_EINVAL, "unknown native op code");
+    for (int j = 0; j < ar; j++)
+      if (ops[i].q[j] < 0 || ops[i].q[j] >= n || (j == 1 && ops[i].q[1] == ops[i].q[0]))
+        throw Error(VQD_EINVAL, "bad target qubit");
+    list.push_back(compile_native(ops[i], flags));
+  }
+  return list;
+}
+
+int vqd_tc_plan_info(int n, int nops, const vqd_native_op* ops, int k, unsigned flags, int64_t* info) {
+  API_BEGIN
+  if (!info) throw Error(VQD_EINVAL, "NULL info");
+  if (k < 4 || k > 6 || k > n) throw Error(VQD_EINVAL, "k must be 4, 5 or 6 and at most n");
+  std::vector<Op> list = compile_for(n, nops, ops, flags);
+  std::vector<TcBlock> blocks = plan_tc_blocks(list, n, k);
+  info[0] = (int64_t)blocks.size();
+  info[1] = nops;
+  info[2] = 0;
+  for (const TcBlock& b : blocks) info[2] = std::max<int64_t>(info[2], (int64_t)b.ops.size());
+  API_END(nullptr)
+}
+
+int vqd_run_program_tc(vqd_t c, int inst, int nops, const vqd_native_op* ops, int k, int scheme, unsigned flags) {
+  API_BEGIN
+  need_ctx(c);
+  need_inst(c, inst);
+  if (c->prec != VQD_F32) throw Error(VQD_ENOTSUP, "the tensor-core path needs a complex64 (VQD_F32) context");
+  const int n = c->n[inst];
+  if (k < 4 || k > 6 || k > n) throw Error(VQD_EINVAL, "k must be 4, 5 or 6 and at most the qubit count");
+  if (scheme != VQD_TC_3XTF32 && scheme != VQD_TC_BF16X3) throw Error(VQD_EINVAL, "scheme must be VQD_TC_3XTF32 or VQD_TC_BF16X3");
+  std::vector<Op> list = compile_list(c, inst, nops, ops, flags);
+  std::vector<TcBlock> blocks = plan_tc_blocks(list, n, k);
+  const size_t bytes = c->bytes(inst);
+  grow_dev(&c->tc_alt, &c->tc_alt_cap, bytes, "tensor-core second state buffer");
+  grow_dev(&c->tc_S, &c->tc_S_cap, tc_compose_bytes(k), "tensor-core composition buffer");
+  grow_dev(&c->tc_R, &c->tc_R_cap, tc_r_bytes(k, scheme), "tensor-core operand limbs");
+  if (!c->tc_err) cuda_check(cudaMalloc((void**)&c->tc_err, sizeof(int)), "tensor-core error flag");
+  cuda_check(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream), "clear error flag");
+  char* cur = c->ptr(inst);
+  char* other = (char*)c->tc_alt;
+  for (const TcBlock& b : blocks) {
+    // the block's qubits, ascending, padded with unused qubits up to k
+    int q[6], nq = 0;
+    for (int x = 0; x < n && nq < k; x++)
+      if (b.qmask >> x & 1) q[nq++] = x;
+    for (int x = 0; x < n && nq < k; x++)
+      if (!(b.qmask >> x & 1)) q[nq++] = x;
+    std::sort(q, q + k);
+    int local[VQD_MAX_QUBITS];
+    for (int j = 0; j < k; j++) local[q[j]] = j;
+    // FP64 composition: the block's operators applied in order to the identity superoperator, as passes
+    // of the plain FP64 kernels over the 2k-qubit composition layout
+    timed(c, SC_TC_COMPOSE, 0.0, 0.0, (int64_t)b.ops.size() + 2, [&] {
+      cudaError_t e = tc_compose_init(c->tc_S, k, c->stream);
+      for (size_t i = 0; i < b.ops.size() && e == cudaSuccess; i++) {
+        Op o = list[b.ops[i]];
+        for (int j = 0; j < o.k; j++) o.q[j] = local[o.q[j]];
+        e = launch_pass(VQD_F64, c->tc_S, 2 * k, classify(o), c->stream);
+      }
+      if (e == cudaSuccess) e = tc_build_r(c->tc_S, k, scheme, c->tc_R, c->stream);
+      return e;
+    });
+    timed(c, SC_TC_GEMM, 2.0 * (double)bytes, b.weight * std::ldexp(1.0, 2 * n), 1,
+          [&] { return tc_apply(cur, other, n, k, q, scheme, c->tc_R, c->tc_err, c->stream); });
+    std::swap(cur, other);
+  }
+  if (cur != c->ptr(inst))
+    cuda_check(cudaMemcpyAsync(c->ptr(inst), cur, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy back");
+  int herr = 0;
+  cuda_check(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error flag");
+  cuda_check(cudaStreamSynchronize(c->stream), "tensor-core path");
+  if (herr) throw Error(VQD_EDEVICE, "tensor-core kernel: a bounded wait expired (copy or tensor-core operation did not complete)");
   API_END(c)
 }
 

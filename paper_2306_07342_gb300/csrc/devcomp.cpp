@@ -328,9 +328,10 @@ std::vector<cd> superop_from_kraus(int k, int nK, const cd* K) {
   return sup_kraus(k, ks);
 }
 
-// A diagonal unitary has |U_rr| = 1, so the factors U_rr conj(U_rr) of the members whose row and column
-// index agree are exactly 1; they are set to 1 rather than to the rounded product, which lets the
-// elementwise passes leave those members untouched.
+// A diagonal unitary has |U_rr| = 1, so its superoperator's factors U_rr conj(U_cc) are exactly 1
+// whenever U_rr and U_cc are the same number (always for r = c; for r != c in phases such as ZZ or CPh);
+// they are set to 1 rather than to the rounded product, which lets the elementwise passes leave those
+// members untouched.
 bool is_diagonal_matrix(int d, const cd* M) {
   for (int i = 0; i < d; i++)
     for (int j = 0; j < d; j++)
@@ -342,10 +343,11 @@ std::vector<cd> superop_from_unitary(int k, const cd* U) {
   int d = 1 << k;
   std::vector<cd> S = sup_kraus(k, {Mat(U, U + d * d)});
   if (is_diagonal_matrix(d, U))
-    for (int r = 0; r < d; r++) {
-      const int s = r | (r << k);
-      S[(size_t)s * d * d + s] = 1.0;
-    }
+    for (int r = 0; r < d; r++)
+      for (int c = 0; c < d; c++) {
+        const int s = r | (c << k);
+        S[(size_t)s * d * d + s] = diag_unitary_factor(U[r * d + r], U[c * d + c]);
+      }
   return S;
 }
 
@@ -423,12 +425,11 @@ Pass classify(const Op& op) {
     for (int i = 0; i < d; i++)
       for (int j = 0; j < d; j++)
         if (i != j && op.m[i * d + j] != 0.0) diag = false;
-    if (diag) {  // factor for amplitude (r, c): U[r][r] conj(U[c][c]), exactly 1 for r == c
+    if (diag) {  // factor for amplitude (r, c): U[r][r] conj(U[c][c]), exactly 1 when the entries are equal
       p.kind = KK_ELEM;
       p.coef.resize(D);
       for (int r = 0; r < d; r++)
-        for (int c = 0; c < d; c++)
-          p.coef[r | (c << op.k)] = r == c ? cd(1.0) : op.m[r * d + r] * std::conj(op.m[c * d + c]);
+        for (int c = 0; c < d; c++) p.coef[r | (c << op.k)] = diag_unitary_factor(op.m[r * d + r], op.m[c * d + c]);
       return p;
     }
     if (op.k == 1) {

@@ -187,7 +187,7 @@ static double sweep_cost(const Op& op, double branch) {
   if (is_diag(op)) {
     for (int s = 0; s < D; s++) {
       const int r = s & (d - 1), cc = s >> op.k;
-      const cd f = op.unitary ? (r == cc ? cd(1.0) : op.m[r * d + r] * std::conj(op.m[cc * d + cc])) : op.m[(size_t)s * D + s];
+      const cd f = op.unitary ? diag_unitary_factor(op.m[r * d + r], op.m[cc * d + cc]) : op.m[(size_t)s * D + s];
       c += f == 1.0 ? 0.0 : (f == 0.0 ? 1.0 : coef_cost(f)) + branch;
     }
     return c / D;
@@ -272,7 +272,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
     if (is_diag(op)) {  // factor of member t = r | c << 1
       for (int t = 0; t < 4; t++) {
         const int r = t & 1, c = t >> 1;
-        out.push_back(op.unitary ? (r == c ? cd(1.0) : op.m[r * 2 + r] * std::conj(op.m[c * 2 + c])) : op.m[t * 5]);
+        out.push_back(op.unitary ? diag_unitary_factor(op.m[r * 2 + r], op.m[c * 2 + c]) : op.m[t * 5]);
       }
       return on_b ? BK_DIAG_B : BK_DIAG_A;
     }
@@ -284,7 +284,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
   if (is_diag(op)) {  // factor of member t = r | c << 2
     for (int t = 0; t < 16; t++) {
       const int r = t & 3, c = t >> 2;
-      out.push_back(op.unitary ? (r == c ? cd(1.0) : m[r * 4 + r] * std::conj(m[c * 4 + c])) : m[t * 17]);
+      out.push_back(op.unitary ? diag_unitary_factor(m[r * 4 + r], m[c * 4 + c]) : m[t * 17]);
     }
     return BK_DIAG2;
   }
@@ -768,6 +768,123 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
 }  // KIND != BK_DIAG2
 }
 
+// ---- FP64 and float-float sweeps.  Their arithmetic (FP64 at 1/58 of the FP32 rate; a float-float
+// multiply-add is about 15 FP32 instructions) dwarfs a shared-memory read, so each term reads its
+// coefficient and structure flag from shared memory (a broadcast: every thread reads the same word)
+// instead of holding all of them in registers, and a two-qubit unitary U A U^dagger is applied as a
+// column pass and a row pass over 4-member vectors.  This keeps the live state to a few amplitudes per
+// thread, so that two CTAs (16 warps) fit on an SM to hide the long dependency chains.
+template <class T>
+__device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, const TileBlock& B, const cx<T>* __restrict__ c,
+                                         const uint8_t* __restrict__ fl, uint32_t skip, bool diag) {
+  const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
+  const uint32_t ng = 1u << (nbits - 2);
+  const Inserter<2> ins(B.lsorted);
+  for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
+    const uint32_t b = sw<T>(ins(g));
+    const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
+    if (diag) {
+#pragma unroll
+      for (int t = 0; t < 4; t++)
+        if (!(skip >> t & 1u)) {
+          cx<T> x = sm[a[t]];
+          cscale_flag<T>(x, c[t], fl[t]);
+          sm[a[t]] = x;
+        }
+    } else {
+      cx<T> x[4];
+#pragma unroll
+      for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
+#pragma unroll
+      for (int t = 0; t < 4; t++) {
+        cx<T> y;
+        y.x = 0; y.y = 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) cmac_flag<T>(y, c[t * 4 + u], fl[t * 4 + u], x[u]);
+        sm[a[t]] = y;
+      }
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, const TileBlock& B, const cx<T>* __restrict__ c,
+                                         const uint8_t* __restrict__ fl, uint32_t skip, int kind) {
+  uint32_t soff[16];
+#pragma unroll
+  for (int s = 0; s < 16; s++) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      if (s >> j & 1) o |= 1u << B.lbit[j];
+    soff[s] = sw<T>(o);
+  }
+  const uint32_t ng = 1u << (nbits - 4);
+  const Inserter<4> ins(B.lsorted);
+  for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
+    const uint32_t b = sw<T>(ins(g));
+    if (kind == BK_DIAG2) {
+#pragma unroll 4
+      for (int s = 0; s < 16; s++)
+        if (!(skip >> s & 1u)) {
+          cx<T> x = sm[b ^ soff[s]];
+          cscale_flag<T>(x, c[s], fl[s]);
+          sm[b ^ soff[s]] = x;
+        }
+    } else if (kind == BK_UNI2) {
+      // columns: A[:, cc] <- U A[:, cc]; then rows: A[r, :] <- A[r, :] U^dagger (A[r][cc] = member r | cc << 2)
+#pragma unroll 1
+      for (int cc = 0; cc < 4; cc++) {
+        cx<T> x[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[m | (cc << 2)]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          cx<T> t;
+          t.x = 0; t.y = 0;
+#pragma unroll
+          for (int m = 0; m < 4; m++) cmac_flag<T>(t, c[r * 4 + m], fl[r * 4 + m], x[m]);
+          sm[b ^ soff[r | (cc << 2)]] = t;
+        }
+      }
+#pragma unroll 1
+      for (int r = 0; r < 4; r++) {
+        cx<T> x[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[r | (m << 2)]];
+#pragma unroll
+        for (int cc = 0; cc < 4; cc++) {
+          cx<T> t;
+          t.x = 0; t.y = 0;
+#pragma unroll
+          for (int m = 0; m < 4; m++) {
+            cx<T> uc = c[cc * 4 + m];
+            uc.y = -uc.y;
+            cmac_flag<T>(t, uc, fl[cc * 4 + m], x[m]);
+          }
+          sm[b ^ soff[r | (cc << 2)]] = t;
+        }
+      }
+    } else {
+      cx<T> x[16];
+#pragma unroll
+      for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
+#pragma unroll 1
+      for (int i = 0; i < 16; i++) {
+        cx<T> y;
+        y.x = 0; y.y = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) cmac_flag<T>(y, c[i * 16 + j], fl[i * 16 + j], x[j]);
+        uint32_t o = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          if (i >> j & 1) o |= 1u << B.lbit[j];
+        sm[b ^ sw<T>(o)] = y;
+      }
+    }
+  }
+}
+
 // Apply the stage's operators (one block each) to the tile, one sweep per operator.
 template <class T>
 __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
@@ -779,6 +896,12 @@ __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>*
     const BlockOp bo = sops[B.op_begin - op0];
     const cx<T>* c = csm + bo.coef;
     const uint8_t* f = fsm + bo.coef;
+    if constexpr (Structured<T>::value) {
+      if (bo.kind == BK_DIAG_A || bo.kind == BK_SUP1_A) sweep1_s<T>(sm, nbits, B, c, f, bo.skip, bo.kind == BK_DIAG_A);
+      else sweep2_s<T>(sm, nbits, B, c, f, bo.skip, bo.kind);
+      __syncthreads();
+      continue;
+    }
     switch (bo.kind) {
       case BK_DIAG_A: sweep1<T, true>(sm, nbits, B, c, f, bo.skip); break;
       case BK_SUP1_A: sweep1<T, false>(sm, nbits, B, c, f, 0u); break;
@@ -803,7 +926,7 @@ __device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __restrict__ st, const StageDesc S,
+__global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const StageDesc S,
                                                                        const TileBlock* __restrict__ blocks,
                                                                        const BlockOp* __restrict__ bops,
                                                                        const cx<T>* __restrict__ coef,
@@ -835,7 +958,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_stage(cx<T>* __
 // queue; a CTA restages coefficients and operator descriptors only when its next item belongs to
 // another stage.  Items of one wave never depend on each other, so no CTA waits for another.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_wave(cx<T>* __restrict__ all,
+__global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
                                                                       const BatchInst* __restrict__ inst,
                                                                       const StageDesc* __restrict__ stages,
                                                                       const TileBlock* __restrict__ blocks,

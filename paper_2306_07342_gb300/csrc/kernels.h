@@ -13,9 +13,9 @@ namespace vqd {
 
 // A diagonal factor equal to 1: elementwise passes (plain and fused) leave the amplitudes with this
 // factor untouched.  The comparison is exact.  The device compiler and the fused composer write the
-// factors |U_rr|^2 of diagonal unitaries as exactly 1 (see superop_from_unitary), so a phase or a
-// dephasing skips the members whose row and column index agree; a factor of a caller's superoperator
-// is skipped only when it is exactly 1.
+// factors U_rr conj(U_cc) of diagonal unitaries as exactly 1 when U_rr and U_cc are the same number
+// (see diag_unitary_factor), so a phase or a dephasing skips the members it leaves unchanged; a factor
+// of a caller's superoperator is skipped only when it is exactly 1.
 inline bool is_unit_factor(const std::complex<double>& c) { return c.real() == 1.0 && c.imag() == 0.0; }
 // Fraction of the state's amplitudes a plain pass reads and writes: elementwise passes skip the
 // amplitudes whose factor is 1; every other pass touches all of them.

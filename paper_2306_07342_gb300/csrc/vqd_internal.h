@@ -33,6 +33,9 @@ Op compile_native(const vqd_native_op& op, unsigned flags);
 void stderr_params(int nq, double fbar, double x, double* p_deph, double* q_depol);
 std::vector<cd> superop_from_kraus(int k, int nK, const cd* K);   // sum conj(K) (x) K
 std::vector<cd> superop_from_unitary(int k, const cd* U);            // |U_rr|^2 of a diagonal U set to 1
+// Factor U_rr conj(U_cc) of a diagonal unitary's superoperator: exactly 1 when the two entries are the
+// same number (|U_rr| = 1), else their product.
+inline cd diag_unitary_factor(const cd& ur, const cd& uc) { return ur == uc ? cd(1.0) : ur * std::conj(uc); }
 bool is_diagonal_matrix(int d, const cd* M);
 void check_unitary(int k, const cd* U);                           // throws VQD_ENOTCP
 void check_cptn(int k, int nK, const cd* K);                      // throws VQD_ENOTCP

@@ -100,6 +100,10 @@ class na_device(ctypes.Structure):
 VQD_NA_NO_PASSIVE = 1
 
 
+VQD_TC_3XTF32 = 0
+VQD_TC_BF16X3 = 1
+
+
 class VQDError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libvqd error {code}: {msg}")
@@ -161,6 +165,8 @@ def lib() -> ctypes.CDLL:
             "vqd_ion_compile": (I, [P, I, P, I, I, P, P]),
             "vqd_na_compile": (I, [P, I, P, I, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
+            "vqd_run_program_tc": (I, [P, I, I, P, I, I, U]),
+            "vqd_tc_plan_info": (I, [I, I, P, I, U, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -286,6 +292,20 @@ def vqd_apply_native(ctx, inst: int, ops, flags: int = 0):
 def vqd_run_program(ctx, inst: int, ops, fuse_qubits: int = 0, flags: int = 0):
     a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
     _check(lib().vqd_run_program(ctx, inst, len(a), _ptr(a), fuse_qubits, flags), ctx)
+
+
+def vqd_run_program_tc(ctx, inst: int, ops, k: int = 4, scheme: int = VQD_TC_3XTF32, flags: int = 0):
+    """Fused k-qubit blocks applied as split-precision GEMMs on the tensor cores (complex64 contexts)."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    _check(lib().vqd_run_program_tc(ctx, inst, len(a), _ptr(a), k, scheme, flags), ctx)
+
+
+def vqd_tc_plan_info(n: int, ops, k: int = 4, flags: int = 0) -> dict:
+    """Blocks of the tensor-core form for a program (host only, no GPU needed)."""
+    a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
+    info = np.zeros(3, dtype=np.int64)
+    _check(lib().vqd_tc_plan_info(n, len(a), _ptr(a), k, flags, _ptr(info)))
+    return {"blocks": int(info[0]), "native_ops": int(info[1]), "max_block_ops": int(info[2])}
 
 
 def vqd_run_batch(ctx, programs_ops: Sequence, fuse_qubits: int = 0, flags: int = 0):

@@ -208,3 +208,20 @@ def test_prob_static_refuses_misaligned_addresses(vqd, prec_name, state_addr, ou
         vqd.vqd_prob_static(state_addr, 4, prec, [0, 1], out_addr)
     assert e.value.code == vqd.VQD_EINVAL and "aligned" in str(e.value)
 
+
+
+def test_tc_plan_blocks_keep_per_qubit_order_and_cover_every_op(vqd):
+    """The tensor-core planner's blocks hold at most k qubits and, for ion-trap all-to-all programs, absorb
+    several native ops each; every op lands in exactly one block (host-only planning call)."""
+    from workloads import config3_ion_alltoall
+    prog = config3_ion_alltoall(seed=3, n=15, n_gates=800)
+    prev = None
+    for k in (4, 5, 6):
+        info = vqd.vqd_tc_plan_info(15, prog.ops, k)
+        assert info["native_ops"] == len(prog.ops) and info["max_block_ops"] >= 1
+        assert info["blocks"] * k >= 2 * 1 and info["blocks"] < len(prog.ops) / 4
+        if prev is not None:
+            assert info["blocks"] <= prev                 # wider blocks never need more passes here
+        prev = info["blocks"]
+    with pytest.raises(vqd.VQDError):
+        vqd.vqd_tc_plan_info(15, prog.ops, 7)
