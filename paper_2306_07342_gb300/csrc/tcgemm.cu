@@ -7,8 +7,9 @@
 // with complex numbers interleaved (re, im), this is Y = X R^T over all groups: X has one row per group
 // and 2 * 4^k columns, R = [[Re S, -Im S], [Im S, Re S]] interleaved the same way.  The GEMM runs with
 //   M = 128 groups per tile (one TMEM lane each),
-//   N = 512 output reals per n-tile (TMEM columns: 128 lanes x 512 columns of FP32 = all of TMEM),
-//   K = 2 * 4^k input reals, in chunks of 16.
+//   N = 128 output reals per work item (one TMEM accumulator slot of 128 columns; two slots per CTA),
+//   K = 2 * 4^k input reals, in chunks of 16, each chunk accumulated in its own slot and the chunks
+//   summed in FP32 registers.
 // Split precision: the FP32 operands are split into limbs and the limb products accumulate in FP32:
 //   3xTF32: x = hi + lo (hi = tf32(x), lo = tf32(x - hi)), products lo*hi + hi*lo + hi*hi;
 //   BF16x3: x = b1 + b2 + b3 (each the bf16 rounding of the remainder), the six products b_i*b_j with
@@ -38,7 +39,7 @@ namespace vqd {
 namespace tc {
 
 constexpr int kM = 128;       // groups per tile (MMA M, TMEM lanes)
-constexpr int kNT = 512;      // output reals per n-tile (TMEM columns)
+constexpr int kNT = 128;      // output reals per work item (TMEM columns of one accumulator slot)
 constexpr int kKc = 16;       // input reals per K chunk
 constexpr int kThreads = 128;
 constexpr int kStages = 2;
@@ -66,7 +67,7 @@ template <int SCHEME> __host__ __device__ constexpr int stage_bytes() {
 }
 constexpr int kMaxMembers = 4096;  // 4^6
 template <int SCHEME> __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + 256;
+  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + 8 * (kStages + 2) + 16;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -178,14 +179,20 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 };
 
 // ------------------------------------------------------------------ the block kernel
+// Per work item (a tile of kM groups and kNT output reals) the K chunks run as a two-slot pipeline: the
+// tensor core accumulates chunk c into TMEM slot c % 2, starting from zero, while the threads read chunk
+// c - 1's slot and add it into FP32 registers.  The tensor core's accumulation rounds toward zero, so
+// summing all 2 * 4^k inputs in TMEM would shrink every output by roughly (number of additions) x 2^-25
+// (measured: a trace 3.6e-5 low after 17 blocks of k = 4); summing one chunk's 16 inputs there and the
+// chunks in registers (round to nearest) keeps the result unbiased.
 template <int SCHEME>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
+__global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
   using Sc = Scheme<SCHEME>;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint32_t* s_off = (uint32_t*)(sm + kStages * stage_bytes<SCHEME>());
-  uint64_t* s_bar = (uint64_t*)(s_off + kMaxMembers);  // [0,1]: TMA per stage, [2,3]: MMA per stage
-  uint32_t* s_tmem = (uint32_t*)(s_bar + 4);
+  uint64_t* s_bar = (uint64_t*)(s_off + kMaxMembers);  // [0, kStages): TMA per stage; then MMA per TMEM slot
+  uint32_t* s_tmem = (uint32_t*)(s_bar + kStages + 2);
   int* s_flag = (int*)(s_tmem + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   auto a_tile = [&](int st, int limb) { return sm + st * stage_bytes<SCHEME>() + limb * a_bytes<SCHEME>(); };
@@ -194,11 +201,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
   };
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(kNT) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(2 * kNT)
+                 : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; i++) mbar_init(su32(&s_bar[i]), 1);
+    for (int i = 0; i < kStages + 2; i++) mbar_init(su32(&s_bar[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
   }
@@ -213,19 +221,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 
-  const uint32_t id = idesc(SCHEME == VQD_TC_3XTF32 ? 2u : 1u, kM, 256);
+  const uint32_t id = idesc(SCHEME == VQD_TC_3XTF32 ? 2u : 1u, kM, kNT);
   constexpr uint32_t kAslice = kM * 16, kBslice = kNT * 16;  // bytes per 16-byte K slice of A and B
   constexpr int kElemPer16 = 16 / Sc::esz;
-  constexpr int kSteps = kKc / Sc::kper;                       // MMAs along K per chunk
+  constexpr int kSteps = kKc / Sc::kper;                       // MMAs along K per chunk and product
   const uint32_t stage_tx = (uint32_t)(Sc::limbs * b_bytes<SCHEME>());
-  uint32_t tma_par[kStages] = {0, 0}, mma_par[kStages] = {0, 0};
-  bool mma_pend[kStages] = {false, false};
-  uint32_t chunk = 0;
+  uint32_t tma_par[kStages], acc_par[2] = {0, 0};
+  for (int i = 0; i < kStages; i++) tma_par[i] = 0;
+  bool acc_pend[2] = {false, false};
   bool ok = true;
   const uint64_t items = (uint64_t)P.n_gtiles * P.n_ntiles;
   const float2* __restrict__ X = P.X;
   float2* __restrict__ Y = P.Y;
+
+  float sum[kNT];
+  // read TMEM slot `slot` (this thread's lane, kNT columns) into sum once its chunk's products are complete
+  auto readout = [&](int slot) {
+    const bool w = mbar_wait(su32(&s_bar[kStages + slot]), acc_par[slot]);
+    acc_par[slot] ^= 1u;
+    acc_pend[slot] = false;
+    if (!w) *s_flag = 1;
+    tc_fence_after();
+#pragma unroll
+    for (int c = 0; c < kNT; c += 16) {
+      float v[16];
+      tmem_ld16(lane_addr + slot * kNT + c, v);
+#pragma unroll
+      for (int i = 0; i < 16; i++) sum[c + i] += v[i];
+    }
+    tc_fence_before();
+  };
 
   for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
     const uint32_t gt = (uint32_t)(item / P.n_ntiles), nt = (uint32_t)(item % P.n_ntiles);
@@ -236,14 +263,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       const uint32_t low = (1u << P.pos[j]) - 1u;
       base = (base & low) | ((base & ~low) << 1);
     }
-    for (int kc = 0; kc < P.n_kchunks && ok; kc++, chunk++) {
-      const int st = chunk & 1;
-      if (mma_pend[st]) {  // the tensor core has finished reading this stage's buffers
-        const bool w = mbar_wait(su32(&s_bar[2 + st]), mma_par[st]);
-        mma_par[st] ^= 1u;
-        mma_pend[st] = false;
-        if (!w) *s_flag = 1;
-      }
+#pragma unroll
+    for (int i = 0; i < kNT; i++) sum[i] = 0.f;
+    for (int kc = 0; kc < P.n_kchunks; kc++) {
+      const int st = kc % kStages, slot = kc & 1;
+      // stage st and slot were last used by chunk kc - 2, read out (so complete) in the previous iteration
       __syncthreads();
       if (*s_flag) { ok = false; break; }
       if (tid == 0) {
@@ -251,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
         mbar_expect_tx(bar, stage_tx);
         for (int l = 0; l < Sc::limbs; l++) {
           const int blk = (nt * P.n_kchunks + kc) * Sc::limbs + l;
-          tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * 32, bar);
+          tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), bar);
         }
       }
       // gather this chunk's 8 members of group g, split into limbs, K-major rows
@@ -278,17 +302,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
         for (int q = 0; q < kKc / kElemPer16; q++) {
           if constexpr (SCHEME == VQD_TC_3XTF32) {
             float4 w;
-            w.x = ((const float*)lre[2 * q].l)[l];
-            w.y = ((const float*)lim[2 * q].l)[l];
-            w.z = ((const float*)lre[2 * q + 1].l)[l];
-            w.w = ((const float*)lim[2 * q + 1].l)[l];
+            w.x = lre[2 * q].l[l];
+            w.y = lim[2 * q].l[l];
+            w.z = lre[2 * q + 1].l[l];
+            w.w = lim[2 * q + 1].l[l];
             *(float4*)(at + q * kAslice + 16 * tid) = w;
           } else {
             __nv_bfloat16 h[8];
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-              h[2 * e] = ((const __nv_bfloat16*)lre[4 * q + e].l)[l];
-              h[2 * e + 1] = ((const __nv_bfloat16*)lim[4 * q + e].l)[l];
+              h[2 * e] = lre[4 * q + e].l[l];
+              h[2 * e + 1] = lim[4 * q + e].l[l];
             }
             *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
           }
@@ -301,58 +325,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
         if (!w) *s_flag = 1;
         else {
           tc_fence_after();
+          const uint32_t d = tmem + slot * kNT;
 #pragma unroll
-          for (int h = 0; h < 2; h++)
+          for (int ks = 0; ks < kSteps; ks++)
 #pragma unroll
-            for (int ks = 0; ks < kSteps; ks++)
-#pragma unroll
-              for (int p = 0; p < Sc::nprod; p++) {
-                const uint64_t ad = sdesc(su32(a_tile(st, Sc::pa(p))) + ks * 2 * kAslice, kAslice, 128);
-                const uint64_t bd = sdesc(su32(b_tile(st, Sc::pb(p))) + h * 256 * 16 + ks * 2 * kBslice, kBslice, 128);
-                mma<SCHEME>(tmem + h * 256, ad, bd, id, (kc > 0 || ks > 0 || p > 0) ? 1u : 0u);
-              }
-          mma_commit(su32(&s_bar[2 + st]));
+            for (int p = 0; p < Sc::nprod; p++) {
+              const uint64_t ad = sdesc(su32(a_tile(st, Sc::pa(p))) + ks * 2 * kAslice, kAslice, 128);
+              const uint64_t bd = sdesc(su32(b_tile(st, Sc::pb(p))) + ks * 2 * kBslice, kBslice, 128);
+              mma<SCHEME>(d, ad, bd, id, (ks > 0 || p > 0) ? 1u : 0u);
+            }
+          mma_commit(su32(&s_bar[kStages + slot]));
         }
       }
       tma_par[st] ^= 1u;
-      mma_pend[st] = true;
+      acc_pend[slot] = true;
+      if (kc > 0) readout(slot ^ 1);
     }
-    // all of the item's products are in TMEM once both stages' last commits have completed
-    for (int st = 0; st < kStages; st++)
-      if (mma_pend[st]) {
-        const bool w = mbar_wait(su32(&s_bar[2 + st]), mma_par[st]);
-        mma_par[st] ^= 1u;
-        mma_pend[st] = false;
-        if (!w) *s_flag = 1;
-      }
+    if (!ok) break;
+    if (acc_pend[(P.n_kchunks - 1) & 1]) readout((P.n_kchunks - 1) & 1);
     __syncthreads();
     if (*s_flag) { ok = false; break; }
-    tc_fence_after();
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (its groups), 16 columns (8 output members) at a time
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t out0 = nt * (kNT / 2);
-    for (int c = 0; c < kNT; c += 16) {
-      float v[16];
-      tmem_ld16(lane_addr + c, v);
-      if (valid) {
+    if (valid) {
+      const uint32_t out0 = nt * (kNT / 2);
 #pragma unroll
-        for (int e = 0; e < 8; e++) Y[base + s_off[out0 + c / 2 + e]] = make_float2(v[2 * e], v[2 * e + 1]);
-      }
+      for (int e = 0; e < kNT / 2; e++) Y[base + s_off[out0 + e]] = make_float2(sum[2 * e], sum[2 * e + 1]);
     }
-    tc_fence_before();
-    __syncthreads();
   }
   // leave with no copy or tensor-core operation of this CTA in flight (bounded waits), then free TMEM
+  __syncthreads();
   if (tid == 0) {
-    for (int st = 0; st < kStages; st++) {
-      if (mma_pend[st]) mbar_wait(su32(&s_bar[2 + st]), mma_par[st]);
-    }
+    for (int slot = 0; slot < 2; slot++)
+      if (acc_pend[slot]) mbar_wait(su32(&s_bar[kStages + slot]), acc_par[slot]);
     if (*s_flag) atomicExch(P.err, 1);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNT) : "memory");
 }
 
 // ------------------------------------------------------------------ R: limbs in the tiled K-major layout
@@ -495,12 +504,12 @@ static cudaError_t launch_t(const TcParams& P, const void* R, int k, cudaStream_
   using Sc = Scheme<SCHEME>;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  // R as a 2-D tensor of rows of 256 elements; one limb's chunk is 32 rows (kNT * kKc elements)
+  // R as a 2-D tensor of rows of 256 elements; one limb's chunk is kNT * kKc / 256 rows
   const uint64_t elems = (uint64_t)(2u << (2 * k)) * (2u << (2 * k)) * Sc::limbs;
   CUtensorMap tm;
   cuuint64_t gdim[2] = {256, (cuuint64_t)(elems / 256)};
   cuuint64_t gstride[1] = {(cuuint64_t)256 * Sc::esz};
-  cuuint32_t box[2] = {256, 32};
+  cuuint32_t box[2] = {256, (cuuint32_t)(kNT * kKc / 256)};
   cuuint32_t estride[2] = {1, 1};
   CUresult cr = enc(&tm, SCHEME == VQD_TC_3XTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     const_cast<void*>(R), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -510,7 +519,12 @@ static cudaError_t launch_t(const TcParams& P, const void* R, int k, cudaStream_
   cudaError_t e = cudaFuncSetAttribute(k_tc_block<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t items = (uint64_t)P.n_gtiles * P.n_ntiles;
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)num_sms()));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_block<SCHEME>, kThreads, smem) != cudaSuccess ||
+      per_sm <= 0)
+    per_sm = 1;
+  per_sm = std::min(per_sm, 2);  // two CTAs of 256 TMEM columns fill an SM's 512
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)per_sm * num_sms()));
   k_tc_block<SCHEME><<<grid, kThreads, smem, s>>>(tm, P);
   return cudaGetLastError();
 }
