@@ -112,18 +112,25 @@ Mat sup_kraus(int k, const std::vector<Mat>& ks) {
 }
 
 // Pauli channel sum_s w_s P_s rho P_s on one (k=1) or two (k=2) qubits, weights indexed by
-// s = s_lo + 4 s_hi.  Its superoperator is diagonal in the Pauli basis; built here from Kraus form.
+// s = s_lo + 4 s_hi.  Its superoperator is sum_s w_s conj(P_s) (x) P_s; a Pauli's entries are 0, +-1
+// or +-i, so every entry is a signed sum of the weights, formed here without the square roots of a Kraus
+// form: the entries that the mathematics makes 1 (for example the populations under a dephasing,
+// (1 - p) + p) come out as exactly 1.
 Mat sup_pauli(int k, const double* w) {
-  std::vector<Mat> ks;
-  int np = k == 1 ? 4 : 16;
+  const int d = 1 << k, D = d * d, np = k == 1 ? 4 : 16;
+  Mat S(D * D, 0.0);
   for (int s = 0; s < np; s++) {
     if (w[s] == 0.0) continue;
-    Mat P = k == 1 ? pauli(s) : kron(pauli(s / 4), 2, pauli(s % 4), 2);
-    for (cd& x : P) x *= std::sqrt(w[s]);
-    ks.push_back(P);
+    const Mat P = k == 1 ? pauli(s) : kron(pauli(s / 4), 2, pauli(s % 4), 2);
+    for (int r1 = 0; r1 < d; r1++)
+      for (int c1 = 0; c1 < d; c1++)
+        for (int r2 = 0; r2 < d; r2++)
+          for (int c2 = 0; c2 < d; c2++) {
+            const cd e = P[r1 * d + r2] * std::conj(P[c1 * d + c2]);  // 0, +-1 or +-i, exact
+            if (e != 0.0) S[(r1 | (c1 << k)) * D + (r2 | (c2 << k))] += w[s] * e;
+          }
   }
-  if (ks.empty()) return Mat((1 << (2 * k)) * (1 << (2 * k)), 0.0);
-  return sup_kraus(k, ks);
+  return S;
 }
 
 Mat sup_depol1(double p) { double w[4] = {1 - p, p / 3, p / 3, p / 3}; return sup_pauli(1, w); }
