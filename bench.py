@@ -1,21 +1,27 @@
 #!/usr/bin/env python
-"""Benchmark: density-matrix amplitude-updates per second on the 14-qubit superconducting-grid workload.
+"""Benchmark: density-matrix amplitude-updates/s, the fused path against the plain FP64 path at stated error.
 
-Workload: a 2 x 7 grid of transmon-like qubits (n = 14, complex64 state of 2.15 GB), depth-60 brickwork of
-native ZX(pi/2) cross-resonance gates and Rz.SX.Rz layers, static ZZ crosstalk (50 kHz) on idle grid edges,
-T1 log-uniform in 50-200 us with T2 = 0.7 T1 as passive decay after every sublayer, and a 2 % readout flip
-(6494 native ops; seeded synthetic program from workloads.config2_sc_grid).  One step = reset to |0><0|,
-the whole program through the plain unfused kernels (one pass over the state per native op), then the
-FP64 reductions (14-qubit Z-basis probabilities, trace, purity) read back to the host.
+Headline workload: the superconducting-like 2 x 7 grid (n = 14), the full depth-60 program of 6494 native ops
+(Rz.SX.Rz layers, ZX(pi/2) cross-resonance brickwork, static ZZ crosstalk of 50 kHz on idle edges, T1/T2 idle
+decay with T1 log-uniform in 50-200 us and T2 = 0.7 T1, a 2 % readout flip; seeded synthetic program from
+workloads.config2_sc_grid).  One step = reset to |0><0|, the whole program through the fused path (stages of
+operators on shared-memory tiles) with float-float storage and arithmetic (every real and imaginary part a
+pair of FP32 numbers, about 48 significant bits: FP64-class accuracy on the FP32 pipes), then the FP64
+reductions (14-qubit Z-basis probabilities, trace, purity) read back to the host.
 
 Metric: amplitude-updates/s = sum over the program's native ops of 4^n, divided by the time.  The state
-(2.15 GB) is larger than L2 (129 MB), so no L2 flush is needed between steps.
+(4.3 GB in float-float) is larger than L2 (129 MB), so no L2 flush is needed between steps.
 
-The JSON line also reports the fused path (stages of ops on shared-memory tiles) and the plain FP64
-(complex128) path on a sample of the same program, the roofline of the dominant kernel, the oracle timed
-on the host cores, and the SM clocks sampled during the timed region.
+Beside the headline the JSON line reports, each with its error against the plain FP64 (complex128) run of
+the same program (max-abs, Frobenius norm, the trace-distance bound 1/2 2^(n/2) ||rho - sigma||_F and the
+super-fidelity): the plain FP64 path, the fused FP64 path, plain float-float, the fused and plain complex64
+paths; the 15-qubit ion-trap program through the tensor-core blocks (tcgen05, 3xTF32 and BF16x3, k = 4..6)
+and through the CUDA-core fused path; the 16-qubit spin chain (34 GB complex64 density matrix) fused in
+complex64 and float-float; the 1024-instance batch with an autotuned fusion width and tile shape; the
+trajectory, device-compiler and noise-sweep workloads; the roofline of each path's dominant kernel; the
+oracle timed on the host cores (single thread and all cores); and the SM clocks during the timed region.
 
---impl reference times the FP64 numpy oracle on the host cores on a bounded sample of the same workload.
+--impl reference times the FP64 oracle (its C loops, all host cores) on a bounded sample of the same workload.
 With --gpus N > 1 every rank runs an independent replica of the workload (the path has no data exchange).
 """
 from __future__ import annotations
@@ -32,10 +38,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "density-matrix amplitude-updates/s (sum over native ops of 4^n per second)"
+METRIC = "density-matrix amplitude-updates/s & HBM roofline %, fused vs plain FP64 at stated error"
 UNIT = "amp-updates/s"
-WORKLOAD = ("superconducting-like 2x7 grid, 14 qubits, depth-60 ZX(pi/2)+Rz/SX brickwork, ZZ crosstalk 50 kHz, "
-            "T1/T2 idle decay, readout flip 2e-2; complex64 state; plain unfused kernels")
+WORKLOAD = ("superconducting-like 2x7 grid, 14 qubits, full depth-60 program (6494 native ops: Rz/SX layers, "
+            "ZX(pi/2) brickwork, ZZ crosstalk 50 kHz, T1/T2 idle decay, readout flip 2e-2)")
+PREC_NAMES = {"split": "f32x2", "f64": "f64", "f32": "f32"}
 
 
 def parse():
@@ -44,8 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vqd", choices=["vqd", "reference"])
-    ap.add_argument("--no-extra", action="store_true", help="skip the fused / FP64 / oracle side measurements")
-    ap.add_argument("--error", action="store_true", help="also measure the complex64 error against an FP64 run")
+    ap.add_argument("--path", default="fused", choices=["plain", "fused"], help="path of the headline")
+    ap.add_argument("--prec", default="split", choices=["split", "f64", "f32"], help="precision of the headline")
+    ap.add_argument("--no-extra", action="store_true", help="only the headline (profiling runs)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 15- and 16-qubit lines")
     ap.add_argument("--rows", type=int, default=2, help="grid rows (profiling cases only; the benchmark is 2x7)")
     ap.add_argument("--cols", type=int, default=7)
     ap.add_argument("--depth", type=int, default=60)
@@ -55,8 +64,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["sc_grid14", "ion15", "spin16"],
                     help="instead of timing: error of the complex64 paths against the FP64 path on one workload")
     ap.add_argument("--prefix", type=int, default=0, help="--precision: only the first N native ops (0 = all)")
-    ap.add_argument("--path", default="plain", choices=["plain", "fused"],
-                    help="path of the headline measurement (profiling cases; the benchmark is plain)")
+    ap.add_argument("--oracle-plan", action="store_true",
+                    help="time the oracle on every configuration (single thread and all cores) and exit")
     return ap.parse_args()
 
 
@@ -116,43 +125,126 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+
 # ---------------------------------------------------------------- oracle (host) timing
-def oracle_rate(prog, n_ops: int):
-    """Time the FP64 numpy oracle on the first n_ops native ops of prog at full size."""
-    from oracle import evolve
+def host_ram_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError, AttributeError):
+        return 0
+
+
+def oracle_time(prog, n_ops, threads):
+    """Seconds the oracle's C loops take for the first n_ops native ops of prog at full size (the state
+    allocation and initialisation are not timed)."""
+    import numpy as np
+    from oracle import cloop, evolve
+    from oracle import compile as oc
+    cloop.set_threads(threads)
+    rho = np.array(evolve.initial_state(prog), dtype=np.complex128, order="C")
     t = time.perf_counter()
-    evolve.run_program(prog, max_ops=n_ops)
+    for o in prog.ops[:n_ops]:
+        cloop.apply_steps(rho, oc.compile_op(o.name, o.qubits, o.params))
     dt = time.perf_counter() - t
-    return n_ops * 4.0 ** prog.n / dt, dt
+    del rho
+    return dt
+
+
+def oracle_line(name, prog, n_ops, threads, kind):
+    dt = oracle_time(prog, n_ops, threads)
+    units = n_ops * 4.0 ** prog.n
+    rec = {"config": name, "n": prog.n, "threads": threads, "ops_timed": n_ops, "ops_total": len(prog.ops),
+           "seconds": dt, "value": units / dt, "unit": UNIT}
+    if n_ops < len(prog.ops):
+        rec["extrapolated_full_program_s"] = dt * len(prog.ops) / n_ops
+        rec["kind"] = f"{kind}; extrapolated from the first {n_ops} of {len(prog.ops)} ops"
+    else:
+        rec["kind"] = kind
+    return rec
+
+
+def cpu_baseline_block(quick=True):
+    """The FP64 oracle (plain C loops, OpenMP) on the host cores, on bounded samples of the configurations:
+    configuration 1 in full, the 14-qubit grid on a prefix (all cores and one thread), the 15-qubit ion
+    program on a prefix, the 16-qubit spin chain on one op when the host has the RAM (68.7 GB), and the
+    neutral-atom batch on its first instances, scaled by sum 4^n.  Per-op cost is the same along a program
+    of one kind of op mix, so prefix timings are extrapolated to the full program (labelled)."""
+    from oracle import cloop
+    from workloads import (config1_chain6, config2_sc_grid, config3_ion_alltoall, config4_neutral_batch,
+                           config5_spin_chain)
+    allc = cloop.max_threads()
+    out = {"threads_all": allc, "lines": []}
+    c1 = config1_chain6()
+    out["lines"].append(oracle_line("chain6 (n=6, full)", c1, len(c1.ops), allc, "all cores"))
+    out["lines"].append(oracle_line("chain6 (n=6, full)", c1, len(c1.ops), 1, "one thread"))
+    c2 = config2_sc_grid()
+    out["lines"].append(oracle_line("sc_grid14 (n=14)", c2, 12 if quick else 60, allc, "all cores"))
+    out["lines"].append(oracle_line("sc_grid14 (n=14)", c2, 2 if quick else 12, 1, "one thread"))
+    if not quick:
+        c3 = config3_ion_alltoall()
+        out["lines"].append(oracle_line("ion15 (n=15)", c3, 50, allc, "all cores"))
+        if host_ram_bytes() > 160e9:
+            c5 = config5_spin_chain()
+            out["lines"].append(oracle_line("spin16 (n=16)", c5, 50, allc, "all cores"))
+        progs = config4_neutral_batch(count=1024)
+        sample = progs[:32]
+        t = 0.0
+        for q in sample:
+            t += oracle_time(q, len(q.ops), allc)
+        su = sum(len(q.ops) * 4.0 ** q.n for q in sample)
+        tu = sum(len(q.ops) * 4.0 ** q.n for q in progs)
+        out["lines"].append({"config": "neutral batch (1024 instances)", "threads": allc, "instances_timed": 32,
+                             "seconds": t, "value": su / t, "unit": UNIT, "scaled_full_batch_s": t * tu / su,
+                             "kind": "all cores; scaled by sum 4^n from the first 32 instances"})
+    cloop.set_threads(allc)
+    return out
+
+
+def run_oracle_plan(args):
+    print(json.dumps(cpu_baseline_block(quick=False)), flush=True)
 
 
 def run_reference(args):
+    """The oracle arm: its C loops on all host cores, each step the first 4 native ops of the 14-qubit grid
+    program at full size (the state is allocated once; the work per op does not depend on its values)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
+    from oracle import cloop, evolve
+    from oracle import compile as oc
     from workloads import config2_sc_grid
     prog = config2_sc_grid()
-    per_step = 2
+    per_step = 4
+    threads = cloop.max_threads()
+    cloop.set_threads(threads)
+    rho = np.array(evolve.initial_state(prog), dtype=np.complex128, order="C")
+    steps = [oc.compile_op(o.name, o.qubits, o.params) for o in prog.ops[:per_step]]
+
+    def step():
+        for s in steps:
+            cloop.apply_steps(rho, s)
+
     for _ in range(args.warmup):
-        oracle_rate(prog, per_step)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_rate(prog, per_step)
+        step()
     dt = time.perf_counter() - t0
     value = args.steps * per_step * 4.0 ** prog.n / dt
-    cores = os.cpu_count()
-    sample = f"first {per_step} native ops of the 14-qubit program at full size per step (FP64 numpy oracle)"
+    sample = (f"first {per_step} native ops of the 14-qubit program at full size per step (FP64 oracle, plain C "
+              f"loops, {threads} threads)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- GPU arm helpers
 def load_traffic(kernel_class: str):
     """DRAM bytes per launch of a kernel class from a committed ncu summary, if the kernel source still
     matches the hash recorded with the counters; else None."""
@@ -166,6 +258,127 @@ def load_traffic(kernel_class: str):
     src = os.path.join(ROOT, "paper_2306_07342_gb300", "csrc", rec["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return rec["bytes_per_launch"] if h == rec["source_sha256_16"] else None
+
+
+def state_view(torch, vqd, ctx, prec):
+    """Zero-copy complex128-convertible chunks of a context's state: yields complex torch tensors."""
+    n = vqd.vqd_num_qubits(ctx, 0)
+    N = 4 ** n
+    ptr = vqd.vqd_state_ptr(ctx, 0)
+    if prec == vqd.VQD_F32_SPLIT:
+        v = split_view(torch, ptr, N)
+        return lambda a, b: torch.complex(v[a:b, 0].double() + v[a:b, 1].double(), v[a:b, 2].double() + v[a:b, 3].double())
+    v = device_view(torch, ptr, N, prec == vqd.VQD_F32)
+    return lambda a, b: v[a:b].to(torch.complex128)
+
+
+def state_error(torch, vqd, ref_ctx, ref_prec, ctx, prec):
+    """Error of a state against a reference state on the device: max-abs, Frobenius norm, the trace-distance
+    bound 1/2 2^(n/2) ||rho - sigma||_F, and the super-fidelity tr(rho sigma) + sqrt((1 - tr rho^2)(1 - tr sigma^2))
+    (an upper bound of the Uhlmann fidelity), with the total-variation distance of the Z-basis probabilities."""
+    import numpy as np
+    n = vqd.vqd_num_qubits(ctx, 0)
+    N = 4 ** n
+    a_of, b_of = state_view(torch, vqd, ref_ctx, ref_prec), state_view(torch, vqd, ctx, prec)
+    maxabs, fro2, overlap = 0.0, 0.0, 0.0
+    chunk = 1 << 25
+    for i in range(0, N, chunk):
+        a, b = a_of(i, min(N, i + chunk)), b_of(i, min(N, i + chunk))
+        d = b - a
+        maxabs = max(maxabs, float(d.abs().max()))
+        fro2 += float((d.real ** 2 + d.imag ** 2).sum())
+        overlap += float((a.conj() * b).real.sum())          # tr(rho sigma) for Hermitian rho, sigma
+        del a, b, d
+    pr, pa = vqd.vqd_purity(ref_ctx, 0), vqd.vqd_purity(ctx, 0)
+    qr, qa = vqd.vqd_prob(ref_ctx, 0, list(range(n))), vqd.vqd_prob(ctx, 0, list(range(n)))
+    return {"max_abs": maxabs, "frobenius": fro2 ** 0.5, "trace_distance_bound": 0.5 * 2 ** (n / 2) * fro2 ** 0.5,
+            "super_fidelity": overlap + float(np.sqrt(max(0.0, (1 - pr) * (1 - pa)))),
+            "prob_tv_distance": 0.5 * float(np.abs(qa - qr).sum()),
+            "trace_err": abs(vqd.vqd_trace(ctx, 0).real - vqd.vqd_trace(ref_ctx, 0).real)}
+
+
+def roofline_hbm(stats, peak, peak_src, steps=1, exclude=("reduce", "init", "tc_compose")):
+    """Dominant kernel class (by device time) as an HBM-bound kernel: algorithmic bytes (2 x state bytes per
+    full pass, the touched fraction for elementwise passes) per launch over its average launch time."""
+    kern = {k: v for k, v in stats.items() if k not in exclude and v["launches"]}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    s = kern[dom]
+    per_launch = s["alg_bytes"] / s["launches"]
+    avg_ms = s["total_ms"] / s["launches"]
+    achieved = per_launch / (avg_ms * 1e-3) / 1e9
+    total = sum(v["total_ms"] for v in stats.values())
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": load_traffic(dom), "kernel": dom, "peak_source": peak_src,
+            "launches": s["launches"] // max(1, steps), "share_of_kernel_time": s["total_ms"] / total if total else None,
+            "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms}
+
+
+def per_class(stats, steps=1):
+    return {k: {"launches": v["launches"] // max(1, steps), "avg_ms": v["total_ms"] / v["launches"]}
+            for k, v in stats.items() if v["launches"]}
+
+
+def timed_steps(torch, vqd, stream, ctx, step, steps, warmup, clocks=None, sync=None):
+    """Warm-up steps, then `steps` steps between CUDA events on the context's stream (no per-launch accounting
+    inside the timed region); returns (ms, clock record)."""
+    for _ in range(warmup):
+        step()
+    vqd.vqd_profile(ctx, 0)
+    (sync or torch.cuda.synchronize)()
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    return e0.elapsed_time(e1), ck
+
+
+def profiled_step(torch, vqd, ctx, step):
+    """One step with every launch timed by CUDA events (the library's accounting): per-class device times."""
+    vqd.vqd_profile(ctx, 2)
+    vqd.vqd_profile_reset(ctx)
+    step()
+    torch.cuda.synchronize()
+    st = vqd.vqd_profile_read(ctx)
+    vqd.vqd_profile(ctx, 0)
+    return st
+
+
+def make_step(vqd, ctx, n, native, path, fuse=0, tc=None):
+    def step():
+        vqd.vqd_init_zero(ctx, 0)
+        if path == "plain":
+            vqd.vqd_apply_native(ctx, 0, native)
+        elif path == "fused":
+            vqd.vqd_run_program(ctx, 0, native, fuse)
+        else:
+            vqd.vqd_run_program_tc(ctx, 0, native, tc[0], tc[1])
+        vqd.vqd_prob(ctx, 0, list(range(n)))
+        vqd.vqd_trace(ctx, 0)
+        vqd.vqd_purity(ctx, 0)
+    return step
+
+
+def tensor_roofline(stats, n, k, scheme, bf16_peak_tflops):
+    """tcgen05 blocks against the tensor pipe: algorithmic flops of one block application are the real GEMM's
+    2 x 4^(n-k) groups x (2 4^k)^2, times the split products (3 for 3xTF32, 6 for BF16x3); the peak is the
+    measured dense BF16 rate, halved for TF32 (the nominal ratio of the two, 1.1 vs 2.25 PFLOP/s)."""
+    s = stats.get("tc_gemm")
+    if not s or not s["launches"]:
+        return None
+    nprod = 3 if scheme == 0 else 6
+    flops = 2.0 * 4 ** (n - k) * (2 * 4 ** k) ** 2 * nprod
+    avg_ms = s["total_ms"] / s["launches"]
+    peak = bf16_peak_tflops * (0.5 if scheme == 0 else 1.0)
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "tc_gemm (k_tc_block)", "launches": s["launches"], "avg_launch_ms": avg_ms,
+            "flops_per_launch": flops, "peak_source": "measured bf16" + (" x 0.5 (TF32)" if scheme == 0 else ""),
+            "hbm_GBps_per_launch": s["alg_bytes"] / s["launches"] / (avg_ms * 1e-3) / 1e9}
 
 
 def measure_trajectories(vqd, torch, prog, native, stream_handle, ntraj=1024):
@@ -279,75 +492,6 @@ def measure_nv_noise_sweep(vqd, torch, count=256, props=16):
         vqd.vqd_destroy(ctx)
 
 
-def measure_batch(vqd, torch, stream_handle, count):
-    """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of
-    persistent kernels), against one launch sequence per instance (fused and plain) on a sample."""
-    import numpy as np
-    from workloads import config4_neutral_batch
-    progs = config4_neutral_batch(count=count)
-    arrays = [vqd.native_ops(p.ops) for p in progs]
-    ns = [p.n for p in progs]
-    units = sum(len(p.ops) * 4.0 ** p.n for p in progs)
-    bstream = torch.cuda.Stream()                          # a capturable stream: the batch becomes a CUDA graph
-    ctx = vqd.vqd_create_batch(ns, vqd.VQD_F32, bstream.cuda_stream)
-    try:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        vqd.vqd_run_batch(ctx, arrays)                       # first run: compile, plan, capture, launch
-        torch.cuda.synchronize()
-        first_wall = time.perf_counter() - t0
-        vqd.vqd_profile(ctx, 2)
-        vqd.vqd_profile_reset(ctx)
-        t0 = time.perf_counter()
-        for i in range(count):
-            vqd.vqd_init_zero(ctx, i)
-        vqd.vqd_run_batch(ctx, arrays)                       # same batch again: one graph launch
-        bstream.synchronize()
-        t1 = time.perf_counter()
-        probs, trs, purs = vqd.vqd_batch_reduce(ctx, ns)     # every instance's results, one launch, one read-back
-        wall = time.perf_counter() - t0
-        reduce_wall = time.perf_counter() - t1
-        assert np.abs(trs - 1).max() < 1e-3 and all(abs(p.sum() - 1) < 1e-3 for p in probs)
-        st = vqd.vqd_profile_read(ctx)["batch"]
-        vqd.vqd_profile(ctx, 0)
-        kern_s = st["total_ms"] * 1e-3
-        # one launch sequence per instance, on every 16th instance (all sizes represented)
-        sample = list(range(0, count, 16))
-        sunits = sum(len(progs[i].ops) * 4.0 ** progs[i].n for i in sample)
-        res = {}
-        for path in ("fused", "plain"):
-            for i in sample[:2]:
-                (vqd.vqd_run_program if path == "fused" else vqd.vqd_apply_native)(ctx, i, arrays[i])
-            torch.cuda.synchronize()
-            vqd.vqd_profile(ctx, 2)
-            vqd.vqd_profile_reset(ctx)
-            t0 = time.perf_counter()
-            for i in sample:
-                if path == "fused":
-                    vqd.vqd_run_program(ctx, i, arrays[i])
-                else:
-                    vqd.vqd_apply_native(ctx, i, arrays[i])
-            torch.cuda.synchronize()
-            w = time.perf_counter() - t0
-            ps = vqd.vqd_profile_read(ctx)
-            vqd.vqd_profile(ctx, 0)
-            kms = sum(v["total_ms"] for k, v in ps.items() if k not in ("reduce", "init"))
-            res[path] = {"value": sunits / w, "kernel_value": sunits / (kms * 1e-3),
-                         "launches": int(sum(v["launches"] for v in ps.values()))}
-        return {"value": units / wall, "unit": "amp-updates/s", "kernel_value": units / kern_s,
-                "first_run_value": units / first_wall, "first_run_s": first_wall,
-                "instances": count, "native_ops": int(sum(len(a) for a in arrays)), "amp_updates": units,
-                "kernel_s": kern_s, "wall_s": wall, "host_init_replay_s": wall - reduce_wall - kern_s,
-                "batch_reduce_s": reduce_wall,
-                "state_bytes": int(sum(vqd.vqd_state_bytes(n, vqd.VQD_F32) for n in ns)),
-                "per_instance_sample": {"instances": len(sample), **res},
-                "note": "value = wall clock of re-initialising every state, one vqd_run_batch of a batch seen "
-                        "before (one CUDA-graph launch of all stage waves) and one vqd_batch_reduce reading every "
-                        "instance's probabilities, trace and purity back to the host; first_run_value includes host compile, "
-                        "fusion planning and graph capture; kernel_value = CUDA-event time of the waves only"}
-    finally:
-        vqd.vqd_destroy(ctx)
-
 
 def device_view(torch, ptr: int, count: int, prec_f32: bool):
     """Zero-copy complex torch view of `count` amplitudes at a library device address (measurement only)."""
@@ -360,21 +504,6 @@ def device_view(torch, ptr: int, count: int, prec_f32: bool):
     return torch.view_as_complex(t.view(-1, 2))
 
 
-def fp64_alu_roof(stats, n):
-    """FP64 elementwise passes as an ALU-bound kernel: a complex phase multiply is 4 FP64 instructions per
-    amplitude it changes (2 DMUL + 2 DFMA; amplitudes with factor 1 are skipped), against 0.625e12 FP64 FMA
-    instructions/s (the GPU's nominal 1.25 TFLOP/s FP64; no measured FP64 peak is on file)."""
-    s = stats.get("elem")
-    if not s or not s.get("launches"):
-        return None
-    per_launch_s = s["total_ms"] * 1e-3 / s["launches"]
-    amps = s["alg_bytes"] / s["launches"] / 32.0        # amplitudes each launch reads and writes (16 B each way)
-    achieved = 4.0 * amps / per_launch_s
-    peak = 0.625e12
-    return {"bound": "alu", "kernel": "elem (k_diag1/k_diag2, complex factors)", "achieved": achieved, "peak": peak,
-            "unit": "FP64 instructions/s", "frac": achieved / peak, "peak_source": "nominal 1.25 TFLOP/s FP64",
-            "instructions_per_changed_amplitude": 4}
-
 
 def split_view(torch, ptr: int, count: int):
     """Zero-copy view of a float-float state as (count, 4) float32 rows: re.hi, re.lo, im.hi, im.lo."""
@@ -383,6 +512,7 @@ def split_view(torch, ptr: int, count: int):
     a = _A()
     a.__cuda_array_interface__ = {"shape": (4 * count,), "typestr": "<f4", "data": (ptr, False), "version": 3}
     return torch.as_tensor(a, device="cuda").view(-1, 4)
+
 
 
 def run_precision(args):
@@ -455,6 +585,148 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def measure_ion15(torch, vqd, stream, bf16_peak):
+    """The 15-qubit ion-trap program (800 gates: XX on random pairs and R(theta, phi), dephasing after each;
+    2000 native ops; complex64 8.6 GB): fused k-qubit blocks on the tensor cores (3xTF32 for k = 4, 5, 6 and
+    BF16x3 for k = 4) and the CUDA-core fused path, each with its error against the plain FP64 run."""
+    from workloads import config3_ion_alltoall
+    prog = config3_ion_alltoall()
+    n = prog.n
+    native = vqd.native_ops(prog.ops)
+    units = len(native) * 4.0 ** n
+    sh = stream.cuda_stream
+    out = {"workload": "ion-trap all-to-all, 15 qubits, 800 gates (2000 native ops)", "native_ops": len(native)}
+    ref = vqd.vqd_create(n, vqd.VQD_F64, sh)
+    try:
+        ms, _ = timed_steps(torch, vqd, stream, ref, make_step(vqd, ref, n, native, "plain"), 1, 0)
+        out["plain_f64"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+        runs = [("tc_3xtf32_k4", "tc", (4, 0)), ("tc_bf16x3_k4", "tc", (4, 1)), ("tc_3xtf32_k5", "tc", (5, 0)),
+                ("tc_3xtf32_k6", "tc", (6, 0)), ("fused_c64", "fused", None)]
+        for name, path, tc in runs:
+            ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
+            try:
+                step = make_step(vqd, ctx, n, native, path, tc=tc)
+                ms, _ = timed_steps(torch, vqd, stream, ctx, step, 1, 1 if path == "fused" else 0)
+                rec = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                       "error_vs_plain_f64": state_error(torch, vqd, ref, vqd.VQD_F64, ctx, vqd.VQD_F32)}
+                st = profiled_step(torch, vqd, ctx, step)
+                rec["per_class"] = per_class(st)
+                if tc:
+                    rec["blocks"] = vqd.vqd_tc_plan_info(n, native, tc[0])["blocks"]
+                    rec["roofline"] = tensor_roofline(st, n, tc[0], tc[1], bf16_peak)
+                out[name] = rec
+            finally:
+                vqd.vqd_destroy(ctx)
+                torch.cuda.empty_cache()
+    finally:
+        vqd.vqd_destroy(ref)
+    return out
+
+
+def measure_spin16(torch, vqd, stream):
+    """The 16-qubit spin chain (2000 gates, 4000 native ops), the largest single-GPU configuration: the density
+    matrix is 34.4 GB in complex64 and 68.7 GB in float-float.  Both through the fused path, once each;
+    complex64's error is stated against the float-float run (FP64-class: float-float is within 1e-13 of FP64
+    on the 14-qubit program)."""
+    from workloads import config5_spin_chain
+    prog = config5_spin_chain()
+    n = prog.n
+    native = vqd.native_ops(prog.ops)
+    units = len(native) * 4.0 ** n
+    sh = stream.cuda_stream
+    out = {"workload": "silicon-spin / NV-like chain, 16 qubits, 2000 gates (4000 native ops)", "native_ops": len(native)}
+    ref = vqd.vqd_create(n, vqd.VQD_F32_SPLIT, sh)
+    try:
+        ms, _ = timed_steps(torch, vqd, stream, ref, make_step(vqd, ref, n, native, "fused"), 1, 0)
+        out["fused_split"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                              "state_bytes": vqd.vqd_state_bytes(n, vqd.VQD_F32_SPLIT)}
+        ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
+        try:
+            step = make_step(vqd, ctx, n, native, "fused")
+            ms, _ = timed_steps(torch, vqd, stream, ctx, step, 1, 0)
+            out["fused_c64"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                "state_bytes": vqd.vqd_state_bytes(n, vqd.VQD_F32),
+                                "error_vs_fused_split": state_error(torch, vqd, ref, vqd.VQD_F32_SPLIT, ctx, vqd.VQD_F32)}
+        finally:
+            vqd.vqd_destroy(ctx)
+    finally:
+        vqd.vqd_destroy(ref)
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_batch(vqd, torch, count):
+    """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of persistent
+    kernels replayed as one CUDA graph), with the fusion width and tile shape picked by the batch autotuner
+    (candidates timed on the batch itself), against one launch sequence per instance (fused and plain) on every
+    16th instance, scaled to the batch."""
+    import numpy as np
+    from paper_2306_07342_gb300 import autotune
+    from workloads import config4_neutral_batch
+    progs = config4_neutral_batch(count=count)
+    arrays = [vqd.native_ops(p.ops) for p in progs]
+    ns = [p.n for p in progs]
+    units = sum(len(p.ops) * 4.0 ** p.n for p in progs)
+    bstream = torch.cuda.Stream()                          # a capturable stream: the batch becomes a CUDA graph
+    choice = autotune.tune_batch(ns, vqd.VQD_F32, arrays, bstream.cuda_stream)
+    ctx = vqd.vqd_create_batch(ns, vqd.VQD_F32, bstream.cuda_stream)
+    try:
+        fuse = autotune.apply(ctx, choice)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vqd.vqd_run_batch(ctx, arrays, fuse)                 # first run: compile, plan, capture, launch
+        torch.cuda.synchronize()
+        first_wall = time.perf_counter() - t0
+        vqd.vqd_profile(ctx, 2)
+        vqd.vqd_profile_reset(ctx)
+        t0 = time.perf_counter()
+        for i in range(count):
+            vqd.vqd_init_zero(ctx, i)
+        vqd.vqd_run_batch(ctx, arrays, fuse)                 # same batch again: one graph launch
+        bstream.synchronize()
+        t1 = time.perf_counter()
+        probs, trs, purs = vqd.vqd_batch_reduce(ctx, ns)     # every instance's results, one launch, one read-back
+        wall = time.perf_counter() - t0
+        reduce_wall = time.perf_counter() - t1
+        assert np.abs(trs - 1).max() < 1e-3 and all(abs(p.sum() - 1) < 1e-3 for p in probs)
+        st = vqd.vqd_profile_read(ctx)["batch"]
+        vqd.vqd_profile(ctx, 0)
+        kern_s = st["total_ms"] * 1e-3
+        sample = list(range(0, count, 16))
+        sunits = sum(len(progs[i].ops) * 4.0 ** progs[i].n for i in sample)
+        res = {}
+        for path in ("fused", "plain"):
+            for i in sample[:2]:
+                (vqd.vqd_run_program if path == "fused" else vqd.vqd_apply_native)(ctx, i, arrays[i])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in sample:
+                if path == "fused":
+                    vqd.vqd_run_program(ctx, i, arrays[i], fuse)
+                else:
+                    vqd.vqd_apply_native(ctx, i, arrays[i])
+            torch.cuda.synchronize()
+            w = time.perf_counter() - t0
+            res[path] = {"value": sunits / w, "scaled_batch_s": w * units / sunits}
+        return {"value": units / wall, "unit": UNIT, "kernel_value": units / kern_s,
+                "first_run_value": units / first_wall, "first_run_s": first_wall,
+                "instances": count, "native_ops": int(sum(len(a) for a in arrays)), "amp_updates": units,
+                "kernel_s": kern_s, "wall_s": wall, "batch_reduce_s": reduce_wall,
+                "autotuned": {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")},
+                "autotune_trials": choice["trials"],
+                "state_bytes": int(sum(vqd.vqd_state_bytes(n, vqd.VQD_F32) for n in ns)),
+                "one_launch_sequence_per_instance": {
+                    "instances_timed": len(sample), **res,
+                    "note": "every 16th instance timed one launch sequence after another; value = their amp-updates "
+                            "over their wall clock, scaled_batch_s = that rate applied to the whole batch"},
+                "note": "value = wall clock of re-initialising every state, one vqd_run_batch of a batch seen before "
+                        "(one CUDA-graph launch of all stage waves) and one vqd_batch_reduce reading every instance's "
+                        "probabilities, trace and purity back to the host; first_run_value includes host compile, "
+                        "fusion planning and graph capture; kernel_value = CUDA-event time of the waves only"}
+    finally:
+        vqd.vqd_destroy(ctx)
+
+
 def run_fp64_diag():
     """FP64 elementwise passes on a 14-qubit complex128 state: a real diagonal superoperator that changes every
     amplitude, a dephasing and an Rz (both leave half of the amplitudes untouched); 20 timed passes each after 3
@@ -471,7 +743,7 @@ def run_fp64_diag():
     cases = {"real_full": lambda: vqd.vqd_apply_superop(ctx, 0, [7], real),
              "deph_half": lambda: vqd.vqd_apply_native(ctx, 0, [NativeOp("deph1", (7,), (0.1,))]),
              "rz_complex_half": lambda: vqd.vqd_apply_native(ctx, 0, [NativeOp("rz", (7,), (0.3,))])}
-    out = {}
+    out = {"fp64_fma_per_s": vqd.vqd_measure_fma_rate(0), "fp32_fma_per_s": vqd.vqd_measure_fma_rate(1)}
     try:
         for name, f in cases.items():
             for _ in range(3):
@@ -499,6 +771,9 @@ def main():
     if args.precision:
         run_precision(args)
         return
+    if args.oracle_plan:
+        run_oracle_plan(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -515,7 +790,7 @@ def main():
         _b.build()
     if world > 1:
         torch.distributed.barrier()
-    from paper_2306_07342_gb300 import vqd
+    from paper_2306_07342_gb300 import autotune, replicas, vqd
     from workloads import config2_sc_grid
 
     prog = config2_sc_grid(rows=args.rows, cols=args.cols, depth=args.depth)
@@ -529,173 +804,159 @@ def main():
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
-    from paper_2306_07342_gb300 import replicas
 
     def sync_all():
         torch.cuda.synchronize()
         replicas.barrier()
 
-    max_over_ranks = replicas.max_over_ranks
+    prec = {"split": vqd.VQD_F32_SPLIT, "f64": vqd.VQD_F64, "f32": vqd.VQD_F32}[args.prec]
+    layer_ops = len(prog.ops) // prog.meta["depth"]
 
-    def make_step(ctx, path, ops=native):
-        def step():
-            vqd.vqd_init_zero(ctx, 0)
-            if path == "plain":
-                vqd.vqd_apply_native(ctx, 0, ops)
-            else:
-                vqd.vqd_run_program(ctx, 0, ops)
-            vqd.vqd_prob(ctx, 0, list(range(n)))
-            vqd.vqd_trace(ctx, 0)
-            vqd.vqd_purity(ctx, 0)
-        return step
+    # ---- headline: the FP64-class fused path (float-float) on the full program
+    ctx = vqd.vqd_create(n, prec, sh)
+    fuse = 0
+    choice = None
+    if args.path == "fused":
+        choice = autotune.tune(n, prec, native, sh, prefix=3 * layer_ops)   # outside the timed region
+        fuse = autotune.apply(ctx, choice)
+    step = make_step(vqd, ctx, n, native, args.path, fuse)
+    clocks = ClockSampler(local)
+    ms, ck = timed_steps(torch, vqd, stream, ctx, step, args.steps, args.warmup, clocks, sync_all)
+    ms = replicas.max_over_ranks(ms)
+    value = world * args.steps * units_per_step / (ms * 1e-3)
+    stats = profiled_step(torch, vqd, ctx, step)                         # per-class times, outside the timed region
+    roof = roofline_hbm(stats, hbm_peak, peak_src)
+    launches = int(sum(v["launches"] for v in stats.values()))
 
-    def timed(step, steps, warmup, ctx, clocks=None):
+    # ---- end to end through the C ABI with host buffers (wall clock; results read back every step)
+    e2e_steps = min(args.steps, 5)
+    sync_all()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step()
+    torch.cuda.synchronize()
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * e2e_steps * units_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(native.nbytes), "d2h_bytes_per_step": int(8 * 2 ** n + 16 + 8), "steps": e2e_steps,
+           "note": "wall clock through vqd_init_zero/vqd_run_program/vqd_prob/vqd_trace/vqd_purity; the native op "
+                   "list is a host array compiled and marshalled every step; results copied to host every step"}
+
+    extra, error = {}, None
+    fp64_fma = vqd.vqd_measure_fma_rate(0, sh)
+    fp32_fma = vqd.vqd_measure_fma_rate(1, sh)
+    if not args.no_extra:
+        # ---- the plain FP64 path on the full program: the reference state for every error below
+        ref = vqd.vqd_create(n, vqd.VQD_F64, sh)
+        rstep = make_step(vqd, ref, n, native[:layer_ops], "plain")
+        rstep()                                                           # warm-up on the first layer
+        rms, _ = timed_steps(torch, vqd, stream, ref, make_step(vqd, ref, n, native, "plain"), 1, 0)
+        st64 = profiled_step(torch, vqd, ref, make_step(vqd, ref, n, native[:2 * layer_ops], "plain"))
+        vqd.vqd_init_zero(ref, 0)
+        vqd.vqd_apply_native(ref, 0, native)
+        f64_rate = units_per_step / (rms * 1e-3)
+        extra["plain_f64"] = {
+            "value": world * f64_rate, "unit": UNIT, "ms_per_step": rms,
+            "roofline_hbm": roofline_hbm(st64, hbm_peak, peak_src),
+            "per_class_first_two_layers": per_class(st64),
+            "fp64_fma_per_s_measured": fp64_fma, "fp32_fma_per_s_measured": fp32_fma,
+            "note": "complex128 plain kernels (one pass per native op), the full program; per-class times from a "
+                    "profiled pass over the first two layers"}
+        error = state_error(torch, vqd, ref, vqd.VQD_F64, ctx, prec)
+        error["vs"] = "plain FP64 (complex128) run of the same program on the same GPU"
+        # ---- the other paths on the full program, each with its error against the FP64 state
+        paths = [("fused_f64", vqd.VQD_F64, "fused", 1), ("plain_split", vqd.VQD_F32_SPLIT, "plain", 1),
+                 ("fused_c64", vqd.VQD_F32, "fused", min(args.steps, 5)), ("plain_c64", vqd.VQD_F32, "plain", 2)]
+        for name, pp, path, nsteps in paths:
+            if pp == prec and path == args.path:
+                continue
+            c2 = vqd.vqd_create(n, pp, sh)
+            try:
+                f2 = 0
+                tuned = None
+                if path == "fused" and pp == vqd.VQD_F32:
+                    tuned = autotune.tune(n, pp, native, sh, prefix=10 * layer_ops)
+                    f2 = autotune.apply(c2, tuned)
+                s2 = make_step(vqd, c2, n, native, path, f2)
+                ms2, _ = timed_steps(torch, vqd, stream, c2, s2, nsteps, 1 if nsteps > 1 else 0)
+                rec = {"value": world * nsteps * units_per_step / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / nsteps,
+                       "steps": nsteps, "error_vs_plain_f64": state_error(torch, vqd, ref, vqd.VQD_F64, c2, pp)}
+                rec["speedup_vs_plain_f64"] = rec["value"] / (world * f64_rate)
+                if tuned:
+                    rec["autotuned"] = {k: tuned[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")}
+                if path == "fused":
+                    st2 = profiled_step(torch, vqd, c2, s2)
+                    rec["roofline"] = roofline_hbm(st2, hbm_peak, peak_src)
+                    rec["stages_per_step"] = st2.get("fused_stage", {}).get("launches", 0)
+                extra[name] = rec
+            finally:
+                vqd.vqd_destroy(c2)
+        vqd.vqd_destroy(ref)
+        torch.cuda.empty_cache()
+    headline_rec = {"speedup_vs_plain_f64": (value / extra["plain_f64"]["value"]) if "plain_f64" in extra else None}
+    if choice:
+        headline_rec["autotuned"] = {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")}
+    vqd.vqd_destroy(ctx)
+    torch.cuda.empty_cache()
+
+    if not args.no_extra and not args.no_large:
+        extra["ion15_tensor_core"] = measure_ion15(torch, vqd, stream, bf16_peak)
+        extra["spin16"] = measure_spin16(torch, vqd, stream)
+    if not args.no_extra:
+        extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
+        extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed_legacy(torch, vqd, stream), 3)
+        extra["trajectories_spin16_c64"] = measure_trajectories_spin16(vqd, sh)
+        extra["nv5_noise_sweep_batch_c64"] = measure_nv_noise_sweep(vqd, torch)
+        if args.batch_count > 0:
+            extra["batch_c64"] = measure_batch(vqd, torch, args.batch_count)
+
+    cpu = None
+    if rank == 0 and not args.no_extra:
+        blk = cpu_baseline_block(quick=True)
+        grid_all = next(l for l in blk["lines"] if l["config"].startswith("sc_grid14") and l["threads"] > 1)
+        cpu = {"value": grid_all["value"], "unit": UNIT, "cores": grid_all["threads"], "kind": "oracle",
+               "sample": f"first {grid_all['ops_timed']} native ops of the 14-qubit program at full size, FP64 oracle "
+                         f"(plain C loops, {grid_all['threads']} threads), {grid_all['seconds']:.1f} s",
+               "lines": blk["lines"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[args.prec], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": n, "native_ops": len(prog.ops),
+                       "path": f"{args.path} ({'float-float pairs' if args.prec == 'split' else args.prec})",
+                       "state_bytes": vqd.vqd_state_bytes(n, prec),
+                       "l2": "inputs larger than L2 (state of 2.1-4.3 GB vs 129 MB L2), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "error": error, "headline": headline_rec,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": ck, "paths": extra, "per_class": per_class(stats),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def timed_legacy(torch, vqd, stream):
+    """Timer with the per-class accounting of the side workloads: (ms, stats, None)."""
+    def timed(step, steps, warmup, ctx):
         for _ in range(warmup):
             step()
-        vqd.vqd_profile(ctx, 0)
+        torch.cuda.synchronize()
+        vqd.vqd_profile(ctx, 1)
         vqd.vqd_profile_reset(ctx)
-        vqd.vqd_profile(ctx, 2)
-        sync_all()
-        if clocks:
-            clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ck = clocks.stop() if clocks else None
-        ms = max_over_ranks(e0.elapsed_time(e1))
-        stats = vqd.vqd_profile_read(ctx)
+        st = vqd.vqd_profile_read(ctx)
         vqd.vqd_profile(ctx, 0)
-        return ms, stats, ck
-
-    def roofline(stats, steps):
-        kern = {k: v for k, v in stats.items() if k not in ("reduce", "init")}
-        dom = max(kern, key=lambda k: kern[k]["total_ms"])
-        s = kern[dom]
-        per_launch_bytes = s["alg_bytes"] / s["launches"]
-        avg_ms = s["total_ms"] / s["launches"]
-        achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-        total_ms = sum(v["total_ms"] for v in stats.values())
-        return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": load_traffic(dom), "kernel": dom,
-                     "peak_source": peak_src, "launches": s["launches"] // max(1, steps),
-                     "share_of_kernel_time": s["total_ms"] / total_ms if total_ms else None,
-                     "alg_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms}
-
-    # ---- headline: plain complex64 kernels
-    ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
-    clocks = ClockSampler(local)
-    ms, stats, ck = timed(make_step(ctx, args.path), args.steps, args.warmup, ctx, clocks)
-    value = world * args.steps * units_per_step / (ms * 1e-3)
-    dom, roof = roofline(stats, args.steps)
-    launches = int(sum(v["launches"] for v in stats.values()) / args.steps)
-
-    # ---- end to end through the C ABI with host buffers (wall clock; results read back every step)
-    step = make_step(ctx, args.path)
-    sync_all()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * args.steps * units_per_step / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(native.nbytes), "d2h_bytes_per_step": int(8 * 2 ** n + 16 + 8),
-           "note": "wall clock through vqd_init_zero/vqd_apply_native/vqd_prob/vqd_trace/vqd_purity; the native "
-                   "op list is a host array marshalled into kernel parameters; results copied to host every step"}
-
-    extra = {}
-    if not args.no_extra:
-        # ---- fused path, complex64, with the autotuned fusion width and tile shape (tuned on the first
-        # 10 layers, outside the timed region)
-        from paper_2306_07342_gb300 import autotune
-        layer_ops = len(prog.ops) // prog.meta["depth"]
-        choice = autotune.tune(n, vqd.VQD_F32, native, sh, prefix=10 * layer_ops)
-        fuse = autotune.apply(ctx, choice)
-
-        def fused_step():
-            vqd.vqd_init_zero(ctx, 0)
-            vqd.vqd_run_program(ctx, 0, native, fuse)
-            vqd.vqd_prob(ctx, 0, list(range(n)))
-            vqd.vqd_trace(ctx, 0)
-            vqd.vqd_purity(ctx, 0)
-
-        fms, fstats, _ = timed(fused_step, args.steps, 1, ctx)
-        fdom, froof = roofline(fstats, args.steps)
-        extra["fused_c64"] = {"value": world * args.steps * units_per_step / (fms * 1e-3), "unit": UNIT,
-                              "ms_per_step": fms / args.steps, "speedup_vs_plain": ms / fms,
-                              "stages_per_step": fstats.get("fused_stage", {}).get("launches", 0) // args.steps,
-                              "autotuned": {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")},
-                              "roofline": froof}
-    vqd.vqd_destroy(ctx)
-    if not args.no_extra:
-        # ---- plain FP64 (complex128) kernels on the first two layers of the program
-        layer_ops = len(prog.ops) // prog.meta["depth"]
-        sample = native[:2 * layer_ops]
-        ctx64 = vqd.vqd_create(n, vqd.VQD_F64, sh)
-        dms, dstats, _ = timed(make_step(ctx64, "plain", sample), 1, 1, ctx64)
-        ddom, droof = roofline(dstats, 1)
-        kern_ms = sum(v["total_ms"] for k, v in dstats.items() if k not in ("reduce", "init"))
-        fp64_rate = len(sample) * 4.0 ** n / (kern_ms * 1e-3)
-        droof["bound"] = "alu" if ddom in ("sup1", "uni2", "sup2") else "hbm"
-        # the same sample through the fused path in FP64
-        fms64, fst64, _ = timed(make_step(ctx64, "fused", sample), 1, 1, ctx64)
-        fk64 = sum(v["total_ms"] for k, v in fst64.items() if k not in ("reduce", "init"))
-        extra["fused_f64_sample"] = {"value": world * len(sample) * 4.0 ** n / (fk64 * 1e-3), "unit": UNIT,
-                                     "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
-                                     "stages": fst64.get("fused_stage", {}).get("launches", 0)}
-        extra["plain_f64_sample"] = {"value": world * fp64_rate, "unit": UNIT,
-                                     "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
-                                     "roofline_hbm": droof,
-                                     "roofline_fp64_alu": fp64_alu_roof(dstats, n),
-                                     "per_class": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"]}
-                                                   for k, v in dstats.items()}}
-        vqd.vqd_destroy(ctx64)
-        # ---- the same sample with float-float storage (FP64-class accuracy on the FP32 pipes)
-        ctxs = vqd.vqd_create(n, vqd.VQD_F32_SPLIT, sh)
-        for path in ("plain", "fused"):
-            tms, tst, _ = timed(make_step(ctxs, path, sample), 1, 1, ctxs)
-            kms = sum(v["total_ms"] for k, v in tst.items() if k not in ("reduce", "init"))
-            extra[f"{path}_split_sample"] = {
-                "value": world * len(sample) * 4.0 ** n / (kms * 1e-3), "unit": UNIT,
-                "sample": f"first 2 of 60 layers ({len(sample)} native ops), kernel time only",
-                "vs_f64_plain": (len(sample) * 4.0 ** n / (kms * 1e-3)) / fp64_rate}
-        vqd.vqd_destroy(ctxs)
-
-    if not args.no_extra:
-        extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
-        extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed, args.steps)
-        extra["trajectories_spin16_c64"] = measure_trajectories_spin16(vqd, sh)
-        extra["nv5_noise_sweep_batch_c64"] = measure_nv_noise_sweep(vqd, torch)
-
-    if not args.no_extra and args.batch_count > 0:
-        extra["batch_c64"] = measure_batch(vqd, torch, sh, args.batch_count)
-
-    cpu = None
-    if rank == 0 and not args.no_extra:
-        rate, dt = oracle_rate(prog, 2)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"first 2 native ops of the 14-qubit program at full size, FP64 numpy, {dt:.1f} s"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": n, "native_ops": len(prog.ops), "state_bytes": 8 * 4 ** n,
-                       "l2": "inputs larger than L2 (2.15 GB state vs 129 MB L2), no flush",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": ck, "paths": extra,
-            "per_class": {k: {"launches": v["launches"] // args.steps, "avg_ms": v["total_ms"] / v["launches"]}
-                          for k, v in stats.items()},
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+        return e0.elapsed_time(e1), st, None
+    return timed
 
 
 if __name__ == "__main__":

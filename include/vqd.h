@@ -565,6 +565,14 @@ int vqd_prob_static(const void* dev_state, int n, int prec, int m, const int* qu
                     void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Arithmetic peak of this GPU (the paper has no counterpart: it is the denominator of the roofline of
+ * the kernels bound by FP64 or FP32 arithmetic rather than by memory).  which = 0: FP64 FMA, 1: FP32
+ * FMA.  Times one launch of independent FMA chains on every SM (CUDA events on `stream`, a cudaStream_t)
+ * and returns the FMA instructions per second (2 flops each).  Synchronous; allocates and frees 8 bytes.
+ * ---------------------------------------------------------------------------------------- */
+int vqd_measure_fma_rate(int which, void* stream, double* fma_per_s);
+
+/* ------------------------------------------------------------------------------------------
  * Launch accounting: per kernel class, the number of launches, their summed device time
  * (CUDA events recorded on the context stream around every launch while enabled) and the
  * algorithmic bytes they move.  Used to report achieved bandwidth against the roofline.

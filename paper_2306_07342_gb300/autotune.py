@@ -1,4 +1,4 @@
-"""Autotuner of the fused path: fusion width and tile shape, picked by timing candidates.
+"""Autotuner of the fused and batched paths: fusion width and tile shape, picked by timing candidates.
 
 A candidate is (fuse_qubits, tile_bits, passenger_bits). The tuner runs a prefix of the program
 through ``vqd_run_program`` on a scratch state of the same size, for every candidate. It times the
@@ -19,7 +19,14 @@ from . import vqd
 
 CANDIDATES = {
     vqd.VQD_F32: [(f, tb, p) for f in (4, 5, 6) for (tb, p) in ((13, 3), (13, 2), (12, 2))],
-    vqd.VQD_F64: [(f, tb, p) for f in (4, 5, 6) for (tb, p) in ((12, 2), (12, 1), (11, 1))],
+    vqd.VQD_F64: [(f, tb, p) for f in (5, 6) for (tb, p) in ((12, 2), (12, 1), (11, 1))],
+    vqd.VQD_F32_SPLIT: [(f, tb, p) for f in (5, 6) for (tb, p) in ((12, 2), (12, 1), (11, 1))],
+}
+# The batched path: whole batches are timed, so fewer candidates (fusion width x tile shape).
+BATCH_CANDIDATES = {
+    vqd.VQD_F32: [(6, 13, 3), (5, 13, 3), (6, 12, 2), (4, 13, 3)],
+    vqd.VQD_F64: [(6, 12, 2), (5, 12, 2), (6, 11, 1)],
+    vqd.VQD_F32_SPLIT: [(6, 12, 2), (5, 12, 2), (6, 11, 1)],
 }
 
 
@@ -66,6 +73,30 @@ def tune(n: int, prec: int, ops, stream: int = 0, prefix: int = 0, candidates: O
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return result
+
+
+def tune_batch(ns, prec: int, arrays, stream: int = 0, candidates: Optional[Iterable] = None) -> dict:
+    """Fastest (fuse_qubits, tile_bits, passenger_bits) for a batch of programs (one per instance, n qubits
+    each): every candidate runs the whole batch once (planning and graph capture) and is then timed on a
+    replay of its CUDA graph with the library's CUDA-event accounting of the batch waves."""
+    cands = list(candidates) if candidates is not None else BATCH_CANDIDATES[prec]
+    ctx = vqd.vqd_create_batch(list(ns), prec, stream)
+    trials = []
+    try:
+        for f, tb, p in cands:
+            vqd.vqd_set_tile_shape(ctx, tb, p)
+            vqd.vqd_run_batch(ctx, arrays, f)            # plan, capture
+            vqd.vqd_sync(ctx)
+            vqd.vqd_profile(ctx, 2)
+            vqd.vqd_profile_reset(ctx)
+            vqd.vqd_run_batch(ctx, arrays, f)            # replay
+            st = vqd.vqd_profile_read(ctx).get("batch", {"total_ms": 0.0, "launches": 0})
+            vqd.vqd_profile(ctx, 0)
+            trials.append({"fuse_qubits": f, "tile_bits": tb, "passenger_bits": p, "ms": st["total_ms"]})
+    finally:
+        vqd.vqd_destroy(ctx)
+    best = min(trials, key=lambda t: t["ms"])
+    return dict(best, trials=trials)
 
 
 def apply(ctx, choice: dict) -> int:

@@ -702,6 +702,50 @@ void batch_reduce_items(const std::vector<int>& n, const std::vector<size_t>& of
   }
 }
 
+// ================================================================== arithmetic peak probe
+namespace dev {
+// Eight independent FMA chains per thread (enough to cover the pipe latency), many warps per SM.
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* __restrict__ sink, int iters, T seed) {
+  T a[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) a[i] = seed + (T)(i + threadIdx.x) * (T)1e-3;
+  const T m = (T)0.9999999, c = (T)1e-7;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) a[i] = fma(a[i], m, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) s += a[i];
+  if (s == (T)-1) sink[0] = s;  // never true; keeps the chains live
+}
+}  // namespace dev
+
+template <class T>
+static cudaError_t fma_probe_t(cudaStream_t s, double* out) {
+  T* sink = nullptr;  // never written (the kernel's condition is false); a valid address is still passed
+  cudaError_t e = cudaMalloc(&sink, sizeof(T));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int iters = sizeof(T) == 8 ? 4096 : 65536;
+  const unsigned grid = 8u * num_sms();
+  dev::k_fma_probe<T><<<grid, 256, 0, s>>>(sink, 256, (T)1);  // warm-up
+  cudaEventRecord(a, s);
+  dev::k_fma_probe<T><<<grid, 256, 0, s>>>(sink, iters, (T)1);
+  cudaEventRecord(b, s);
+  e = cudaEventSynchronize(b);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (e == cudaSuccess) *out = (double)grid * 256.0 * iters * 8.0 / (ms * 1e-3);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  return e;
+}
+
 // ================================================================== allocation-free probabilities
 // vqd_prob_static: the marginal-probability reduction with its partial sums in a file-scope device
 // array instead of memory from cudaMalloc.  Every GPU that loads the library holds this array
@@ -748,6 +792,18 @@ static cudaError_t prob_static_t(const cx<T>* st, int n, int m, const int* qubit
 }
 
 }  // namespace vqd
+
+extern "C" int vqd_measure_fma_rate(int which, void* stream, double* fma_per_s) {
+  using namespace vqd;
+  if (!fma_per_s || (which != 0 && which != 1)) return report_static_error(VQD_EINVAL, "vqd_measure_fma_rate: bad argument");
+  cudaError_t e = which == 0 ? fma_probe_t<double>((cudaStream_t)stream, fma_per_s)
+                             : fma_probe_t<float>((cudaStream_t)stream, fma_per_s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return report_static_error(VQD_EDEVICE, cudaGetErrorString(e));
+  }
+  return VQD_OK;
+}
 
 extern "C" int vqd_prob_static(const void* dev_state, int n, int prec, int m, const int* qubits, double* dev_out,
                                void* stream) {

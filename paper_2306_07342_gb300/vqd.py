@@ -166,6 +166,7 @@ def lib() -> ctypes.CDLL:
             "vqd_na_compile": (I, [P, I, P, I, I, I, P, P]),
             "vqd_traj_expect": (I, [I, I, I, P, U, I, ctypes.c_uint64, I, P, P, P, P, P, P]),
             "vqd_run_program_tc": (I, [P, I, I, P, I, I, U]),
+            "vqd_measure_fma_rate": (I, [I, P, P]),
             "vqd_tc_plan_info": (I, [I, I, P, I, U, P]),
         }
         for name, (res, args) in sig.items():
@@ -298,6 +299,13 @@ def vqd_run_program_tc(ctx, inst: int, ops, k: int = 4, scheme: int = VQD_TC_3XT
     """Fused k-qubit blocks applied as split-precision GEMMs on the tensor cores (complex64 contexts)."""
     a = ops if isinstance(ops, np.ndarray) else native_ops(ops)
     _check(lib().vqd_run_program_tc(ctx, inst, len(a), _ptr(a), k, scheme, flags), ctx)
+
+
+def vqd_measure_fma_rate(which: int, stream: int = 0) -> float:
+    """FMA instructions per second of this GPU: which = 0 for FP64, 1 for FP32 (synchronous)."""
+    out = ctypes.c_double()
+    _check(lib().vqd_measure_fma_rate(which, ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
 
 
 def vqd_tc_plan_info(n: int, ops, k: int = 4, flags: int = 0) -> dict:
