@@ -797,11 +797,11 @@ __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, cons
       for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
 #pragma unroll
       for (int t = 0; t < 4; t++) {
-        cx<T> y;
-        y.x = 0; y.y = 0;
+        CAcc<T> y;
+        y.zero();
 #pragma unroll
-        for (int u = 0; u < 4; u++) cmac_flag<T>(y, c[t * 4 + u], fl[t * 4 + u], x[u]);
-        sm[a[t]] = y;
+        for (int u = 0; u < 4; u++) y.mac(c[t * 4 + u], fl[t * 4 + u], x[u]);
+        sm[a[t]] = y.get();
       }
     }
   }
@@ -840,11 +840,11 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
         for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[m | (cc << 2)]];
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-          cx<T> t;
-          t.x = 0; t.y = 0;
+          CAcc<T> t;
+          t.zero();
 #pragma unroll
-          for (int m = 0; m < 4; m++) cmac_flag<T>(t, c[r * 4 + m], fl[r * 4 + m], x[m]);
-          sm[b ^ soff[r | (cc << 2)]] = t;
+          for (int m = 0; m < 4; m++) t.mac(c[r * 4 + m], fl[r * 4 + m], x[m]);
+          sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
       }
 #pragma unroll 1
@@ -854,15 +854,15 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
         for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[r | (m << 2)]];
 #pragma unroll
         for (int cc = 0; cc < 4; cc++) {
-          cx<T> t;
-          t.x = 0; t.y = 0;
+          CAcc<T> t;
+          t.zero();
 #pragma unroll
           for (int m = 0; m < 4; m++) {
             cx<T> uc = c[cc * 4 + m];
             uc.y = -uc.y;
-            cmac_flag<T>(t, uc, fl[cc * 4 + m], x[m]);
+            t.mac(uc, fl[cc * 4 + m], x[m]);
           }
-          sm[b ^ soff[r | (cc << 2)]] = t;
+          sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
       }
     } else {
@@ -871,15 +871,15 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
       for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
 #pragma unroll 1
       for (int i = 0; i < 16; i++) {
-        cx<T> y;
-        y.x = 0; y.y = 0;
+        CAcc<T> y;
+        y.zero();
 #pragma unroll
-        for (int j = 0; j < 16; j++) cmac_flag<T>(y, c[i * 16 + j], fl[i * 16 + j], x[j]);
+        for (int j = 0; j < 16; j++) y.mac(c[i * 16 + j], fl[i * 16 + j], x[j]);
         uint32_t o = 0;
 #pragma unroll
         for (int j = 0; j < 4; j++)
           if (i >> j & 1) o |= 1u << B.lbit[j];
-        sm[b ^ sw<T>(o)] = y;
+        sm[b ^ sw<T>(o)] = y.get();
       }
     }
   }

@@ -110,6 +110,74 @@ __device__ __forceinline__ void cscale_flag(cx<T>& x, const cx<T>& f, int fl) {
   x.x = re;
 }
 
+// Accumulator of a complex sum of products sum_j c_j x_j.  For float and double it is the complex value
+// itself (one FMA per real product).  For float-float it keeps, per real and imaginary part, a running
+// float sum s whose rounding errors (Knuth two-sum) and the products' low parts (exact FMA residue and
+// the cross terms with the low words) are gathered in a second float l, normalised once at the end:
+// the compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 2005), as accurate
+// as a float-float evaluation, with one float add on the critical path per term instead of a
+// renormalisation after every term.
+template <class T>
+struct CAcc {
+  cx<T> v;
+  __device__ __forceinline__ void zero() { v.x = T(0.0f); v.y = T(0.0f); }
+  __device__ __forceinline__ void mac(const cx<T>& c, int fl, const cx<T>& x) { cmac_flag<T>(v, c, fl, x); }
+  __device__ __forceinline__ cx<T> get() const { return v; }
+};
+
+__device__ __forceinline__ void dot2_step(float& s, float& l, const df& a, const df& b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s2 = s + p;
+  const float v = s2 - s;
+  const float err = (s - (s2 - v)) + (p - v);
+  s = s2;
+  l = l + (err + e);
+}
+__device__ __forceinline__ void dot2_add(float& s, float& l, const df& a) {
+  const float s2 = s + a.hi;
+  const float v = s2 - s;
+  const float err = (s - (s2 - v)) + (a.hi - v);
+  s = s2;
+  l = l + (err + a.lo);
+}
+
+template <>
+struct CAcc<df> {
+  float rs, rl, is, il;
+  __device__ __forceinline__ void zero() { rs = rl = is = il = 0.0f; }
+  __device__ __forceinline__ void mac(const cdf& c, int fl, const cdf& x) {
+    if (fl == FL_ZERO) return;
+    if (fl == FL_ONE) {
+      dot2_add(rs, rl, x.x);
+      dot2_add(is, il, x.y);
+      return;
+    }
+    if (fl == FL_REAL) {
+      dot2_step(rs, rl, c.x, x.x);
+      dot2_step(is, il, c.x, x.y);
+      return;
+    }
+    if (fl == FL_IMAG) {
+      dot2_step(rs, rl, -c.y, x.y);
+      dot2_step(is, il, c.y, x.x);
+      return;
+    }
+    dot2_step(rs, rl, c.x, x.x);
+    dot2_step(rs, rl, -c.y, x.y);
+    dot2_step(is, il, c.x, x.y);
+    dot2_step(is, il, c.y, x.x);
+  }
+  __device__ __forceinline__ cdf get() const {
+    cdf r;
+    r.x = df_fast_two_sum(rs, rl);
+    r.y = df_fast_two_sum(is, il);
+    return r;
+  }
+};
+
 }  // namespace dev
 
 // Host-side structure of a coefficient (FL_*), for the structured kernels.
