@@ -265,6 +265,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
     }
 #pragma unroll
     for (int i = 0; i < kNT; i++) sum[i] = 0.f;
+    // the chunk's 8 members of group g, loaded one chunk ahead so that the loads are in flight while the
+    // previous chunk is stored, multiplied and read out
+    float2 vcur[kKc / 2], vnext[kKc / 2];
+#pragma unroll
+    for (int e = 0; e < kKc / 2; e++) vcur[e] = valid ? X[base + s_off[e]] : make_float2(0.f, 0.f);
     for (int kc = 0; kc < P.n_kchunks; kc++) {
       const int st = kc % kStages, slot = kc & 1;
       // stage st and slot were last used by chunk kc - 2, read out (so complete) in the previous iteration
@@ -278,22 +283,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
           tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), bar);
         }
       }
-      // gather this chunk's 8 members of group g, split into limbs, K-major rows
-      const int m0 = kc * (kKc / 2);
-      Limbs<SCHEME> lre[kKc / 2] = {Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f),
-                                    Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f)};
-      Limbs<SCHEME> lim[kKc / 2] = {Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f),
-                                    Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f), Limbs<SCHEME>(0.f)};
-      if (valid) {
-        float2 v[kKc / 2];
+      // next chunk's members (in flight until the next iteration), this chunk's split into limbs, K-major rows
+      if (kc + 1 < P.n_kchunks) {
+        const int m1 = (kc + 1) * (kKc / 2);
 #pragma unroll
-        for (int e = 0; e < kKc / 2; e++) v[e] = X[base + s_off[m0 + e]];
-#pragma unroll
-        for (int e = 0; e < kKc / 2; e++) {
-          lre[e] = Limbs<SCHEME>(v[e].x);
-          lim[e] = Limbs<SCHEME>(v[e].y);
-        }
+        for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[m1 + e]] : make_float2(0.f, 0.f);
       }
+      Limbs<SCHEME> lre[kKc / 2] = {Limbs<SCHEME>(vcur[0].x), Limbs<SCHEME>(vcur[1].x), Limbs<SCHEME>(vcur[2].x),
+                                    Limbs<SCHEME>(vcur[3].x), Limbs<SCHEME>(vcur[4].x), Limbs<SCHEME>(vcur[5].x),
+                                    Limbs<SCHEME>(vcur[6].x), Limbs<SCHEME>(vcur[7].x)};
+      Limbs<SCHEME> lim[kKc / 2] = {Limbs<SCHEME>(vcur[0].y), Limbs<SCHEME>(vcur[1].y), Limbs<SCHEME>(vcur[2].y),
+                                    Limbs<SCHEME>(vcur[3].y), Limbs<SCHEME>(vcur[4].y), Limbs<SCHEME>(vcur[5].y),
+                                    Limbs<SCHEME>(vcur[6].y), Limbs<SCHEME>(vcur[7].y)};
 #pragma unroll
       for (int l = 0; l < Sc::limbs; l++) {
         unsigned char* at = a_tile(st, l);
@@ -340,6 +341,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
       tma_par[st] ^= 1u;
       acc_pend[slot] = true;
       if (kc > 0) readout(slot ^ 1);
+#pragma unroll
+      for (int e = 0; e < kKc / 2; e++) vcur[e] = vnext[e];
     }
     if (!ok) break;
     if (acc_pend[(P.n_kchunks - 1) & 1]) readout((P.n_kchunks - 1) & 1);
