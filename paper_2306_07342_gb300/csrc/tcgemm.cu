@@ -270,19 +270,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
     float2 vcur[kKc / 2], vnext[kKc / 2];
 #pragma unroll
     for (int e = 0; e < kKc / 2; e++) vcur[e] = valid ? X[base + s_off[e]] : make_float2(0.f, 0.f);
+    // R's chunks are loaded one chunk ahead: chunk kc + 1 as soon as chunk kc - 1's products are complete
+    auto load_r = [&](int kc) {
+      const int st = kc % kStages;
+      const uint32_t bar = su32(&s_bar[st]);
+      mbar_expect_tx(bar, stage_tx);
+      for (int l = 0; l < Sc::limbs; l++) {
+        const int blk = (nt * P.n_kchunks + kc) * Sc::limbs + l;
+        tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), bar);
+      }
+    };
+    if (tid == 0) load_r(0);
     for (int kc = 0; kc < P.n_kchunks; kc++) {
       const int st = kc % kStages, slot = kc & 1;
       // stage st and slot were last used by chunk kc - 2, read out (so complete) in the previous iteration
       __syncthreads();
       if (*s_flag) { ok = false; break; }
-      if (tid == 0) {
-        const uint32_t bar = su32(&s_bar[st]);
-        mbar_expect_tx(bar, stage_tx);
-        for (int l = 0; l < Sc::limbs; l++) {
-          const int blk = (nt * P.n_kchunks + kc) * Sc::limbs + l;
-          tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), bar);
-        }
-      }
       // next chunk's members (in flight until the next iteration), this chunk's split into limbs, K-major rows
       if (kc + 1 < P.n_kchunks) {
         const int m1 = (kc + 1) * (kKc / 2);
@@ -341,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
       tma_par[st] ^= 1u;
       acc_pend[slot] = true;
       if (kc > 0) readout(slot ^ 1);
+      if (tid == 0 && kc + 1 < P.n_kchunks) load_r(kc + 1);
 #pragma unroll
       for (int e = 0; e < kKc / 2; e++) vcur[e] = vnext[e];
     }
