@@ -41,8 +41,8 @@ namespace tc {
 constexpr int kM = 128;       // groups per tile (MMA M, TMEM lanes)
 constexpr int kNT = 128;      // output reals per work item (TMEM columns of one accumulator slot)
 constexpr int kKc = 16;       // input reals per K chunk
-constexpr int kThreads = 128;
-constexpr int kStages = 2;
+constexpr int kThreads = 320;  // 4 gather warps, 4 readout warps, a TMA warp and an MMA warp
+constexpr int kStages = 4;
 
 // Limb schemes: element size, limbs, MMA K per instruction, products (pairs of limbs, smallest first).
 template <int SCHEME> struct Scheme;
@@ -67,7 +67,7 @@ template <int SCHEME> __host__ __device__ constexpr int stage_bytes() {
 }
 constexpr int kMaxMembers = 4096;  // 4^6
 template <int SCHEME> __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + 8 * (kStages + 2) + 16;
+  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + 8 * (3 * kStages + 4) + 16;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -179,22 +179,37 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 };
 
 // ------------------------------------------------------------------ the block kernel
-// Per work item (a tile of kM groups and kNT output reals) the K chunks run as a two-slot pipeline: the
-// tensor core accumulates chunk c into TMEM slot c % 2, starting from zero, while the threads read chunk
-// c - 1's slot and add it into FP32 registers.  The tensor core's accumulation rounds toward zero, so
-// summing all 2 * 4^k inputs in TMEM would shrink every output by roughly (number of additions) x 2^-25
-// (measured: a trace 3.6e-5 low after 17 blocks of k = 4); summing one chunk's 16 inputs there and the
-// chunks in registers (round to nearest) keeps the result unbiased.
+// Warp-specialised and persistent: every role walks the same sequence of (work item, K chunk) pairs and
+// the roles hand chunks to one another through mbarriers.
+//   warps 0-3, gather: thread m loads group m's 8 members of the chunk (one chunk ahead in registers),
+//     splits them into limbs and stores them into the K-major A tile of a shared-memory stage;
+//   warp 8 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
+//   warp 9 (one lane), MMA: when both halves of a stage are full and a TMEM slot is free, issues the
+//     chunk's tcgen05.mma (accumulating into the slot from zero) and commits to the stage's "empty" and the
+//     slot's "full" barriers;
+//   warps 4-7, readout: thread m reads its lane of the slot (tcgen05.ld), adds it into FP32 registers and
+//     frees the slot; after the item's last chunk it writes the group's outputs.
+// The tensor core's accumulation rounds toward zero, so summing all 2 * 4^k inputs in TMEM would shrink
+// every output by roughly (number of additions) x 2^-25 (measured: a trace 3.6e-5 low after 17 blocks of
+// k = 4); summing one chunk's 16 inputs there and the chunks in registers (round to nearest) keeps the
+// result unbiased.
+constexpr int kGatherThreads = 128, kReadThreads = 128;
+constexpr int kTmaWarp = 8, kMmaWarp = 9;
+
 template <int SCHEME>
-__global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
+__global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
   using Sc = Scheme<SCHEME>;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint32_t* s_off = (uint32_t*)(sm + kStages * stage_bytes<SCHEME>());
-  uint64_t* s_bar = (uint64_t*)(s_off + kMaxMembers);  // [0, kStages): TMA per stage; then MMA per TMEM slot
-  uint32_t* s_tmem = (uint32_t*)(s_bar + kStages + 2);
-  int* s_flag = (int*)(s_tmem + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t* full_a = (uint64_t*)(s_off + kMaxMembers);
+  uint64_t* full_b = full_a + kStages;
+  uint64_t* empty = full_b + kStages;
+  uint64_t* tfull = empty + kStages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* s_tmem = (uint32_t*)(tempty + 2);
+  volatile int* s_flag = (volatile int*)(s_tmem + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto a_tile = [&](int st, int limb) { return sm + st * stage_bytes<SCHEME>() + limb * a_bytes<SCHEME>(); };
   auto b_tile = [&](int st, int limb) {
     return sm + st * stage_bytes<SCHEME>() + Sc::limbs * a_bytes<SCHEME>() + limb * b_bytes<SCHEME>();
@@ -206,7 +221,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < kStages + 2; i++) mbar_init(su32(&s_bar[i]), 1);
+    for (int i = 0; i < kStages; i++) {
+      mbar_init(su32(&full_a[i]), kGatherThreads);
+      mbar_init(su32(&full_b[i]), 1);
+      mbar_init(su32(&empty[i]), 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(su32(&tfull[i]), 1);
+      mbar_init(su32(&tempty[i]), kReadThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
   }
@@ -221,113 +244,151 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 
-  const uint32_t id = idesc(SCHEME == VQD_TC_3XTF32 ? 2u : 1u, kM, kNT);
-  constexpr uint32_t kAslice = kM * 16, kBslice = kNT * 16;  // bytes per 16-byte K slice of A and B
-  constexpr int kElemPer16 = 16 / Sc::esz;
-  constexpr int kSteps = kKc / Sc::kper;                       // MMAs along K per chunk and product
-  const uint32_t stage_tx = (uint32_t)(Sc::limbs * b_bytes<SCHEME>());
-  uint32_t tma_par[kStages], acc_par[2] = {0, 0};
-  for (int i = 0; i < kStages; i++) tma_par[i] = 0;
-  bool acc_pend[2] = {false, false};
-  bool ok = true;
   const uint64_t items = (uint64_t)P.n_gtiles * P.n_ntiles;
-  const float2* __restrict__ X = P.X;
-  float2* __restrict__ Y = P.Y;
-
-  float sum[kNT];
-  // read TMEM slot `slot` (this thread's lane, kNT columns) into sum once its chunk's products are complete
-  auto readout = [&](int slot) {
-    const bool w = mbar_wait(su32(&s_bar[kStages + slot]), acc_par[slot]);
-    acc_par[slot] ^= 1u;
-    acc_pend[slot] = false;
-    if (!w) *s_flag = 1;
-    tc_fence_after();
-#pragma unroll
-    for (int c = 0; c < kNT; c += 16) {
-      float v[16];
-      tmem_ld16(lane_addr + slot * kNT + c, v);
-#pragma unroll
-      for (int i = 0; i < 16; i++) sum[c + i] += v[i];
-    }
-    tc_fence_before();
-  };
-
-  for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
-    const uint32_t gt = (uint32_t)(item / P.n_ntiles), nt = (uint32_t)(item % P.n_ntiles);
-    const uint32_t g = gt * kM + tid;
-    const bool valid = g < P.groups;
-    uint32_t base = g;  // zero bits inserted at the block's (ascending) bit positions
+  const int nk = P.n_kchunks;
+  auto group_base = [&](uint32_t g) {  // zero bits inserted at the block's (ascending) bit positions
+    uint32_t b = g;
     for (int j = 0; j < P.mb; j++) {
       const uint32_t low = (1u << P.pos[j]) - 1u;
-      base = (base & low) | ((base & ~low) << 1);
+      b = (b & low) | ((b & ~low) << 1);
     }
+    return b;
+  };
+  // a wait that gave up marks the CTA failed; every role then leaves its loop
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if (mbar_wait(su32(bar), parity)) return true;
+    *s_flag = 1;
+    return false;
+  };
+
+  if (warp < 4) {
+    // ---------------------------------------------------------------- gather
+    const float2* __restrict__ X = P.X;
+    constexpr uint32_t kAslice = kM * 16;
+    constexpr int kElemPer16 = 16 / Sc::esz;
+    uint32_t c = 0;
+    bool ok = true;
+    for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const uint32_t gt = (uint32_t)(item / P.n_ntiles);
+      const uint32_t g = gt * kM + tid;
+      const bool valid = g < P.groups;
+      const uint32_t base = group_base(g);
+      float2 vnext[kKc / 2];
 #pragma unroll
-    for (int i = 0; i < kNT; i++) sum[i] = 0.f;
-    // the chunk's 8 members of group g, loaded one chunk ahead so that the loads are in flight while the
-    // previous chunk is stored, multiplied and read out
-    float2 vcur[kKc / 2], vnext[kKc / 2];
+      for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[e]] : make_float2(0.f, 0.f);
+      for (int kc = 0; kc < nk; kc++, c++) {
+        const int st = c % kStages;
+        const uint32_t ph = (c / kStages) & 1u;
+        float2 vcur[kKc / 2];
 #pragma unroll
-    for (int e = 0; e < kKc / 2; e++) vcur[e] = valid ? X[base + s_off[e]] : make_float2(0.f, 0.f);
-    // R's chunks are loaded one chunk ahead: chunk kc + 1 as soon as chunk kc - 1's products are complete
-    auto load_r = [&](int kc) {
-      const int st = kc % kStages;
-      const uint32_t bar = su32(&s_bar[st]);
-      mbar_expect_tx(bar, stage_tx);
-      for (int l = 0; l < Sc::limbs; l++) {
-        const int blk = (nt * P.n_kchunks + kc) * Sc::limbs + l;
-        tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), bar);
-      }
-    };
-    if (tid == 0) load_r(0);
-    for (int kc = 0; kc < P.n_kchunks; kc++) {
-      const int st = kc % kStages, slot = kc & 1;
-      // stage st and slot were last used by chunk kc - 2, read out (so complete) in the previous iteration
-      __syncthreads();
-      if (*s_flag) { ok = false; break; }
-      // next chunk's members (in flight until the next iteration), this chunk's split into limbs, K-major rows
-      if (kc + 1 < P.n_kchunks) {
-        const int m1 = (kc + 1) * (kKc / 2);
+        for (int e = 0; e < kKc / 2; e++) vcur[e] = vnext[e];
+        if (kc + 1 < nk) {
+          const int m1 = (kc + 1) * (kKc / 2);
 #pragma unroll
-        for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[m1 + e]] : make_float2(0.f, 0.f);
-      }
-      Limbs<SCHEME> lre[kKc / 2] = {Limbs<SCHEME>(vcur[0].x), Limbs<SCHEME>(vcur[1].x), Limbs<SCHEME>(vcur[2].x),
-                                    Limbs<SCHEME>(vcur[3].x), Limbs<SCHEME>(vcur[4].x), Limbs<SCHEME>(vcur[5].x),
-                                    Limbs<SCHEME>(vcur[6].x), Limbs<SCHEME>(vcur[7].x)};
-      Limbs<SCHEME> lim[kKc / 2] = {Limbs<SCHEME>(vcur[0].y), Limbs<SCHEME>(vcur[1].y), Limbs<SCHEME>(vcur[2].y),
-                                    Limbs<SCHEME>(vcur[3].y), Limbs<SCHEME>(vcur[4].y), Limbs<SCHEME>(vcur[5].y),
-                                    Limbs<SCHEME>(vcur[6].y), Limbs<SCHEME>(vcur[7].y)};
+          for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[m1 + e]] : make_float2(0.f, 0.f);
+        }
+        if (!wait(&empty[st], ph ^ 1u) || *s_flag) { ok = false; break; }
 #pragma unroll
-      for (int l = 0; l < Sc::limbs; l++) {
-        unsigned char* at = a_tile(st, l);
-        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk; row tid at 16 * tid
+        for (int l = 0; l < Sc::limbs; l++) {
+          unsigned char* at = a_tile(st, l);
+          // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk; row tid at 16 * tid
 #pragma unroll
-        for (int q = 0; q < kKc / kElemPer16; q++) {
-          if constexpr (SCHEME == VQD_TC_3XTF32) {
-            float4 w;
-            w.x = lre[2 * q].l[l];
-            w.y = lim[2 * q].l[l];
-            w.z = lre[2 * q + 1].l[l];
-            w.w = lim[2 * q + 1].l[l];
-            *(float4*)(at + q * kAslice + 16 * tid) = w;
-          } else {
-            __nv_bfloat16 h[8];
+          for (int q = 0; q < kKc / kElemPer16; q++) {
+            if constexpr (SCHEME == VQD_TC_3XTF32) {
+              float4 w;
+              w.x = Limbs<SCHEME>(vcur[2 * q].x).l[l];
+              w.y = Limbs<SCHEME>(vcur[2 * q].y).l[l];
+              w.z = Limbs<SCHEME>(vcur[2 * q + 1].x).l[l];
+              w.w = Limbs<SCHEME>(vcur[2 * q + 1].y).l[l];
+              *(float4*)(at + q * kAslice + 16 * tid) = w;
+            } else {
+              __nv_bfloat16 h[8];
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-              h[2 * e] = lre[4 * q + e].l[l];
-              h[2 * e + 1] = lim[4 * q + e].l[l];
+              for (int e = 0; e < 4; e++) {
+                h[2 * e] = Limbs<SCHEME>(vcur[4 * q + e].x).l[l];
+                h[2 * e + 1] = Limbs<SCHEME>(vcur[4 * q + e].y).l[l];
+              }
+              *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
             }
-            *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
+          }
+        }
+        fence_proxy_async();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
+      }
+    }
+  } else if (warp < 8) {
+    // ---------------------------------------------------------------- readout
+    float2* __restrict__ Y = P.Y;
+    const int row = tid - kGatherThreads;  // TMEM lane = group row; warp w reads lanes 32 (w % 4) ..
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t c = 0;
+    bool ok = true;
+    float sum[kNT];
+    for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const uint32_t gt = (uint32_t)(item / P.n_ntiles), nt = (uint32_t)(item % P.n_ntiles);
+      const uint32_t g = gt * kM + row;
+#pragma unroll
+      for (int i = 0; i < kNT; i++) sum[i] = 0.f;
+      for (int kc = 0; kc < nk; kc++, c++) {
+        const int slot = c & 1;
+        if (!wait(&tfull[slot], (c >> 1) & 1u) || *s_flag) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int c0 = 0; c0 < kNT; c0 += 32) {
+          float v[32];
+          tmem_ld16(lane_addr + slot * kNT + c0, v);
+          tmem_ld16(lane_addr + slot * kNT + c0 + 16, v + 16);
+#pragma unroll
+          for (int i = 0; i < 32; i++) sum[c0 + i] += v[i];
+        }
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[slot])) : "memory");
+      }
+      if (!ok) break;
+      if (g < P.groups) {
+        const uint32_t base = group_base(g);
+        const uint32_t out0 = nt * (kNT / 2);
+#pragma unroll
+        for (int e = 0; e < kNT / 2; e++) Y[base + s_off[out0 + e]] = make_float2(sum[2 * e], sum[2 * e + 1]);
+      }
+    }
+  } else if (warp == kTmaWarp) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      const uint32_t stage_tx = (uint32_t)(Sc::limbs * b_bytes<SCHEME>());
+      uint32_t c = 0;
+      bool ok = true;
+      for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const uint32_t nt = (uint32_t)(item % P.n_ntiles);
+        for (int kc = 0; kc < nk; kc++, c++) {
+          const int st = c % kStages;
+          if (!wait(&empty[st], ((c / kStages) & 1u) ^ 1u) || *s_flag) { ok = false; break; }
+          mbar_expect_tx(su32(&full_b[st]), stage_tx);
+          for (int l = 0; l < Sc::limbs; l++) {
+            const int blk = (nt * nk + kc) * Sc::limbs + l;
+            tma_load_2d(su32(b_tile(st, l)), &tmB, 0, blk * (kNT * kKc / 256), su32(&full_b[st]));
           }
         }
       }
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        const bool w = mbar_wait(su32(&s_bar[st]), tma_par[st]);
-        if (!w) *s_flag = 1;
-        else {
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t id = idesc(SCHEME == VQD_TC_3XTF32 ? 2u : 1u, kM, kNT);
+      constexpr uint32_t kAslice = kM * 16, kBslice = kNT * 16;  // bytes per 16-byte K slice of A and B
+      constexpr int kSteps = kKc / Sc::kper;                       // MMAs along K per chunk and product
+      uint32_t c = 0;
+      bool ok = true;
+      for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        for (int kc = 0; kc < nk; kc++, c++) {
+          const int st = c % kStages, slot = c & 1;
+          const uint32_t ph = (c / kStages) & 1u;
+          if (!wait(&full_b[st], ph) || !wait(&full_a[st], ph) || !wait(&tempty[slot], ((c >> 1) & 1u) ^ 1u) ||
+              *s_flag) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
           const uint32_t d = tmem + slot * kNT;
 #pragma unroll
@@ -338,36 +399,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_block(const __grid_constant_
               const uint64_t bd = sdesc(su32(b_tile(st, Sc::pb(p))) + ks * 2 * kBslice, kBslice, 128);
               mma<SCHEME>(d, ad, bd, id, (ks > 0 || p > 0) ? 1u : 0u);
             }
-          mma_commit(su32(&s_bar[kStages + slot]));
+          mma_commit(su32(&empty[st]));
+          mma_commit(su32(&tfull[slot]));
         }
       }
-      tma_par[st] ^= 1u;
-      acc_pend[slot] = true;
-      if (kc > 0) readout(slot ^ 1);
-      if (tid == 0 && kc + 1 < P.n_kchunks) load_r(kc + 1);
-#pragma unroll
-      for (int e = 0; e < kKc / 2; e++) vcur[e] = vnext[e];
+      // leave with no tensor-core operation of this CTA in flight (bounded), whatever happened
+      if (c > 0) mbar_wait(su32(&tfull[(c - 1) & 1]), ((c - 1) >> 1) & 1u);
     }
-    if (!ok) break;
-    if (acc_pend[(P.n_kchunks - 1) & 1]) readout((P.n_kchunks - 1) & 1);
-    __syncthreads();
-    if (*s_flag) { ok = false; break; }
-    if (valid) {
-      const uint32_t out0 = nt * (kNT / 2);
-#pragma unroll
-      for (int e = 0; e < kNT / 2; e++) Y[base + s_off[out0 + e]] = make_float2(sum[2 * e], sum[2 * e + 1]);
-    }
-  }
-  // leave with no copy or tensor-core operation of this CTA in flight (bounded waits), then free TMEM
-  __syncthreads();
-  if (tid == 0) {
-    for (int slot = 0; slot < 2; slot++)
-      if (acc_pend[slot]) mbar_wait(su32(&s_bar[kStages + slot]), acc_par[slot]);
-    if (*s_flag) atomicExch(P.err, 1);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (tid == 0 && *s_flag) atomicExch(P.err, 1);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNT) : "memory");
 }
 
@@ -530,7 +573,7 @@ static cudaError_t launch_t(const TcParams& P, const void* R, int k, cudaStream_
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_block<SCHEME>, kThreads, smem) != cudaSuccess ||
       per_sm <= 0)
     per_sm = 1;
-  per_sm = std::min(per_sm, 2);  // two CTAs of 256 TMEM columns fill an SM's 512
+  per_sm = std::min(per_sm, 2);  // at most two CTAs of 256 TMEM columns fill an SM's 512
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)per_sm * num_sms()));
   k_tc_block<SCHEME><<<grid, kThreads, smem, s>>>(tm, P);
   return cudaGetLastError();
