@@ -66,8 +66,10 @@ template <int SCHEME> __host__ __device__ constexpr int stage_bytes() {
   return Scheme<SCHEME>::limbs * (a_bytes<SCHEME>() + b_bytes<SCHEME>());
 }
 constexpr int kMaxMembers = 4096;  // 4^6
+constexpr int kBarBytes = 8 * (3 * kStages + 4) + 16;  // mbarriers, TMEM address, failure flag
+constexpr int kRingBytes = 4 * 16 / 2 * 128 * 8;         // 4 chunks x 8 members x 128 groups x float2
 template <int SCHEME> __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + 8 * (3 * kStages + 4) + 16;
+  return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + kBarBytes + kRingBytes;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -139,18 +141,16 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 32 lanes x 16 columns of 32 bits: thread i of the warp receives lane (base lane + i), 16 columns.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 32 lanes x 16 columns of 32 bits: thread i of the warp receives lane (base lane + i), 16 columns.  The
+// registers are valid after tmem_wait().
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32r(float x) {
   uint32_t r;
@@ -195,6 +195,7 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 // result unbiased.
 constexpr int kGatherThreads = 128, kReadThreads = 128;
 constexpr int kTmaWarp = 8, kMmaWarp = 9;
+constexpr int kAhead = 3, kRing = kAhead + 1;  // chunks of the state in flight ahead of the one being split
 
 template <int SCHEME>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
@@ -264,59 +265,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
 
   if (warp < 4) {
     // ---------------------------------------------------------------- gather
+    // The members of chunk c + kAhead are copied into a ring of raw FP32 values in shared memory
+    // (cp.async, [slot][member][thread] so that a warp's copies and reads are conflict-free) while chunk c
+    // is split; each thread reads back only what it copied itself.
     const float2* __restrict__ X = P.X;
+    float2* ring = (float2*)(sm + kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + kBarBytes);
     constexpr uint32_t kAslice = kM * 16;
     constexpr int kElemPer16 = 16 / Sc::esz;
-    uint32_t c = 0;
-    bool ok = true;
-    for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      const uint32_t gt = (uint32_t)(item / P.n_ntiles);
-      const uint32_t g = gt * kM + tid;
-      const bool valid = g < P.groups;
-      const uint32_t base = group_base(g);
-      float2 vnext[kKc / 2];
+    const uint64_t my_items = items > blockIdx.x ? (items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const uint64_t total = my_items * nk;
+    auto issue = [&](uint64_t cc) {  // copies of chunk cc (if any), one commit group per chunk
+      if (cc < total) {
+        const uint64_t item = blockIdx.x + (cc / nk) * gridDim.x;
+        const int kc = (int)(cc % nk);
+        const uint32_t g = (uint32_t)(item / P.n_ntiles) * kM + tid;
+        float2* dst = ring + (size_t)(cc % kRing) * (kKc / 2) * kM + tid;
+        if (g < P.groups) {
+          const uint32_t base = group_base(g);
 #pragma unroll
-      for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[e]] : make_float2(0.f, 0.f);
-      for (int kc = 0; kc < nk; kc++, c++) {
-        const int st = c % kStages;
-        const uint32_t ph = (c / kStages) & 1u;
-        float2 vcur[kKc / 2];
+          for (int e = 0; e < kKc / 2; e++)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst + e * kM)),
+                         "l"(X + base + s_off[kc * (kKc / 2) + e])
+                         : "memory");
+        } else {
 #pragma unroll
-        for (int e = 0; e < kKc / 2; e++) vcur[e] = vnext[e];
-        if (kc + 1 < nk) {
-          const int m1 = (kc + 1) * (kKc / 2);
-#pragma unroll
-          for (int e = 0; e < kKc / 2; e++) vnext[e] = valid ? X[base + s_off[m1 + e]] : make_float2(0.f, 0.f);
+          for (int e = 0; e < kKc / 2; e++) dst[e * kM] = make_float2(0.f, 0.f);
         }
-        if (!wait(&empty[st], ph ^ 1u) || *s_flag) { ok = false; break; }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int a = 0; a < kAhead; a++) issue((uint64_t)a);
+    for (uint64_t c = 0; c < total; c++) {
+      issue(c + kAhead);
+      asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
+      const float2* src = ring + (size_t)(c % kRing) * (kKc / 2) * kM + tid;
+      float2 vcur[kKc / 2];
 #pragma unroll
-        for (int l = 0; l < Sc::limbs; l++) {
-          unsigned char* at = a_tile(st, l);
-          // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk; row tid at 16 * tid
+      for (int e = 0; e < kKc / 2; e++) vcur[e] = src[e * kM];
+      const int st = (int)(c % kStages);
+      const uint32_t ph = (uint32_t)(c / kStages) & 1u;
+      if (!wait(&empty[st], ph ^ 1u) || *s_flag) break;
 #pragma unroll
-          for (int q = 0; q < kKc / kElemPer16; q++) {
-            if constexpr (SCHEME == VQD_TC_3XTF32) {
-              float4 w;
-              w.x = Limbs<SCHEME>(vcur[2 * q].x).l[l];
-              w.y = Limbs<SCHEME>(vcur[2 * q].y).l[l];
-              w.z = Limbs<SCHEME>(vcur[2 * q + 1].x).l[l];
-              w.w = Limbs<SCHEME>(vcur[2 * q + 1].y).l[l];
-              *(float4*)(at + q * kAslice + 16 * tid) = w;
-            } else {
-              __nv_bfloat16 h[8];
+      for (int l = 0; l < Sc::limbs; l++) {
+        unsigned char* at = a_tile(st, l);
+        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk; row tid at 16 * tid
 #pragma unroll
-              for (int e = 0; e < 4; e++) {
-                h[2 * e] = Limbs<SCHEME>(vcur[4 * q + e].x).l[l];
-                h[2 * e + 1] = Limbs<SCHEME>(vcur[4 * q + e].y).l[l];
-              }
-              *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
+        for (int q = 0; q < kKc / kElemPer16; q++) {
+          if constexpr (SCHEME == VQD_TC_3XTF32) {
+            float4 w;
+            w.x = Limbs<SCHEME>(vcur[2 * q].x).l[l];
+            w.y = Limbs<SCHEME>(vcur[2 * q].y).l[l];
+            w.z = Limbs<SCHEME>(vcur[2 * q + 1].x).l[l];
+            w.w = Limbs<SCHEME>(vcur[2 * q + 1].y).l[l];
+            *(float4*)(at + q * kAslice + 16 * tid) = w;
+          } else {
+            __nv_bfloat16 h[8];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              h[2 * e] = Limbs<SCHEME>(vcur[4 * q + e].x).l[l];
+              h[2 * e + 1] = Limbs<SCHEME>(vcur[4 * q + e].y).l[l];
             }
+            *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
           }
         }
-        fence_proxy_async();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
       }
+      fence_proxy_async();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp < 8) {
     // ---------------------------------------------------------------- readout
     float2* __restrict__ Y = P.Y;
@@ -336,11 +352,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
         tc_fence_after();
 #pragma unroll
         for (int c0 = 0; c0 < kNT; c0 += 32) {
-          float v[32];
+          uint32_t v[32];
           tmem_ld16(lane_addr + slot * kNT + c0, v);
           tmem_ld16(lane_addr + slot * kNT + c0 + 16, v + 16);
+          tmem_wait();
 #pragma unroll
-          for (int i = 0; i < 32; i++) sum[c0 + i] += v[i];
+          for (int i = 0; i < 32; i++) sum[c0 + i] += __uint_as_float(v[i]);
         }
         tc_fence_before();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[slot])) : "memory");
