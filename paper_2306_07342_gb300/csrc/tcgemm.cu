@@ -274,36 +274,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     constexpr int kElemPer16 = 16 / Sc::esz;
     const uint64_t my_items = items > blockIdx.x ? (items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const uint64_t total = my_items * nk;
-    auto issue = [&](uint64_t cc) {  // copies of chunk cc (if any), one commit group per chunk
-      if (cc < total) {
-        const uint64_t item = blockIdx.x + (cc / nk) * gridDim.x;
-        const int kc = (int)(cc % nk);
-        const uint32_t g = (uint32_t)(item / P.n_ntiles) * kM + tid;
-        float2* dst = ring + (size_t)(cc % kRing) * (kKc / 2) * kM + tid;
-        if (g < P.groups) {
-          const uint32_t base = group_base(g);
+    // cursor of the chunk whose copies are issued next: (item, chunk), advanced without divisions
+    uint64_t p_item = blockIdx.x;
+    int p_kc = 0, p_slot = 0;
+    uint32_t p_base = 0;
+    bool p_valid = false, p_new = true;
+    uint64_t issued = 0;
+    auto issue = [&]() {  // copies of the next chunk (if any), one commit group per chunk
+      if (issued < total) {
+        if (p_new) {
+          const uint32_t g = (uint32_t)(p_item / P.n_ntiles) * kM + tid;
+          p_valid = g < P.groups;
+          p_base = p_valid ? group_base(g) : 0u;
+          p_new = false;
+        }
+        float2* dst = ring + (size_t)p_slot * (kKc / 2) * kM + tid;
+        const uint32_t* off = s_off + p_kc * (kKc / 2);
+        if (p_valid) {
 #pragma unroll
           for (int e = 0; e < kKc / 2; e++)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst + e * kM)),
-                         "l"(X + base + s_off[kc * (kKc / 2) + e])
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst + e * kM)), "l"(X + p_base + off[e])
                          : "memory");
         } else {
 #pragma unroll
           for (int e = 0; e < kKc / 2; e++) dst[e * kM] = make_float2(0.f, 0.f);
         }
+        issued++;
+        p_slot = p_slot + 1 == kRing ? 0 : p_slot + 1;
+        if (++p_kc == nk) {
+          p_kc = 0;
+          p_item += gridDim.x;
+          p_new = true;
+        }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    for (int a = 0; a < kAhead; a++) issue((uint64_t)a);
+    for (int a = 0; a < kAhead; a++) issue();
+    int r_slot = 0, st = 0;
+    uint32_t ph = 0;
     for (uint64_t c = 0; c < total; c++) {
-      issue(c + kAhead);
+      issue();
       asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
-      const float2* src = ring + (size_t)(c % kRing) * (kKc / 2) * kM + tid;
+      const float2* src = ring + (size_t)r_slot * (kKc / 2) * kM + tid;
+      r_slot = r_slot + 1 == kRing ? 0 : r_slot + 1;
       float2 vcur[kKc / 2];
 #pragma unroll
       for (int e = 0; e < kKc / 2; e++) vcur[e] = src[e * kM];
-      const int st = (int)(c % kStages);
-      const uint32_t ph = (uint32_t)(c / kStages) & 1u;
       if (!wait(&empty[st], ph ^ 1u) || *s_flag) break;
 #pragma unroll
       for (int l = 0; l < Sc::limbs; l++) {
@@ -331,6 +347,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       }
       fence_proxy_async();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
+      if (++st == kStages) {
+        st = 0;
+        ph ^= 1u;
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp < 8) {
