@@ -7,7 +7,7 @@
 // with complex numbers interleaved (re, im), this is Y = X R^T over all groups: X has one row per group
 // and 2 * 4^k columns, R = [[Re S, -Im S], [Im S, Re S]] interleaved the same way.  The GEMM runs with
 //   M = 128 groups per tile (one TMEM lane each),
-//   N = 128 output reals per work item (one TMEM accumulator slot of 128 columns; two slots per CTA),
+//   N = 128 output reals per work item (one TMEM accumulator slot of 128 columns; four slots per CTA),
 //   K = 2 * 4^k input reals, in chunks of 16, each chunk accumulated in its own slot and the chunks
 //   summed in FP32 registers.
 // Split precision: the FP32 operands are split into limbs and the limb products accumulate in FP32:
@@ -66,7 +66,7 @@ template <int SCHEME> __host__ __device__ constexpr int stage_bytes() {
   return Scheme<SCHEME>::limbs * (a_bytes<SCHEME>() + b_bytes<SCHEME>());
 }
 constexpr int kMaxMembers = 4096;  // 4^6
-constexpr int kBarBytes = 8 * (3 * kStages + 4) + 16;  // mbarriers, TMEM address, failure flag
+constexpr int kBarBytes = 8 * (3 * kStages + 8) + 16;  // mbarriers, TMEM address, failure flag
 constexpr int kRingBytes = 4 * 16 / 2 * 128 * 8;         // 4 chunks x 8 members x 128 groups x float2
 template <int SCHEME> __host__ __device__ constexpr size_t smem_bytes() {
   return 1024 + (size_t)kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + kBarBytes + kRingBytes;
@@ -184,7 +184,7 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 //   warps 0-3, gather: thread m loads group m's 8 members of the chunk (one chunk ahead in registers),
 //     splits them into limbs and stores them into the K-major A tile of a shared-memory stage;
 //   warp 8 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
-//   warp 9 (one lane), MMA: when both halves of a stage are full and a TMEM slot is free, issues the
+//   warp 9 (one lane), MMA: when both halves of a stage are full and one of four TMEM slots is free, issues the
 //     chunk's tcgen05.mma (accumulating into the slot from zero) and commits to the stage's "empty" and the
 //     slot's "full" barriers;
 //   warps 4-7, readout: thread m reads its lane of the slot (tcgen05.ld), adds it into FP32 registers and
@@ -196,6 +196,7 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 constexpr int kGatherThreads = 128, kReadThreads = 128;
 constexpr int kTmaWarp = 8, kMmaWarp = 9;
 constexpr int kAhead = 3, kRing = kAhead + 1;  // chunks of the state in flight ahead of the one being split
+constexpr int kSlots = 4;                       // TMEM accumulator slots of kNT columns: all 512 columns
 
 template <int SCHEME>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
@@ -207,8 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
   uint64_t* full_b = full_a + kStages;
   uint64_t* empty = full_b + kStages;
   uint64_t* tfull = empty + kStages;
-  uint64_t* tempty = tfull + 2;
-  uint32_t* s_tmem = (uint32_t*)(tempty + 2);
+  uint64_t* tempty = tfull + kSlots;
+  uint32_t* s_tmem = (uint32_t*)(tempty + kSlots);
   volatile int* s_flag = (volatile int*)(s_tmem + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto a_tile = [&](int st, int limb) { return sm + st * stage_bytes<SCHEME>() + limb * a_bytes<SCHEME>(); };
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
   };
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(2 * kNT)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(kSlots * kNT)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       mbar_init(su32(&full_b[i]), 1);
       mbar_init(su32(&empty[i]), 1);
     }
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < kSlots; i++) {
       mbar_init(su32(&tfull[i]), 1);
       mbar_init(su32(&tempty[i]), kReadThreads);
     }
@@ -367,8 +368,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
 #pragma unroll
       for (int i = 0; i < kNT; i++) sum[i] = 0.f;
       for (int kc = 0; kc < nk; kc++, c++) {
-        const int slot = c & 1;
-        if (!wait(&tfull[slot], (c >> 1) & 1u) || *s_flag) { ok = false; break; }
+        const int slot = c % kSlots;
+        if (!wait(&tfull[slot], (c / kSlots) & 1u) || *s_flag) { ok = false; break; }
         tc_fence_after();
 #pragma unroll
         for (int c0 = 0; c0 < kNT; c0 += 32) {
@@ -419,9 +420,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       bool ok = true;
       for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
         for (int kc = 0; kc < nk; kc++, c++) {
-          const int st = c % kStages, slot = c & 1;
+          const int st = c % kStages, slot = c % kSlots;
           const uint32_t ph = (c / kStages) & 1u;
-          if (!wait(&full_b[st], ph) || !wait(&full_a[st], ph) || !wait(&tempty[slot], ((c >> 1) & 1u) ^ 1u) ||
+          if (!wait(&full_b[st], ph) || !wait(&full_a[st], ph) || !wait(&tempty[slot], ((c / kSlots) & 1u) ^ 1u) ||
               *s_flag) {
             ok = false;
             break;
@@ -441,14 +442,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
         }
       }
       // leave with no tensor-core operation of this CTA in flight (bounded), whatever happened
-      if (c > 0) mbar_wait(su32(&tfull[(c - 1) & 1]), ((c - 1) >> 1) & 1u);
+      if (c > 0) mbar_wait(su32(&tfull[(c - 1) % kSlots]), ((c - 1) / kSlots) & 1u);
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (tid == 0 && *s_flag) atomicExch(P.err, 1);
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNT) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSlots * kNT) : "memory");
 }
 
 // ------------------------------------------------------------------ R: limbs in the tiled K-major layout
