@@ -41,7 +41,7 @@ namespace tc {
 constexpr int kM = 128;       // groups per tile (MMA M, TMEM lanes)
 constexpr int kNT = 128;      // output reals per work item (TMEM columns of one accumulator slot)
 constexpr int kKc = 16;       // input reals per K chunk
-constexpr int kThreads = 320;  // 4 gather warps, 4 readout warps, a TMA warp and an MMA warp
+constexpr int kThreads = 576;  // 8 gather warps, 8 readout warps, a TMA warp and an MMA warp
 constexpr int kStages = 4;
 
 // Limb schemes: element size, limbs, MMA K per instruction, products (pairs of limbs, smallest first).
@@ -181,20 +181,22 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 // ------------------------------------------------------------------ the block kernel
 // Warp-specialised and persistent: every role walks the same sequence of (work item, K chunk) pairs and
 // the roles hand chunks to one another through mbarriers.
-//   warps 0-3, gather: thread m loads group m's 8 members of the chunk (one chunk ahead in registers),
-//     splits them into limbs and stores them into the K-major A tile of a shared-memory stage;
-//   warp 8 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
-//   warp 9 (one lane), MMA: when both halves of a stage are full and one of four TMEM slots is free, issues the
+//   warps 0-7, gather: two threads per group row load the row's 8 members of the chunk (three chunks
+//     ahead, cp.async into a shared-memory ring), split them into limbs and store them into the K-major
+//     A tile of a shared-memory stage;
+//   warp 16 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
+//   warp 17 (one lane), MMA: when both halves of a stage are full and one of four TMEM slots is free, issues the
 //     chunk's tcgen05.mma (accumulating into the slot from zero) and commits to the stage's "empty" and the
 //     slot's "full" barriers;
-//   warps 4-7, readout: thread m reads its lane of the slot (tcgen05.ld), adds it into FP32 registers and
-//     frees the slot; after the item's last chunk it writes the group's outputs.
+//   warps 8-15, readout: two threads per group row read half of the row's lane of the slot each
+//     (tcgen05.ld), add it into FP32 registers and free the slot; after the item's last chunk they write
+//     the group's outputs.
 // The tensor core's accumulation rounds toward zero, so summing all 2 * 4^k inputs in TMEM would shrink
 // every output by roughly (number of additions) x 2^-25 (measured: a trace 3.6e-5 low after 17 blocks of
 // k = 4); summing one chunk's 16 inputs there and the chunks in registers (round to nearest) keeps the
 // result unbiased.
-constexpr int kGatherThreads = 128, kReadThreads = 128;
-constexpr int kTmaWarp = 8, kMmaWarp = 9;
+constexpr int kGatherThreads = 256, kReadThreads = 256;  // two threads per group row in each role
+constexpr int kTmaWarp = 16, kMmaWarp = 17;
 constexpr int kAhead = 3, kRing = kAhead + 1;  // chunks of the state in flight ahead of the one being split
 constexpr int kSlots = 4;                       // TMEM accumulator slots of kNT columns: all 512 columns
 
@@ -264,11 +266,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     return false;
   };
 
-  if (warp < 4) {
+  if (warp < 8) {
     // ---------------------------------------------------------------- gather
-    // The members of chunk c + kAhead are copied into a ring of raw FP32 values in shared memory
-    // (cp.async, [slot][member][thread] so that a warp's copies and reads are conflict-free) while chunk c
-    // is split; each thread reads back only what it copied itself.
+    // Thread (row, half) handles members 4 half .. 4 half + 3 of each chunk of group row `row`.  The
+    // members of chunk c + kAhead are copied into a ring of raw FP32 values in shared memory (cp.async,
+    // [slot][member][row] so that a warp's copies and reads are conflict-free) while chunk c is split; each
+    // thread reads back only what it copied itself.
+    const int row = tid & (kM - 1), half = tid >> 7;
     const float2* __restrict__ X = P.X;
     float2* ring = (float2*)(sm + kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + kBarBytes);
     constexpr uint32_t kAslice = kM * 16;
@@ -284,21 +288,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     auto issue = [&]() {  // copies of the next chunk (if any), one commit group per chunk
       if (issued < total) {
         if (p_new) {
-          const uint32_t g = (uint32_t)(p_item / P.n_ntiles) * kM + tid;
+          const uint32_t g = (uint32_t)(p_item / P.n_ntiles) * kM + row;
           p_valid = g < P.groups;
           p_base = p_valid ? group_base(g) : 0u;
           p_new = false;
         }
-        float2* dst = ring + (size_t)p_slot * (kKc / 2) * kM + tid;
-        const uint32_t* off = s_off + p_kc * (kKc / 2);
+        float2* dst = ring + ((size_t)p_slot * (kKc / 2) + 4 * half) * kM + row;
+        const uint32_t* off = s_off + p_kc * (kKc / 2) + 4 * half;
         if (p_valid) {
 #pragma unroll
-          for (int e = 0; e < kKc / 2; e++)
+          for (int e = 0; e < 4; e++)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst + e * kM)), "l"(X + p_base + off[e])
                          : "memory");
         } else {
 #pragma unroll
-          for (int e = 0; e < kKc / 2; e++) dst[e * kM] = make_float2(0.f, 0.f);
+          for (int e = 0; e < 4; e++) dst[e * kM] = make_float2(0.f, 0.f);
         }
         issued++;
         p_slot = p_slot + 1 == kRing ? 0 : p_slot + 1;
@@ -316,34 +320,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     for (uint64_t c = 0; c < total; c++) {
       issue();
       asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
-      const float2* src = ring + (size_t)r_slot * (kKc / 2) * kM + tid;
+      const float2* src = ring + ((size_t)r_slot * (kKc / 2) + 4 * half) * kM + row;
       r_slot = r_slot + 1 == kRing ? 0 : r_slot + 1;
-      float2 vcur[kKc / 2];
-#pragma unroll
-      for (int e = 0; e < kKc / 2; e++) vcur[e] = src[e * kM];
+      Limbs<SCHEME> lre[4] = {Limbs<SCHEME>(src[0].x), Limbs<SCHEME>(src[kM].x), Limbs<SCHEME>(src[2 * kM].x),
+                              Limbs<SCHEME>(src[3 * kM].x)};
+      Limbs<SCHEME> lim[4] = {Limbs<SCHEME>(src[0].y), Limbs<SCHEME>(src[kM].y), Limbs<SCHEME>(src[2 * kM].y),
+                              Limbs<SCHEME>(src[3 * kM].y)};
       if (!wait(&empty[st], ph ^ 1u) || *s_flag) break;
 #pragma unroll
       for (int l = 0; l < Sc::limbs; l++) {
         unsigned char* at = a_tile(st, l);
-        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk; row tid at 16 * tid
+        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk, row r at 16 r: this thread's
+        // 4 members are slices 2 half, 2 half + 1 (TF32) or slice half (BF16)
+        if constexpr (SCHEME == VQD_TC_3XTF32) {
 #pragma unroll
-        for (int q = 0; q < kKc / kElemPer16; q++) {
-          if constexpr (SCHEME == VQD_TC_3XTF32) {
+          for (int q = 0; q < 2; q++) {
             float4 w;
-            w.x = Limbs<SCHEME>(vcur[2 * q].x).l[l];
-            w.y = Limbs<SCHEME>(vcur[2 * q].y).l[l];
-            w.z = Limbs<SCHEME>(vcur[2 * q + 1].x).l[l];
-            w.w = Limbs<SCHEME>(vcur[2 * q + 1].y).l[l];
-            *(float4*)(at + q * kAslice + 16 * tid) = w;
-          } else {
-            __nv_bfloat16 h[8];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-              h[2 * e] = Limbs<SCHEME>(vcur[4 * q + e].x).l[l];
-              h[2 * e + 1] = Limbs<SCHEME>(vcur[4 * q + e].y).l[l];
-            }
-            *(uint4*)(at + q * kAslice + 16 * tid) = *(const uint4*)h;
+            w.x = lre[2 * q].l[l];
+            w.y = lim[2 * q].l[l];
+            w.z = lre[2 * q + 1].l[l];
+            w.w = lim[2 * q + 1].l[l];
+            *(float4*)(at + (2 * half + q) * kAslice + 16 * row) = w;
           }
+        } else {
+          __nv_bfloat16 h[8];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            h[2 * e] = lre[e].l[l];
+            h[2 * e + 1] = lim[e].l[l];
+          }
+          *(uint4*)(at + half * kAslice + 16 * row) = *(const uint4*)h;
         }
       }
       fence_proxy_async();
@@ -354,31 +360,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (warp < 8) {
+  } else if (warp < 16) {
     // ---------------------------------------------------------------- readout
+    // TMEM lane = group row; warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31, columns [64 ch, 64 ch + 64)
     float2* __restrict__ Y = P.Y;
-    const int row = tid - kGatherThreads;  // TMEM lane = group row; warp w reads lanes 32 (w % 4) ..
-    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    constexpr int kCols = kNT / 2;
+    const int row = (warp & 3) * 32 + lane, ch = (warp - 8) >> 2;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * kCols;
     uint32_t c = 0;
     bool ok = true;
-    float sum[kNT];
+    float sum[kCols];
     for (uint64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
       const uint32_t gt = (uint32_t)(item / P.n_ntiles), nt = (uint32_t)(item % P.n_ntiles);
       const uint32_t g = gt * kM + row;
 #pragma unroll
-      for (int i = 0; i < kNT; i++) sum[i] = 0.f;
+      for (int i = 0; i < kCols; i++) sum[i] = 0.f;
       for (int kc = 0; kc < nk; kc++, c++) {
         const int slot = c % kSlots;
         if (!wait(&tfull[slot], (c / kSlots) & 1u) || *s_flag) { ok = false; break; }
         tc_fence_after();
 #pragma unroll
-        for (int c0 = 0; c0 < kNT; c0 += 32) {
-          uint32_t v[32];
+        for (int c0 = 0; c0 < kCols; c0 += 16) {
+          uint32_t v[16];
           tmem_ld16(lane_addr + slot * kNT + c0, v);
-          tmem_ld16(lane_addr + slot * kNT + c0 + 16, v + 16);
           tmem_wait();
 #pragma unroll
-          for (int i = 0; i < 32; i++) sum[c0 + i] += __uint_as_float(v[i]);
+          for (int i = 0; i < 16; i++) sum[c0 + i] += __uint_as_float(v[i]);
         }
         tc_fence_before();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[slot])) : "memory");
@@ -386,9 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       if (!ok) break;
       if (g < P.groups) {
         const uint32_t base = group_base(g);
-        const uint32_t out0 = nt * (kNT / 2);
+        const uint32_t out0 = nt * (kNT / 2) + ch * (kCols / 2);
 #pragma unroll
-        for (int e = 0; e < kNT / 2; e++) Y[base + s_off[out0 + e]] = make_float2(sum[2 * e], sum[2 * e + 1]);
+        for (int e = 0; e < kCols / 2; e++) Y[base + s_off[out0 + e]] = make_float2(sum[2 * e], sum[2 * e + 1]);
       }
     }
   } else if (warp == kTmaWarp) {
@@ -623,6 +630,7 @@ cudaError_t tc_apply(const void* X, void* Y, int n, int k, const int* q, int sch
   std::memset(&P, 0, sizeof(P));
   P.X = (const float2*)X;
   P.Y = (float2*)Y;
+  P.R = R;
   P.groups = (uint32_t)(1ull << (2 * (n - k)));
   P.n_gtiles = (P.groups + kM - 1) / kM;
   P.n_ntiles = (2 << (2 * k)) / kNT;

@@ -14,6 +14,7 @@ namespace vqd {
 struct TcParams {
   const float2* X;  // input state (complex64)
   float2* Y;        // output state (complex64), a different buffer
+  const void* R;    // the operator's limbs in the tiled layout (read by TMA)
   uint32_t groups;  // 4^(n-k)
   uint32_t n_gtiles;
   uint32_t n_ntiles;
