@@ -226,13 +226,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
   }
   if (tid == 0) {
     for (int i = 0; i < kStages; i++) {
-      mbar_init(su32(&full_a[i]), kGatherThreads);
+      mbar_init(su32(&full_a[i]), kGatherThreads / 32);  // one arrival per gather warp
       mbar_init(su32(&full_b[i]), 1);
       mbar_init(su32(&empty[i]), 1);
     }
     for (int i = 0; i < kSlots; i++) {
       mbar_init(su32(&tfull[i]), 1);
-      mbar_init(su32(&tempty[i]), kReadThreads);
+      mbar_init(su32(&tempty[i]), kReadThreads / 32);  // one arrival per readout warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
@@ -352,8 +352,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
           *(uint4*)(at + half * kAslice + 16 * row) = *(const uint4*)h;
         }
       }
+      // every lane's stores are made visible to the tensor core's (async) proxy, then one lane per warp
+      // arrives: same-address shared-memory arrivals serialise, so 8 per chunk instead of 256
       fence_proxy_async();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full_a[st])) : "memory");
       if (++st == kStages) {
         st = 0;
         ph ^= 1u;
@@ -388,7 +391,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
           for (int i = 0; i < 16; i++) sum[c0 + i] += __uint_as_float(v[i]);
         }
         tc_fence_before();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[slot])) : "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[slot])) : "memory");
       }
       if (!ok) break;
       if (g < P.groups) {
