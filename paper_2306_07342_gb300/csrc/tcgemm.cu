@@ -7,7 +7,7 @@
 // with complex numbers interleaved (re, im), this is Y = X R^T over all groups: X has one row per group
 // and 2 * 4^k columns, R = [[Re S, -Im S], [Im S, Re S]] interleaved the same way.  The GEMM runs with
 //   M = 128 groups per tile (one TMEM lane each),
-//   N = 128 output reals per work item (one TMEM accumulator slot of 128 columns; four slots per CTA),
+//   N = 256 output reals per work item (one TMEM accumulator slot of 256 columns; two slots per CTA),
 //   K = 2 * 4^k input reals, in chunks of 16, each chunk accumulated in its own slot and the chunks
 //   summed in FP32 registers.
 // Split precision: the FP32 operands are split into limbs and the limb products accumulate in FP32:
@@ -39,10 +39,10 @@ namespace vqd {
 namespace tc {
 
 constexpr int kM = 128;       // groups per tile (MMA M, TMEM lanes)
-constexpr int kNT = 128;      // output reals per work item (TMEM columns of one accumulator slot)
+constexpr int kNT = 256;      // output reals per work item (TMEM columns of one accumulator slot)
 constexpr int kKc = 16;       // input reals per K chunk
-constexpr int kThreads = 576;  // 8 gather warps, 8 readout warps, a TMA warp and an MMA warp
-constexpr int kStages = 4;
+constexpr int kThreads = 704;  // 4 gather warps, 16 readout warps, a TMA warp and an MMA warp
+constexpr int kStages = 3;
 
 // Limb schemes: element size, limbs, MMA K per instruction, products (pairs of limbs, smallest first).
 template <int SCHEME> struct Scheme;
@@ -181,24 +181,25 @@ template <> struct Limbs<VQD_TC_BF16X3> {
 // ------------------------------------------------------------------ the block kernel
 // Warp-specialised and persistent: every role walks the same sequence of (work item, K chunk) pairs and
 // the roles hand chunks to one another through mbarriers.
-//   warps 0-7, gather: two threads per group row load the row's 8 members of the chunk (three chunks
-//     ahead, cp.async into a shared-memory ring), split them into limbs and store them into the K-major
+//   warps 0-3, gather: one thread per group row loads the row's 8 members of the chunk (three chunks
+//     ahead, cp.async into a shared-memory ring), splits them into limbs and stores them into the K-major
 //     A tile of a shared-memory stage;
-//   warp 16 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
-//   warp 17 (one lane), MMA: when both halves of a stage are full and one of four TMEM slots is free, issues the
+//   warp 20 (one lane), TMA: loads the chunk's limbs of R into the stage (cp.async.bulk.tensor);
+//   warp 21 (one lane), MMA: when both halves of a stage are full and one of two TMEM slots is free, issues the
 //     chunk's tcgen05.mma (accumulating into the slot from zero) and commits to the stage's "empty" and the
 //     slot's "full" barriers;
-//   warps 8-15, readout: two threads per group row read half of the row's lane of the slot each
+//   warps 4-19, readout: four threads per group row read a quarter of the row's lane of the slot each
 //     (tcgen05.ld), add it into FP32 registers and free the slot; after the item's last chunk they write
 //     the group's outputs.
 // The tensor core's accumulation rounds toward zero, so summing all 2 * 4^k inputs in TMEM would shrink
 // every output by roughly (number of additions) x 2^-25 (measured: a trace 3.6e-5 low after 17 blocks of
 // k = 4); summing one chunk's 16 inputs there and the chunks in registers (round to nearest) keeps the
 // result unbiased.
-constexpr int kGatherThreads = 256, kReadThreads = 256;  // two threads per group row in each role
-constexpr int kTmaWarp = 16, kMmaWarp = 17;
+constexpr int kGatherThreads = 128, kReadThreads = 512;  // one gather thread and four readout threads per group row
+constexpr int kTmaWarp = 20, kMmaWarp = 21;
+constexpr int kGatherWarps = kGatherThreads / 32, kMemPerThread = 8 * kM / kGatherThreads;
 constexpr int kAhead = 3, kRing = kAhead + 1;  // chunks of the state in flight ahead of the one being split
-constexpr int kSlots = 4;                       // TMEM accumulator slots of kNT columns: all 512 columns
+constexpr int kSlots = 2;                       // TMEM accumulator slots of kNT columns: all 512 columns
 
 template <int SCHEME>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant__ CUtensorMap tmB, const TcParams P) {
@@ -266,13 +267,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     return false;
   };
 
-  if (warp < 8) {
+  if (warp < kGatherWarps) {
     // ---------------------------------------------------------------- gather
     // Thread (row, half) handles members 4 half .. 4 half + 3 of each chunk of group row `row`.  The
     // members of chunk c + kAhead are copied into a ring of raw FP32 values in shared memory (cp.async,
     // [slot][member][row] so that a warp's copies and reads are conflict-free) while chunk c is split; each
     // thread reads back only what it copied itself.
-    const int row = tid & (kM - 1), half = tid >> 7;
+    const int row = tid & (kM - 1), half = tid >> 7;  // half = 0 with one gather thread per row
     const float2* __restrict__ X = P.X;
     float2* ring = (float2*)(sm + kStages * stage_bytes<SCHEME>() + kMaxMembers * 4 + kBarBytes);
     constexpr uint32_t kAslice = kM * 16;
@@ -293,16 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
           p_base = p_valid ? group_base(g) : 0u;
           p_new = false;
         }
-        float2* dst = ring + ((size_t)p_slot * (kKc / 2) + 4 * half) * kM + row;
-        const uint32_t* off = s_off + p_kc * (kKc / 2) + 4 * half;
+        float2* dst = ring + ((size_t)p_slot * (kKc / 2) + kMemPerThread * half) * kM + row;
+        const uint32_t* off = s_off + p_kc * (kKc / 2) + kMemPerThread * half;
         if (p_valid) {
 #pragma unroll
-          for (int e = 0; e < 4; e++)
+          for (int e = 0; e < kMemPerThread; e++)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst + e * kM)), "l"(X + p_base + off[e])
                          : "memory");
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; e++) dst[e * kM] = make_float2(0.f, 0.f);
+          for (int e = 0; e < kMemPerThread; e++) dst[e * kM] = make_float2(0.f, 0.f);
         }
         issued++;
         p_slot = p_slot + 1 == kRing ? 0 : p_slot + 1;
@@ -320,36 +321,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
     for (uint64_t c = 0; c < total; c++) {
       issue();
       asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
-      const float2* src = ring + ((size_t)r_slot * (kKc / 2) + 4 * half) * kM + row;
+      const float2* src = ring + ((size_t)r_slot * (kKc / 2) + kMemPerThread * half) * kM + row;
       r_slot = r_slot + 1 == kRing ? 0 : r_slot + 1;
-      Limbs<SCHEME> lre[4] = {Limbs<SCHEME>(src[0].x), Limbs<SCHEME>(src[kM].x), Limbs<SCHEME>(src[2 * kM].x),
-                              Limbs<SCHEME>(src[3 * kM].x)};
-      Limbs<SCHEME> lim[4] = {Limbs<SCHEME>(src[0].y), Limbs<SCHEME>(src[kM].y), Limbs<SCHEME>(src[2 * kM].y),
-                              Limbs<SCHEME>(src[3 * kM].y)};
+      float2 vcur[kMemPerThread];
+#pragma unroll
+      for (int e = 0; e < kMemPerThread; e++) vcur[e] = src[e * kM];
       if (!wait(&empty[st], ph ^ 1u) || *s_flag) break;
 #pragma unroll
       for (int l = 0; l < Sc::limbs; l++) {
         unsigned char* at = a_tile(st, l);
-        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk, row r at 16 r: this thread's
-        // 4 members are slices 2 half, 2 half + 1 (TF32) or slice half (BF16)
-        if constexpr (SCHEME == VQD_TC_3XTF32) {
+        // K slice q holds reals [q * kElemPer16, (q + 1) * kElemPer16) of the chunk, row r at 16 r; this
+        // thread's members start at slice kMemPerThread * half * 2 / kElemPer16
+        constexpr int kPairsPerSlice = kElemPer16 / 2;  // complex members per 16-byte slice
+        const int q0 = kMemPerThread * half / kPairsPerSlice;
 #pragma unroll
-          for (int q = 0; q < 2; q++) {
+        for (int q = 0; q < kMemPerThread / kPairsPerSlice; q++) {
+          if constexpr (SCHEME == VQD_TC_3XTF32) {
             float4 w;
-            w.x = lre[2 * q].l[l];
-            w.y = lim[2 * q].l[l];
-            w.z = lre[2 * q + 1].l[l];
-            w.w = lim[2 * q + 1].l[l];
-            *(float4*)(at + (2 * half + q) * kAslice + 16 * row) = w;
-          }
-        } else {
-          __nv_bfloat16 h[8];
+            w.x = Limbs<SCHEME>(vcur[2 * q].x).l[l];
+            w.y = Limbs<SCHEME>(vcur[2 * q].y).l[l];
+            w.z = Limbs<SCHEME>(vcur[2 * q + 1].x).l[l];
+            w.w = Limbs<SCHEME>(vcur[2 * q + 1].y).l[l];
+            *(float4*)(at + (q0 + q) * kAslice + 16 * row) = w;
+          } else {
+            __nv_bfloat16 h[8];
 #pragma unroll
-          for (int e = 0; e < 4; e++) {
-            h[2 * e] = lre[e].l[l];
-            h[2 * e + 1] = lim[e].l[l];
+            for (int e = 0; e < 4; e++) {
+              h[2 * e] = Limbs<SCHEME>(vcur[4 * q + e].x).l[l];
+              h[2 * e + 1] = Limbs<SCHEME>(vcur[4 * q + e].y).l[l];
+            }
+            *(uint4*)(at + (q0 + q) * kAslice + 16 * row) = *(const uint4*)h;
           }
-          *(uint4*)(at + half * kAslice + 16 * row) = *(const uint4*)h;
         }
       }
       // every lane's stores are made visible to the tensor core's (async) proxy, then one lane per warp
@@ -363,12 +365,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_block(const __grid_constant_
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (warp < 16) {
+  } else if (warp < kGatherWarps + kReadThreads / 32) {
     // ---------------------------------------------------------------- readout
-    // TMEM lane = group row; warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31, columns [64 ch, 64 ch + 64)
+    // TMEM lane = group row; warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31 and one of the column quarters
     float2* __restrict__ Y = P.Y;
-    constexpr int kCols = kNT / 2;
-    const int row = (warp & 3) * 32 + lane, ch = (warp - 8) >> 2;
+    constexpr int kCols = kNT * kM / kReadThreads;
+    const int row = (warp & 3) * 32 + lane, ch = (warp - kGatherWarps) >> 2;
     const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ch * kCols;
     uint32_t c = 0;
     bool ok = true;
