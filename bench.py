@@ -313,6 +313,21 @@ def roofline_hbm(stats, peak, peak_src, steps=1, exclude=("reduce", "init", "tc_
             "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms}
 
 
+def fp64_alu_roofline(stats, fma_rate):
+    """Plain FP64 passes as FP64-arithmetic-bound kernels: the real multiply-adds their structured arithmetic
+    issues (the library's count, from the coefficients' zero/one/real/imaginary structure) per second of
+    device time, against the FP64 FMA rate measured on this GPU (vqd_measure_fma_rate)."""
+    out = {}
+    for k, v in stats.items():
+        if k in ("reduce", "init") or not v["launches"] or not v.get("alg_fma"):
+            continue
+        achieved = v["alg_fma"] / (v["total_ms"] * 1e-3)
+        out[k] = {"bound": "alu", "achieved": achieved, "peak": fma_rate, "unit": "FP64 FMA/s",
+                  "frac": achieved / fma_rate, "peak_source": "measured (vqd_measure_fma_rate)",
+                  "hbm_frac": (v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9)}
+    return out
+
+
 def per_class(stats, steps=1):
     return {k: {"launches": v["launches"] // max(1, steps), "avg_ms": v["total_ms"] / v["launches"]}
             for k, v in stats.items() if v["launches"]}
@@ -868,6 +883,7 @@ def main():
         extra["plain_f64"] = {
             "value": world * f64_rate, "unit": UNIT, "ms_per_step": rms,
             "roofline_hbm": roofline_hbm(st64, hbm_peak, peak_src),
+            "roofline_fp64_alu_per_class": fp64_alu_roofline(st64, fp64_fma),
             "per_class_first_two_layers": per_class(st64),
             "fp64_fma_per_s_measured": fp64_fma, "fp32_fma_per_s_measured": fp32_fma,
             "note": "complex128 plain kernels (one pass per native op), the full program; per-class times from a "

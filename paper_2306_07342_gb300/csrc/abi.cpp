@@ -32,7 +32,7 @@ const char* kStatNames[SC_COUNT] = {"elem",   "sup1", "uni2",       "sup2",   "f
 
 struct Stat {
   int64_t launches = 0;
-  double ms = 0, bytes = 0, amp_updates = 0;
+  double ms = 0, bytes = 0, amp_updates = 0, fma = 0;
 };
 
 void cuda_check(cudaError_t e, const char* what) {
@@ -169,6 +169,7 @@ static void apply_op(vqd_ctx* c, int inst, const Op& op) {
   static const int cls_of[4] = {SC_ELEM, SC_SUP1, SC_UNI2, SC_SUP2};
   timed(c, cls_of[p.kind], 2.0 * c->bytes(inst) * pass_touched_fraction(p), op.weight * std::ldexp(1.0, 2 * n), 1,
         [&] { return launch_pass(c->prec, c->ptr(inst), n, p, c->stream); });
+  if (c->prof) c->stats[cls_of[p.kind]].fma += pass_fma_per_amp(p, c->prec != VQD_F32) * std::ldexp(1.0, 2 * n);
 }
 
 static std::vector<cd> to_cd(const vqd_c128* m, size_t cnt) {
@@ -1427,6 +1428,7 @@ int vqd_profile_read(vqd_t c, int max, vqd_kstat* out, int* n_out) {
       k.total_ms = c->stats[i].ms;
       k.alg_bytes = c->stats[i].bytes;
       k.amp_updates = c->stats[i].amp_updates;
+      k.alg_fma = c->stats[i].fma;
     }
     cnt++;
   }

@@ -495,6 +495,29 @@ double pass_touched_fraction(const Pass& p) {
   return p.coef.empty() ? 1.0 : (double)touched / (double)p.coef.size();
 }
 
+static double flag_cost(const cd& c) {
+  const int f = flag_of(c);
+  return f == FL_ZERO ? 0.0 : f == FL_CPLX ? 4.0 : 2.0;
+}
+
+double pass_fma_per_amp(const Pass& p, bool fp64) {
+  double sparse = 0.0;
+  const double dense = 4.0 * (double)p.coef.size();
+  for (const cd& c : p.coef) sparse += flag_cost(c);
+  const double used = use_sparse(p.coef, fp64) ? sparse : dense;
+  switch (p.kind) {
+    case KK_ELEM: {  // one multiply per changed amplitude: 2 (real or imaginary factor) or 4 (complex)
+      double t = 0.0;
+      for (const cd& c : p.coef)
+        if (!is_unit_factor(c)) t += flag_cost(c);
+      return t / (double)p.coef.size();
+    }
+    case KK_SUP1: return used / 4.0;                         // 16 coefficients per 4 members
+    case KK_UNI2: return (fp64 ? used : dense) * 8.0 / 16.0;  // each of U's 16 entries used 8 times per 16 members
+    default: return used / 16.0;                              // 256 coefficients per 16 members
+  }
+}
+
 cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s) {
   if (prec == VQD_F32) return launch_pass_t<float>((cx<float>*)state, n, p, s);
   if (prec == VQD_F32_SPLIT) return launch_pass_t<df>((cx<df>*)state, n, p, s);

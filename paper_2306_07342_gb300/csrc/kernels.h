@@ -20,6 +20,11 @@ inline bool is_unit_factor(const std::complex<double>& c) { return c.real() == 1
 // Fraction of the state's amplitudes a plain pass reads and writes: elementwise passes skip the
 // amplitudes whose factor is 1; every other pass touches all of them.
 double pass_touched_fraction(const Pass& p);
+// Real multiply-adds per amplitude of the state that a plain pass issues, counting the structure of its
+// coefficients as the kernels use it (a zero costs nothing, a one two adds, a real or imaginary
+// coefficient two multiply-adds and a complex one four; an elementwise pass only on the amplitudes it
+// changes; the dense form where it is cheaper).  For FP64 these are FP64 instructions.
+double pass_fma_per_amp(const Pass& p, bool fp64);
 cudaError_t launch_pass(int prec, void* state, int n, const Pass& p, cudaStream_t s);
 
 // Initialisation.

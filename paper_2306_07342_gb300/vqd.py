@@ -37,7 +37,7 @@ class c128(ctypes.Structure):
 
 class kstat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
-                ("alg_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double)]
+                ("alg_bytes", ctypes.c_double), ("amp_updates", ctypes.c_double), ("alg_fma", ctypes.c_double)]
 
 
 class sc_device(ctypes.Structure):
@@ -567,7 +567,8 @@ def vqd_profile_read(ctx) -> dict:
     n = ctypes.c_int()
     _check(lib().vqd_profile_read(ctx, 16, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(n)), ctx)
     return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
-                                   "alg_bytes": arr[i].alg_bytes, "amp_updates": arr[i].amp_updates}
+                                   "alg_bytes": arr[i].alg_bytes, "amp_updates": arr[i].amp_updates,
+                                   "alg_fma": arr[i].alg_fma}
             for i in range(min(n.value, 16))}
 
 
