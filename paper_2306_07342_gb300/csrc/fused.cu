@@ -780,52 +780,29 @@ __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, cons
   const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
   const uint32_t ng = 1u << (nbits - 2);
   const Inserter<2> ins(B.lsorted);
-  if (diag) {
-    int F[4];
-#pragma unroll
-    for (int t = 0; t < 4; t++) F[t] = fl[t];
-    for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
-      const uint32_t b = sw<T>(ins(g));
-      const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
+  for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
+    const uint32_t b = sw<T>(ins(g));
+    const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
+    if (diag) {
 #pragma unroll
       for (int t = 0; t < 4; t++)
         if (!(skip >> t & 1u)) {
           cx<T> x = sm[a[t]];
-          cscale_flag<T>(x, c[t], F[t]);
+          cscale_flag<T>(x, c[t], fl[t]);
           sm[a[t]] = x;
         }
-    }
-    return;
-  }
-  // the 16 structure flags are read once per sweep; two groups per iteration give each thread 16
-  // independent accumulation chains
-  int F[16];
+    } else {
+      cx<T> x[4];
 #pragma unroll
-  for (int i = 0; i < 16; i++) F[i] = fl[i];
-  for (uint32_t g = threadIdx.x; g < ng; g += 2 * kThreads) {
-    const bool two = g + kThreads < ng;
-    const uint32_t b0 = sw<T>(ins(g)), b1 = two ? sw<T>(ins(g + kThreads)) : b0;
-    const uint32_t a0[4] = {b0, b0 ^ m1, b0 ^ m2, b0 ^ m1 ^ m2};
-    const uint32_t a1[4] = {b1, b1 ^ m1, b1 ^ m2, b1 ^ m1 ^ m2};
-    cx<T> x0[4], x1[4];
+      for (int t = 0; t < 4; t++) x[t] = sm[a[t]];
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-      x0[t] = sm[a0[t]];
-      x1[t] = sm[a1[t]];
-    }
+      for (int t = 0; t < 4; t++) {
+        CAcc<T> y;
+        y.zero();
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-      CAcc<T> y0, y1;
-      y0.zero();
-      y1.zero();
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const cx<T> cu = c[t * 4 + u];
-        y0.mac(cu, F[t * 4 + u], x0[u]);
-        y1.mac(cu, F[t * 4 + u], x1[u]);
+        for (int u = 0; u < 4; u++) y.mac(c[t * 4 + u], fl[t * 4 + u], x[u]);
+        sm[a[t]] = y.get();
       }
-      sm[a0[t]] = y0.get();
-      if (two) sm[a1[t]] = y1.get();
     }
   }
 }
@@ -856,9 +833,6 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
         }
     } else if (kind == BK_UNI2) {
       // columns: A[:, cc] <- U A[:, cc]; then rows: A[r, :] <- A[r, :] U^dagger (A[r][cc] = member r | cc << 2)
-      int F[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) F[i] = fl[i];
 #pragma unroll 1
       for (int cc = 0; cc < 4; cc++) {
         cx<T> x[4];
@@ -869,7 +843,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
           CAcc<T> t;
           t.zero();
 #pragma unroll
-          for (int m = 0; m < 4; m++) t.mac(c[r * 4 + m], F[r * 4 + m], x[m]);
+          for (int m = 0; m < 4; m++) t.mac(c[r * 4 + m], fl[r * 4 + m], x[m]);
           sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
       }
@@ -886,7 +860,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
           for (int m = 0; m < 4; m++) {
             cx<T> uc = c[cc * 4 + m];
             uc.y = -uc.y;
-            t.mac(uc, F[cc * 4 + m], x[m]);
+            t.mac(uc, fl[cc * 4 + m], x[m]);
           }
           sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
