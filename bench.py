@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--prefix", type=int, default=0, help="--precision: only the first N native ops (0 = all)")
     ap.add_argument("--oracle-plan", action="store_true",
                     help="time the oracle on every configuration (single thread and all cores) and exit")
+    ap.add_argument("--tc-case", type=int, nargs=2, default=None, metavar=("N", "GATES"),
+                    help="profiling case: the ion-trap program on N qubits with GATES gates through the tensor-core "
+                         "blocks (k = 4 3xTF32, k = 4 BF16x3, k = 5 3xTF32), block-kernel times, and exit")
     return ap.parse_args()
 
 
@@ -787,8 +790,40 @@ def run_fp64_diag():
     print(json.dumps(out), flush=True)
 
 
+def run_tc_case(args):
+    """The ion-trap program through the tensor-core blocks on a chosen size: per scheme and k, the block
+    kernel's average time (the library's CUDA events)."""
+    import torch
+    from paper_2306_07342_gb300 import build as _b
+    _b.build()
+    from paper_2306_07342_gb300 import vqd
+    from workloads import config3_ion_alltoall
+    n, gates = args.tc_case
+    prog = config3_ion_alltoall(n=n, n_gates=gates)
+    native = vqd.native_ops(prog.ops)
+    ctx = vqd.vqd_create(n, vqd.VQD_F32, torch.cuda.current_stream().cuda_stream)
+    out = {"n": n, "native_ops": len(native)}
+    try:
+        for k, sc in ((4, vqd.VQD_TC_3XTF32), (4, vqd.VQD_TC_BF16X3), (5, vqd.VQD_TC_3XTF32)):
+            vqd.vqd_run_program_tc(ctx, 0, native[:20], k, sc)
+            vqd.vqd_profile(ctx, 2)
+            vqd.vqd_profile_reset(ctx)
+            vqd.vqd_run_program_tc(ctx, 0, native, k, sc)
+            st = vqd.vqd_profile_read(ctx)
+            vqd.vqd_profile(ctx, 0)
+            g = st["tc_gemm"]
+            out[f"k{k}_{'3xtf32' if sc == 0 else 'bf16x3'}"] = {"blocks": g["launches"], "gemm_ms_avg": g["total_ms"] / g["launches"],
+                                                            "compose_ms_total": st["tc_compose"]["total_ms"]}
+    finally:
+        vqd.vqd_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.tc_case:
+        run_tc_case(args)
+        return
     if args.fp64_diag:
         run_fp64_diag()
         return
