@@ -807,7 +807,7 @@ __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, cons
   }
 }
 
-template <class T>
+template <class T, bool SUP2>
 __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, const TileBlock& B, const cx<T>* __restrict__ c,
                                          const uint8_t* __restrict__ fl, uint32_t skip, int kind) {
   uint32_t soff[16];
@@ -824,7 +824,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     if (kind == BK_DIAG2) {
-#pragma unroll 4
+#pragma unroll
       for (int s = 0; s < 16; s++)
         if (!(skip >> s & 1u)) {
           cx<T> x = sm[b ^ soff[s]];
@@ -833,7 +833,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
         }
     } else if (kind == BK_UNI2) {
       // columns: A[:, cc] <- U A[:, cc]; then rows: A[r, :] <- A[r, :] U^dagger (A[r][cc] = member r | cc << 2)
-#pragma unroll 1
+#pragma unroll
       for (int cc = 0; cc < 4; cc++) {
         cx<T> x[4];
 #pragma unroll
@@ -847,7 +847,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
           sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
       }
-#pragma unroll 1
+#pragma unroll
       for (int r = 0; r < 4; r++) {
         cx<T> x[4];
 #pragma unroll
@@ -865,7 +865,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
           sm[b ^ soff[r | (cc << 2)]] = t.get();
         }
       }
-    } else {
+    } else if constexpr (SUP2) {
       cx<T> x[16];
 #pragma unroll
       for (int s = 0; s < 16; s++) x[s] = sm[b ^ soff[s]];
@@ -885,8 +885,11 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
   }
 }
 
-// Apply the stage's operators (one block each) to the tile, one sweep per operator.
-template <class T>
+// Apply the stage's operators (one block each) to the tile, one sweep per operator.  SUP2 = false leaves
+// out the dense two-qubit superoperator sweep, whose 16 amplitudes in registers would otherwise set the
+// register allocation (and the spills) of the whole stage kernel in FP64 and float-float; the host picks
+// that instantiation for stages without such a block.
+template <class T, bool SUP2 = true>
 __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
                                             const uint8_t* __restrict__ fsm, int nbits,
                                             const TileBlock* __restrict__ blocks, int bb, int be,
@@ -898,7 +901,7 @@ __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>*
     const uint8_t* f = fsm + bo.coef;
     if constexpr (Structured<T>::value) {
       if (bo.kind == BK_DIAG_A || bo.kind == BK_SUP1_A) sweep1_s<T>(sm, nbits, B, c, f, bo.skip, bo.kind == BK_DIAG_A);
-      else sweep2_s<T>(sm, nbits, B, c, f, bo.skip, bo.kind);
+      else sweep2_s<T, SUP2>(sm, nbits, B, c, f, bo.skip, bo.kind);
       __syncthreads();
       continue;
     }
@@ -925,7 +928,7 @@ __device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>
   for (int i = threadIdx.x; i < oe - ob; i += kThreads) sops[i] = bops[ob + i];
 }
 
-template <class T>
+template <class T, bool SUP2>
 __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const StageDesc S,
                                                                        const TileBlock* __restrict__ blocks,
                                                                        const BlockOp* __restrict__ bops,
@@ -948,7 +951,7 @@ __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const 
     const uint64_t base = deposit(t, s_rest, nrest);
     tile_load_async<T>(st, sm, base, s_bits, nbits);
     __syncthreads();
-    tile_blocks<T>(sm, csm, fsm, nbits, blocks, bb, be, sops, S.op_begin);
+    tile_blocks<T, SUP2>(sm, csm, fsm, nbits, blocks, bb, be, sops, S.op_begin);
     tile_io<T, false>(st, sm, base, s_bits, nbits);
     __syncthreads();
   }
@@ -1083,16 +1086,23 @@ static size_t stage_smem(int nbits) {
   return ((size_t)kCoefCap + ((size_t)1 << nbits)) * sizeof(cx<T>) + (size_t)kOpCap * sizeof(BlockOp) + (size_t)kCoefCap;
 }
 
+template <class T, bool SUP2>
+static cudaError_t stage_kt(FusedCache& c, const StageDesc& S, void* state, cudaStream_t s) {
+  const size_t smem = stage_smem<T>(S.nbits);
+  cudaError_t e = cudaFuncSetAttribute(k_stage<T, SUP2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  unsigned grid = persistent_grid(k_stage<T, SUP2>, smem, 1ull << S.nrest);
+  k_stage<T, SUP2><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops,
+                                           (const cx<T>*)c.d_coef, (const uint8_t*)c.d_flag);
+  return cudaGetLastError();
+}
+
 template <class T>
 static cudaError_t stage_t(FusedCache& c, const FusedPlan& p, int stage, void* state, cudaStream_t s) {
   const StageDesc& S = p.stages[stage];
-  const size_t smem = stage_smem<T>(S.nbits);
-  cudaError_t e = cudaFuncSetAttribute(k_stage<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  unsigned grid = persistent_grid(k_stage<T>, smem, 1ull << S.nrest);
-  k_stage<T><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops,
-                                     (const cx<T>*)c.d_coef, (const uint8_t*)c.d_flag);
-  return cudaGetLastError();
+  bool sup2 = !Structured<T>::value;  // complex64 keeps one instantiation
+  for (int o = S.op_begin; o < S.op_end && !sup2; o++) sup2 = p.ops[o].kind == BK_SUP2;
+  return sup2 ? stage_kt<T, true>(c, S, state, s) : stage_kt<T, false>(c, S, state, s);
 }
 
 cudaError_t launch_stage(FusedCache& c, const FusedPlan& p, int stage, int prec, void* state, int n, cudaStream_t s) {
