@@ -144,7 +144,7 @@ def oracle_time(prog, n_ops, threads):
     from oracle import cloop, evolve
     from oracle import compile as oc
     cloop.set_threads(threads)
-    rho = np.array(evolve.initial_state(prog), dtype=np.complex128, order="C")
+    rho = np.ascontiguousarray(evolve.initial_state(prog), dtype=np.complex128)   # no second copy (68.7 GB at n = 16)
     t = time.perf_counter()
     for o in prog.ops[:n_ops]:
         cloop.apply_steps(rho, oc.compile_op(o.name, o.qubits, o.params))
@@ -168,10 +168,11 @@ def oracle_line(name, prog, n_ops, threads, kind):
 
 def cpu_baseline_block(quick=True):
     """The FP64 oracle (plain C loops, OpenMP) on the host cores, on bounded samples of the configurations:
-    configuration 1 in full, the 14-qubit grid on a prefix (all cores and one thread), the 15-qubit ion
-    program on a prefix, the 16-qubit spin chain on one op when the host has the RAM (68.7 GB), and the
-    neutral-atom batch on its first instances, scaled by sum 4^n.  Per-op cost is the same along a program
-    of one kind of op mix, so prefix timings are extrapolated to the full program (labelled)."""
+    configuration 1 in full (all cores and one thread), the 14-qubit grid on a prefix (all cores and one
+    thread), the 15-qubit ion program on a prefix, the 16-qubit spin chain on a prefix when the host has the
+    RAM (68.7 GB), and the neutral-atom batch on its first instances, scaled by sum 4^n.  The per-op cost is
+    about the same along a program of one op mix, so prefix timings are extrapolated to the full program
+    (labelled).  quick = the bench line's bounded samples; otherwise the larger ones of --oracle-plan."""
     from oracle import cloop
     from workloads import (config1_chain6, config2_sc_grid, config3_ion_alltoall, config4_neutral_batch,
                            config5_spin_chain)
@@ -183,20 +184,35 @@ def cpu_baseline_block(quick=True):
     c2 = config2_sc_grid()
     out["lines"].append(oracle_line("sc_grid14 (n=14)", c2, 12 if quick else 60, allc, "all cores"))
     out["lines"].append(oracle_line("sc_grid14 (n=14)", c2, 2 if quick else 12, 1, "one thread"))
-    if not quick:
-        c3 = config3_ion_alltoall()
-        out["lines"].append(oracle_line("ion15 (n=15)", c3, 50, allc, "all cores"))
-        if host_ram_bytes() > 160e9:
-            c5 = config5_spin_chain()
-            out["lines"].append(oracle_line("spin16 (n=16)", c5, 50, allc, "all cores"))
-        progs = config4_neutral_batch(count=1024)
+    c3 = config3_ion_alltoall()
+    out["lines"].append(oracle_line("ion15 (n=15)", c3, 3 if quick else 50, allc, "all cores"))
+    if host_ram_bytes() > 160e9:
+        c5 = config5_spin_chain()
+        out["lines"].append(oracle_line("spin16 (n=16)", c5, 1 if quick else 50, allc, "all cores"))
+    else:
+        out["lines"].append({"config": "spin16 (n=16)", "skipped": "the host has less than 160 GB of RAM for the 68.7 GB FP64 state"})
+    progs = config4_neutral_batch(count=1024)
+    tu = sum(len(q.ops) * 4.0 ** q.n for q in progs)
+    if quick:
+        # one instance per qubit count, its first 100 ops: the per-op time of each size, applied to every
+        # instance of that size
+        t_full = 0.0
+        for m in sorted({q.n for q in progs}):
+            q = next(x for x in progs if x.n == m)
+            k = min(100, len(q.ops))
+            per_op = oracle_time(q, k, allc) / k
+            t_full += per_op * sum(len(x.ops) for x in progs if x.n == m)
+        out["lines"].append({"config": "neutral batch (1024 instances)", "threads": allc, "value": tu / t_full,
+                             "unit": UNIT, "scaled_full_batch_s": t_full,
+                             "kind": "all cores; per-op time of one instance per qubit count (first 100 ops), "
+                                     "scaled to every instance of that size"})
+    else:
         sample = progs[:32]
         t = 0.0
         for q in sample:
             t += oracle_time(q, len(q.ops), allc)
         su = sum(len(q.ops) * 4.0 ** q.n for q in sample)
-        tu = sum(len(q.ops) * 4.0 ** q.n for q in progs)
-        out["lines"].append({"config": "neutral batch (1024 instances)", "threads": allc, "instances_timed": 32,
+        out["lines"].append({"config": "neutral batch (1024 instances)", "threads": allc, "instances_timed": len(sample),
                              "seconds": t, "value": su / t, "unit": UNIT, "scaled_full_batch_s": t * tu / su,
                              "kind": "all cores; scaled by sum 4^n from the first 32 instances"})
     cloop.set_threads(allc)
