@@ -332,6 +332,29 @@ def roofline_hbm(stats, peak, peak_src, steps=1, exclude=("reduce", "init", "tc_
             "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms}
 
 
+DOT2_FP32_OPS = 12  # FP32 operations of one float-float multiply-add in the compensated dot product (dot2_step)
+
+
+def roofline_alu(stats, prec_name, fp32_fma, fp64_fma, kernel="fused_stage"):
+    """The fused stage as an arithmetic-bound kernel: the real multiply-adds its sweeps perform (the library's
+    count: structured for FP64 and float-float, dense complex FMAs for complex64) per second of device time,
+    against the measured FMA rate of the pipe that executes them.  A float-float multiply-add (one step of the
+    compensated dot product) takes 12 FP32 operations, each one issue slot of the FP32 pipe, so its peak is the
+    FP32 FMA rate / 12."""
+    s = stats.get(kernel)
+    if not s or not s["launches"] or not s.get("alg_fma"):
+        return None
+    achieved = s["alg_fma"] / (s["total_ms"] * 1e-3)
+    peak, unit, src = {"split": (fp32_fma / DOT2_FP32_OPS, "float-float multiply-adds/s",
+                                 f"measured FP32 FMA rate / {DOT2_FP32_OPS}"),
+                       "f64": (fp64_fma, "FP64 multiply-adds/s", "measured FP64 FMA rate"),
+                       "f32": (fp32_fma, "FP32 multiply-adds/s", "measured FP32 FMA rate")}[prec_name]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "kernel": kernel, "peak_source": src, "launches": s["launches"],
+            "avg_launch_ms": s["total_ms"] / s["launches"], "alg_fma_per_launch": s["alg_fma"] / s["launches"],
+            "traffic": None}
+
+
 def fp64_alu_roofline(stats, fma_rate):
     """Plain FP64 passes as FP64-arithmetic-bound kernels: the real multiply-adds their structured arithmetic
     issues (the library's count, from the coefficients' zero/one/real/imaginary structure) per second of
@@ -902,7 +925,12 @@ def main():
     ms = replicas.max_over_ranks(ms)
     value = world * args.steps * units_per_step / (ms * 1e-3)
     stats = profiled_step(torch, vqd, ctx, step)                         # per-class times, outside the timed region
-    roof = roofline_hbm(stats, hbm_peak, peak_src)
+    fp64_fma = vqd.vqd_measure_fma_rate(0, sh)
+    fp32_fma = vqd.vqd_measure_fma_rate(1, sh)
+    roof_hbm = roofline_hbm(stats, hbm_peak, peak_src)
+    roof_alu = roofline_alu(stats, args.prec, fp32_fma, fp64_fma) if args.path == "fused" else None
+    # the fused stage is bound by its arithmetic, not by HBM: its roofline is the arithmetic one
+    roof = roof_alu if roof_alu else roof_hbm
     launches = int(sum(v["launches"] for v in stats.values()))
 
     # ---- end to end through the C ABI with host buffers (wall clock; results read back every step)
@@ -919,8 +947,6 @@ def main():
                    "list is a host array compiled and marshalled every step; results copied to host every step"}
 
     extra, error = {}, None
-    fp64_fma = vqd.vqd_measure_fma_rate(0, sh)
-    fp32_fma = vqd.vqd_measure_fma_rate(1, sh)
     if not args.no_extra:
         # ---- the plain FP64 path on the full program: the reference state for every error below
         ref = vqd.vqd_create(n, vqd.VQD_F64, sh)
@@ -964,6 +990,8 @@ def main():
                 if path == "fused" and nsteps > 1:
                     st2 = profiled_step(torch, vqd, c2, s2)
                     rec["roofline"] = roofline_hbm(st2, hbm_peak, peak_src)
+                    rec["roofline_alu"] = roofline_alu(st2, {vqd.VQD_F32: "f32", vqd.VQD_F64: "f64",
+                                                             vqd.VQD_F32_SPLIT: "split"}[pp], fp32_fma, fp64_fma)
                     rec["stages_per_step"] = st2.get("fused_stage", {}).get("launches", 0)
                 extra[name] = rec
             finally:
@@ -1007,7 +1035,7 @@ def main():
                        "l2": "inputs larger than L2 (state of 2.1-4.3 GB vs 129 MB L2), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "error": error, "headline": headline_rec,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "roofline_hbm": roof_hbm, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": ck, "paths": extra, "per_class": per_class(stats),
         }
         print(json.dumps(line), flush=True)

@@ -583,8 +583,9 @@ typedef struct {
   double total_ms;     /* summed CUDA-event durations (0 unless timing was enabled) */
   double alg_bytes;    /* algorithmic bytes: 2 x state bytes per pass (read + write once) */
   double amp_updates;  /* sum over original (pre-fusion) ops of the amplitudes they update */
-  double alg_fma;      /* plain passes: real multiply-adds their structured arithmetic issues (FP64
-                          instructions for VQD_F64), for the roofline of arithmetic-bound passes */
+  double alg_fma;      /* real multiply-adds the class's arithmetic performs (plain passes and fused stages:
+                          structured for VQD_F64 and VQD_F32_SPLIT, dense complex FMAs for fused VQD_F32;
+                          a float-float multiply-add is one), for the roofline of arithmetic-bound kernels */
 } vqd_kstat;
 
 /* mode 0: off; 1: count launches only; 2: count and time every launch with CUDA events. */

@@ -423,6 +423,7 @@ int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int f
   for (size_t s = 0; s < plan.stages.size(); s++) {
     timed(c, SC_FUSED, 2.0 * c->bytes(inst), plan.stages[s].weight * std::ldexp(1.0, 2 * n), 1,
           [&] { return launch_stage(c->fused, plan, (int)s, c->prec, c->ptr(inst), n, c->stream); });
+    if (c->prof) c->stats[SC_FUSED].fma += plan.stages[s].fma_per_amp * std::ldexp(1.0, 2 * n);
   }
   API_END(c)
 }

@@ -201,6 +201,23 @@ static double sweep_cost(const Op& op, double branch) {
   return c / D;
 }
 
+// Real multiply-adds per amplitude of one complex64 sweep, which keeps straight-line complex FMAs: 4 per
+// complex coefficient used (a diagonal: 4 per member it changes).
+static double dense_cost(const Op& op) {
+  const int d = 1 << op.k, D = d * d;
+  if (is_diag(op)) {
+    double c = 0.0;
+    for (int s = 0; s < D; s++) {
+      const int r = s & (d - 1), cc = s >> op.k;
+      const cd f = op.unitary ? diag_unitary_factor(op.m[r * d + r], op.m[cc * d + cc]) : op.m[(size_t)s * D + s];
+      if (f != 1.0) c += 4.0;
+    }
+    return c / D;
+  }
+  if (op.k == 2 && op.unitary) return 4.0 * 16.0 * 8.0 / 16.0;
+  return 4.0 * (double)D;  // D x D coefficients per D members
+}
+
 // The stage's operators are merged into composites on at most two qubits, in FP64.  Open
 // composites are kept on pairwise disjoint qubit sets; an operator merges with the composites it
 // touches when their qubits and its own number at most two, otherwise it first emits them, so
@@ -351,6 +368,7 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
         if (is_unit_factor(plan.coef[t])) bo.skip |= 1u << (t - bo.coef - sd.coef_begin);
     plan.ops.push_back(bo);
     sd.weight += o.weight;
+    sd.fma_per_amp += prec == VQD_F32 ? dense_cost(o) : sweep_cost(o, 0.0);
     tb.op_end = (int)plan.ops.size();
     plan.blocks.push_back(tb);
   }

@@ -41,6 +41,8 @@ struct StageDesc {
   int coef_begin, coef_end;  // this stage's coefficients in the plan's array (<= kCoefCap of them)
   int op_begin, op_end;      // this stage's operator descriptors (<= kOpCap of them)
   double weight;             // original operations applied by this stage
+  double fma_per_amp;        // real multiply-adds of the stage's sweeps per amplitude of the state (arithmetic as
+                             // the kernel performs it: dense for complex64, structured for FP64 and float-float)
 };
 
 struct FusedPlan {
