@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--path", default="fused", choices=["plain", "fused"], help="path of the headline")
     ap.add_argument("--prec", default="split", choices=["split", "f64", "f32"], help="precision of the headline")
     ap.add_argument("--no-extra", action="store_true", help="only the headline (profiling runs)")
+    ap.add_argument("--general", action="store_true",
+                    help="fused paths without VQD_HERMITIAN (every tile of every stage; the state need not be Hermitian)")
     ap.add_argument("--no-large", action="store_true", help="skip the 15- and 16-qubit lines")
     ap.add_argument("--rows", type=int, default=2, help="grid rows (profiling cases only; the benchmark is 2x7)")
     ap.add_argument("--cols", type=int, default=7)
@@ -405,13 +407,13 @@ def profiled_step(torch, vqd, ctx, step):
     return st
 
 
-def make_step(vqd, ctx, n, native, path, fuse=0, tc=None):
+def make_step(vqd, ctx, n, native, path, fuse=0, tc=None, flags=0):
     def step():
         vqd.vqd_init_zero(ctx, 0)
         if path == "plain":
             vqd.vqd_apply_native(ctx, 0, native)
         elif path == "fused":
-            vqd.vqd_run_program(ctx, 0, native, fuse)
+            vqd.vqd_run_program(ctx, 0, native, fuse, flags)
         else:
             vqd.vqd_run_program_tc(ctx, 0, native, tc[0], tc[1])
         vqd.vqd_prob(ctx, 0, list(range(n)))
@@ -485,7 +487,7 @@ def measure_trajectories_spin16(vqd, stream_handle, ntraj=256):
             "note": "16-qubit statevectors on 8-CTA clusters; the density matrix (34 GB) is the plain path's"}
 
 
-def measure_sc_device(vqd, torch, stream_handle, timed, steps):
+def measure_sc_device(vqd, torch, stream_handle, timed, steps, flags=0):
     """A second workload: the superconducting device model of Sec. 8 on a 2x7 transmon grid (App. C
     parameter ranges), a depth-60 hardware-efficient ansatz compiled by vqd_sc_compile (static ZZ on every
     coupling, thermal T1/T2 decay, readout noise), run through the fused path in complex64 from the
@@ -501,7 +503,7 @@ def measure_sc_device(vqd, torch, stream_handle, timed, steps):
     try:
         def step():
             vqd.vqd_init_product_diag(ctx, 0, dev["excited"])
-            vqd.vqd_run_program(ctx, 0, native)
+            vqd.vqd_run_program(ctx, 0, native, 0, flags)
             vqd.vqd_prob(ctx, 0, list(range(n)))
             vqd.vqd_trace(ctx, 0)
         ms, st, _ = timed(step, steps, 1, ctx)
@@ -509,6 +511,7 @@ def measure_sc_device(vqd, torch, stream_handle, timed, steps):
         return {"value": steps * units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
                 "logical_gates": len(logical), "native_ops": len(native), "host_compile_s": compile_s,
                 "stages_per_step": st.get("fused_stage", {}).get("launches", 0) // steps,
+                "hermitian_stages": bool(flags),
                 "note": "fused path, default fusion width 6; amp-updates counted over the compiled native ops"}
     finally:
         vqd.vqd_destroy(ctx)
@@ -689,7 +692,7 @@ def measure_ion15(torch, vqd, stream, bf16_peak):
     return out
 
 
-def measure_spin16(torch, vqd, stream):
+def measure_spin16(torch, vqd, stream, herm=0):
     """The 16-qubit spin chain (2000 gates, 4000 native ops), the largest single-GPU configuration: the density
     matrix is 34.4 GB in complex64 and 68.7 GB in float-float.  Both through the fused path, once each;
     complex64's error is stated against the float-float run (FP64-class: float-float is within 1e-13 of FP64
@@ -703,7 +706,7 @@ def measure_spin16(torch, vqd, stream):
     out = {"workload": "silicon-spin / NV-like chain, 16 qubits, 2000 gates (4000 native ops)", "native_ops": len(native)}
     ref = vqd.vqd_create(n, vqd.VQD_F32_SPLIT, sh)
     try:
-        ms, _ = timed_steps(torch, vqd, stream, ref, make_step(vqd, ref, n, native, "fused"), 1, 0)
+        ms, _ = timed_steps(torch, vqd, stream, ref, make_step(vqd, ref, n, native, "fused", flags=herm), 1, 0)
         out["fused_split"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                               "state_bytes": vqd.vqd_state_bytes(n, vqd.VQD_F32_SPLIT)}
         ctx = vqd.vqd_create(n, vqd.VQD_F32, sh)
@@ -721,7 +724,7 @@ def measure_spin16(torch, vqd, stream):
     return out
 
 
-def measure_batch(vqd, torch, count):
+def measure_batch(vqd, torch, count, herm=0):
     """Neutral-atom-like batch: `count` instances with n ~ U{6..12} in one batched run (stage waves of persistent
     kernels replayed as one CUDA graph), with the fusion width and tile shape picked by the batch autotuner
     (candidates timed on the batch itself), against one launch sequence per instance (fused and plain) on every
@@ -734,13 +737,14 @@ def measure_batch(vqd, torch, count):
     ns = [p.n for p in progs]
     units = sum(len(p.ops) * 4.0 ** p.n for p in progs)
     bstream = torch.cuda.Stream()                          # a capturable stream: the batch becomes a CUDA graph
-    choice = autotune.tune_batch(ns, vqd.VQD_F32, arrays, bstream.cuda_stream)
+    choice = autotune.tune_batch(ns, vqd.VQD_F32, arrays, bstream.cuda_stream, flags=herm)
+    herm = choice["flags"]
     ctx = vqd.vqd_create_batch(ns, vqd.VQD_F32, bstream.cuda_stream)
     try:
         fuse = autotune.apply(ctx, choice)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        vqd.vqd_run_batch(ctx, arrays, fuse)                 # first run: compile, plan, capture, launch
+        vqd.vqd_run_batch(ctx, arrays, fuse, herm)           # first run: compile, plan, capture, launch
         torch.cuda.synchronize()
         first_wall = time.perf_counter() - t0
         vqd.vqd_profile(ctx, 2)
@@ -748,7 +752,7 @@ def measure_batch(vqd, torch, count):
         t0 = time.perf_counter()
         for i in range(count):
             vqd.vqd_init_zero(ctx, i)
-        vqd.vqd_run_batch(ctx, arrays, fuse)                 # same batch again: one graph launch
+        vqd.vqd_run_batch(ctx, arrays, fuse, herm)           # same batch again: one graph launch
         bstream.synchronize()
         t1 = time.perf_counter()
         probs, trs, purs = vqd.vqd_batch_reduce(ctx, ns)     # every instance's results, one launch, one read-back
@@ -763,12 +767,15 @@ def measure_batch(vqd, torch, count):
         res = {}
         for path in ("fused", "plain"):
             for i in sample[:2]:
-                (vqd.vqd_run_program if path == "fused" else vqd.vqd_apply_native)(ctx, i, arrays[i])
+                if path == "fused":
+                    vqd.vqd_run_program(ctx, i, arrays[i], fuse, herm)
+                else:
+                    vqd.vqd_apply_native(ctx, i, arrays[i])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for i in sample:
                 if path == "fused":
-                    vqd.vqd_run_program(ctx, i, arrays[i], fuse)
+                    vqd.vqd_run_program(ctx, i, arrays[i], fuse, herm)
                 else:
                     vqd.vqd_apply_native(ctx, i, arrays[i])
             torch.cuda.synchronize()
@@ -778,7 +785,7 @@ def measure_batch(vqd, torch, count):
                 "first_run_value": units / first_wall, "first_run_s": first_wall,
                 "instances": count, "native_ops": int(sum(len(a) for a in arrays)), "amp_updates": units,
                 "kernel_s": kern_s, "wall_s": wall, "batch_reduce_s": reduce_wall,
-                "autotuned": {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")},
+                "autotuned": {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits", "hermitian")},
                 "autotune_trials": choice["trials"],
                 "state_bytes": int(sum(vqd.vqd_state_bytes(n, vqd.VQD_F32) for n in ns)),
                 "one_launch_sequence_per_instance": {
@@ -911,15 +918,18 @@ def main():
 
     prec = {"split": vqd.VQD_F32_SPLIT, "f64": vqd.VQD_F64, "f32": vqd.VQD_F32}[args.prec]
     layer_ops = len(prog.ops) // prog.meta["depth"]
+    # every state here is a density matrix: the fused paths use its Hermiticity (VQD_HERMITIAN)
+    herm = 0 if args.general else vqd.VQD_HERMITIAN
 
     # ---- headline: the FP64-class fused path (float-float) on the full program
     ctx = vqd.vqd_create(n, prec, sh)
     fuse = 0
     choice = None
     if args.path == "fused":
-        choice = autotune.tune(n, prec, native, sh, prefix=3 * layer_ops)   # outside the timed region
+        choice = autotune.tune(n, prec, native, sh, prefix=3 * layer_ops, flags=herm)   # outside the timed region
         fuse = autotune.apply(ctx, choice)
-    step = make_step(vqd, ctx, n, native, args.path, fuse)
+    run_flags = choice["flags"] if choice else 0
+    step = make_step(vqd, ctx, n, native, args.path, fuse, flags=run_flags)
     clocks = ClockSampler(local)
     ms, ck = timed_steps(torch, vqd, stream, ctx, step, args.steps, args.warmup, clocks, sync_all)
     ms = replicas.max_over_ranks(ms)
@@ -968,25 +978,33 @@ def main():
         error = state_error(torch, vqd, ref, vqd.VQD_F64, ctx, prec)
         error["vs"] = "plain FP64 (complex128) run of the same program on the same GPU"
         # ---- the other paths on the full program, each with its error against the FP64 state
-        paths = [("fused_f64", vqd.VQD_F64, "fused", 1), ("plain_split", vqd.VQD_F32_SPLIT, "plain", 1),
-                 ("fused_c64", vqd.VQD_F32, "fused", min(args.steps, 5)), ("plain_c64", vqd.VQD_F32, "plain", 2)]
-        for name, pp, path, nsteps in paths:
-            if pp == prec and path == args.path:
+        paths = [("fused_f64", vqd.VQD_F64, "fused", 1, herm), ("plain_split", vqd.VQD_F32_SPLIT, "plain", 1, 0),
+                 ("fused_c64", vqd.VQD_F32, "fused", min(args.steps, 5), herm), ("plain_c64", vqd.VQD_F32, "plain", 2, 0)]
+        if herm:   # the same fused paths without the Hermitian stages
+            paths += [("fused_split_general", vqd.VQD_F32_SPLIT, "fused", 1, 0),
+                      ("fused_f64_general", vqd.VQD_F64, "fused", 1, 0),
+                      ("fused_c64_general", vqd.VQD_F32, "fused", min(args.steps, 5), 0)]
+        for name, pp, path, nsteps, fl in paths:
+            if pp == prec and path == args.path and fl == herm:
                 continue
             c2 = vqd.vqd_create(n, pp, sh)
             try:
                 f2 = 0
                 tuned = None
-                if path == "fused" and pp == vqd.VQD_F32:
-                    tuned = autotune.tune(n, pp, native, sh, prefix=10 * layer_ops)
+                if path == "fused":
+                    tuned = autotune.tune(n, pp, native, sh, prefix=(10 if pp == vqd.VQD_F32 else 3) * layer_ops,
+                                          flags=fl)
                     f2 = autotune.apply(c2, tuned)
-                s2 = make_step(vqd, c2, n, native, path, f2)
+                    fl = tuned["flags"]
+                s2 = make_step(vqd, c2, n, native, path, f2, flags=fl)
                 ms2, _ = timed_steps(torch, vqd, stream, c2, s2, nsteps, 1 if nsteps > 1 else 0)
                 rec = {"value": world * nsteps * units_per_step / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / nsteps,
                        "steps": nsteps, "error_vs_plain_f64": state_error(torch, vqd, ref, vqd.VQD_F64, c2, pp)}
                 rec["speedup_vs_plain_f64"] = rec["value"] / (world * f64_rate)
                 if tuned:
                     rec["autotuned"] = {k: tuned[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")}
+                if path == "fused":
+                    rec["hermitian_stages"] = bool(fl & vqd.VQD_HERMITIAN)
                 if path == "fused" and nsteps > 1:
                     st2 = profiled_step(torch, vqd, c2, s2)
                     rec["roofline"] = roofline_hbm(st2, hbm_peak, peak_src)
@@ -998,22 +1016,25 @@ def main():
                 vqd.vqd_destroy(c2)
         vqd.vqd_destroy(ref)
         torch.cuda.empty_cache()
-    headline_rec = {"speedup_vs_plain_f64": (value / extra["plain_f64"]["value"]) if "plain_f64" in extra else None}
+    headline_rec = {"speedup_vs_plain_f64": (value / extra["plain_f64"]["value"]) if "plain_f64" in extra else None,
+                    "hermitian_stages": bool(run_flags & vqd.VQD_HERMITIAN)}
+    if "fused_split_general" in extra and args.prec == "split":
+        headline_rec["speedup_vs_fused_general"] = value / extra["fused_split_general"]["value"]
     if choice:
-        headline_rec["autotuned"] = {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")}
+        headline_rec["autotuned"] = {k: choice[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits", "hermitian")}
     vqd.vqd_destroy(ctx)
     torch.cuda.empty_cache()
 
     if not args.no_extra and not args.no_large:
         extra["ion15_tensor_core"] = measure_ion15(torch, vqd, stream, bf16_peak)
-        extra["spin16"] = measure_spin16(torch, vqd, stream)
+        extra["spin16"] = measure_spin16(torch, vqd, stream, herm)
     if not args.no_extra:
         extra["trajectories_c64"] = measure_trajectories(vqd, torch, prog, native, sh)
         extra["sc_device_compiled_c64"] = measure_sc_device(vqd, torch, sh, timed_legacy(torch, vqd, stream), 3)
         extra["trajectories_spin16_c64"] = measure_trajectories_spin16(vqd, sh)
         extra["nv5_noise_sweep_batch_c64"] = measure_nv_noise_sweep(vqd, torch)
         if args.batch_count > 0:
-            extra["batch_c64"] = measure_batch(vqd, torch, args.batch_count)
+            extra["batch_c64"] = measure_batch(vqd, torch, args.batch_count, herm)
 
     cpu = None
     if rank == 0 and not args.no_extra:

@@ -136,6 +136,13 @@ typedef struct {
 /* Flags for compilation and run calls (bitwise or). */
 #define VQD_T2_IS_TOTAL 1u  /* read T2 as the total coherence time: dephase with T_phi, 1/T2 = 1/(2T1) + 1/T_phi */
 #define VQD_NO_CHECK 2u     /* skip the unitarity / CPTN checks of apply_unitary / apply_kraus */
+/* vqd_run_program / vqd_run_batch / vqd_plan_info: the caller asserts that the state is Hermitian, as every
+ * density matrix is (Sec. 2).  The fused path then updates only the tiles on or above the diagonal of
+ * its tile grid and writes each one's conjugate transpose into the mirror tile, halving the arithmetic of a
+ * stage; the state it leaves is exactly Hermitian (lower triangle = conjugate of the upper one, real
+ * diagonal).  Ignored for programs with an operator that does not preserve Hermiticity (every native op
+ * does).  Do not set it for other operators, such as |i><j| when propagating a process basis. */
+#define VQD_HERMITIAN 4u
 
 /* ------------------------------------------------------------------------------------------
  * Contexts and states
@@ -251,13 +258,15 @@ int vqd_compile_op(const vqd_native_op* op, unsigned flags, int* is_unitary, int
 
 /* Tile shape of the fused and batched paths of a context: tile_bits index bits per shared-memory tile
  * (<= 13 for VQD_F32, <= 12 for VQD_F64 and VQD_F32_SPLIT: a 64 KB tile; 0 = that maximum) of which
- * passenger_bits (0..3; -1 = default 3 for VQD_F32, 2 otherwise) are the lowest row bits, carried along so that
- * every tile is made of contiguous DRAM runs.  Needs 4 + passenger_bits <= tile_bits.  Results do
+ * passenger_bits (0..3; -1 = default 3 for VQD_F32, 2 otherwise; 2 and 1 for a VQD_HERMITIAN run) are the lowest
+ * row bits, carried along so that every tile is made of contiguous DRAM runs (a VQD_HERMITIAN run carries their
+ * column bits too and rounds tile_bits down to even).  Needs 4 + passenger_bits <= tile_bits.  Results do
  * not depend on the shape; speed does (the autotuner in the Python package picks it). */
 int vqd_set_tile_shape(vqd_t ctx, int tile_bits, int passenger_bits);
 
 /* Plan of the fused path for an n-qubit program, without running it (host only); tile_bits and
- * passenger_bits as in vqd_set_tile_shape.  info[0..7] =
+ * passenger_bits as in vqd_set_tile_shape, flags as in vqd_run_program (VQD_HERMITIAN plans the Hermitian
+ * stages).  info[0..7] =
  * {stages (one pass over the state each), blocks (one shared-memory sweep each), operators after
  * composition that are diagonal / 1-qubit superoperators / 2-qubit unitaries / 2-qubit
  * superoperators, largest tile (index bits), original operators}. */

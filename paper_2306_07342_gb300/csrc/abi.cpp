@@ -70,6 +70,7 @@ struct vqd_ctx {
   uint64_t batch_key = 0;
   cudaGraphExec_t batch_graph = nullptr;
   std::vector<int> batch_passes;
+  std::vector<double> batch_traffic;  // state sizes read and written per instance (1 + frac per stage)
   std::vector<size_t> batch_nops;
   int64_t batch_waves = 0;
   TileShape shape;           // tile shape of the fused and batched paths (defaults per precision)
@@ -418,12 +419,14 @@ int vqd_run_program(vqd_t c, int inst, int nops, const vqd_native_op* ops, int f
   need_inst(c, inst);
   std::vector<Op> list = compile_list(c, inst, nops, ops, flags);
   const int n = c->n[inst];
-  FusedPlan plan = plan_fused(list, n, c->prec, fuse_qubits, c->shape);
+  FusedPlan plan = plan_fused(list, n, c->prec, fuse_qubits, c->shape, (flags & VQD_HERMITIAN) != 0);
   upload_plan(c->fused, plan, c->prec, c->stream);
   for (size_t s = 0; s < plan.stages.size(); s++) {
-    timed(c, SC_FUSED, 2.0 * c->bytes(inst), plan.stages[s].weight * std::ldexp(1.0, 2 * n), 1,
+    // a stage reads the tiles it runs (a fraction frac of the state) and writes the whole state
+    const StageDesc& sd = plan.stages[s];
+    timed(c, SC_FUSED, (1.0 + sd.frac) * c->bytes(inst), sd.weight * std::ldexp(1.0, 2 * n), 1,
           [&] { return launch_stage(c->fused, plan, (int)s, c->prec, c->ptr(inst), n, c->stream); });
-    if (c->prof) c->stats[SC_FUSED].fma += plan.stages[s].fma_per_amp * std::ldexp(1.0, 2 * n);
+    if (c->prof) c->stats[SC_FUSED].fma += sd.fma_per_amp * sd.frac * std::ldexp(1.0, 2 * n);
   }
   API_END(c)
 }
@@ -453,7 +456,7 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
   auto account = [&](int64_t launches, F_LAUNCH launch) {
     double bytes = 0, upd = 0;
     for (int i = 0; i < count; i++) {
-      bytes += 2.0 * c->bytes(i) * c->batch_passes[i];
+      bytes += c->bytes(i) * c->batch_traffic[i];
       upd += (double)c->batch_nops[i] * std::ldexp(1.0, 2 * c->n[i]);
     }
     timed(c, SC_BATCH, bytes, upd, launches, launch);
@@ -474,7 +477,7 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
       try {
         std::vector<Op> list = compile_list(c, i, (int)(offsets[i + 1] - offsets[i]), ops + offsets[i], flags);
         nops[i] = list.size();
-        plans[i] = plan_fused(list, c->n[i], c->prec, fuse_qubits, c->shape);
+        plans[i] = plan_fused(list, c->n[i], c->prec, fuse_qubits, c->shape, (flags & VQD_HERMITIAN) != 0);
       } catch (const Error& e) {
         codes[i] = e.code;
         errs[i] = e.what();
@@ -497,6 +500,9 @@ int vqd_run_batch(vqd_t c, const int64_t* offsets, const vqd_native_op* ops, int
   }
   upload_batch(c->batch, plan, c->prec, c->stream);
   c->batch_passes = plan.passes;
+  c->batch_traffic.assign(count, 0.0);
+  for (int i = 0; i < count; i++)
+    for (const StageDesc& sd : plans[i].stages) c->batch_traffic[i] += 1.0 + sd.frac;
   c->batch_nops = nops;
   c->batch_waves = (int64_t)plan.wave_begin.size() - 1;
   // On a stream that can be captured (not the legacy default stream), the waves are captured into
@@ -640,7 +646,7 @@ int vqd_plan_info(int n, int prec, int nops, const vqd_native_op* ops, int fuse_
   TileShape shape;
   shape.tile_bits = tile_bits;
   shape.passengers = passenger_bits;
-  FusedPlan plan = plan_fused(list, n, prec, fuse_qubits, shape);
+  FusedPlan plan = plan_fused(list, n, prec, fuse_qubits, shape, (flags & VQD_HERMITIAN) != 0);
   for (int i = 0; i < 8; i++) info[i] = 0;
   info[0] = (int64_t)plan.stages.size();
   info[1] = (int64_t)plan.blocks.size();

@@ -29,16 +29,42 @@
 namespace vqd {
 
 int tile_bits_budget(int prec) { return prec == VQD_F32 ? 13 : 12; }  // 64 KB tiles
-int default_passengers(int prec) { return prec == VQD_F32 ? 3 : 2; }    // 64-byte runs
+// 64-byte runs; a Hermitian plan's tiles carry the passengers' column bits as well, so it takes 32-byte
+// runs (one DRAM sector) to keep the same number of stage qubits.
+int default_passengers(int prec, bool herm) {
+  if (herm) return prec == VQD_F32 ? 2 : 1;
+  return prec == VQD_F32 ? 3 : 2;
+}
 static int default_fuse(int prec) { (void)prec; return 6; }
 
 static int popc(uint32_t x) { return __builtin_popcount(x); }
 
-static int stage_bit_count(uint32_t qmask, int L) {
+// Tile bits of a stage on qubits qmask with L passengers: both index bits of every stage qubit and the
+// passengers' row bits (general plan), or both index bits of every stage or passenger qubit (Hermitian plan).
+static int stage_bit_count(uint32_t qmask, int L, bool herm) {
+  if (herm) return 2 * popc(qmask | ((1u << L) - 1u));
   int c = 2 * popc(qmask);
   for (int b = 0; b < L; b++)
     if (!(qmask >> b & 1)) c++;
   return c;
+}
+
+// A map preserves Hermiticity when its superoperator satisfies S[(c,r),(c',r')] = conj S[(r,c),(r',c')]
+// (s = r | c << k): true of U rho U^dagger and of every Kraus map sum_i K_i rho K_i^dagger (Sec. 2).
+bool preserves_hermiticity(const Op& op) {
+  if (op.unitary) return true;
+  const int d = 1 << op.k, D = d * d;
+  double scale = 0;
+  for (const cd& v : op.m) scale = std::max(scale, std::abs(v));
+  const double tol = 1e-12 * std::max(1.0, scale);
+  for (int s = 0; s < D; s++) {
+    const int ts = (s >> op.k) | (s & (d - 1)) << op.k;
+    for (int t = 0; t < D; t++) {
+      const int tt = (t >> op.k) | (t & (d - 1)) << op.k;
+      if (std::abs(op.m[(size_t)ts * D + tt] - std::conj(op.m[(size_t)s * D + t])) > tol) return false;
+    }
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------- operator algebra (FP64, host)
@@ -310,7 +336,7 @@ static int member_coefs(const Op& op, int nq, const int* bq, std::vector<cd>& ou
 }
 
 static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::vector<int>& idx, uint32_t qmask,
-                        int n, int L, bool whole, int prec) {
+                        int n, int L, bool whole, int prec, bool herm) {
   // Blocks, members and their coefficients first: a stage whose coefficients overflow the shared
   // memory budget is split in two (each half is a valid stage on the same tile).
   const std::vector<Op> comp = compose_stage(ops, idx, prec);
@@ -318,8 +344,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   for (const Op& o : comp) ncoef += is_diag(o) ? (o.k == 1 ? 4 : 16) : (o.k == 1 ? 16 : (o.unitary ? 16 : 256));
   if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap) && idx.size() > 1) {
     std::vector<int> a(idx.begin(), idx.begin() + idx.size() / 2), b(idx.begin() + idx.size() / 2, idx.end());
-    build_stage(plan, ops, a, qmask, n, L, whole, prec);
-    build_stage(plan, ops, b, qmask, n, L, whole, prec);
+    build_stage(plan, ops, a, qmask, n, L, whole, prec, herm);
+    build_stage(plan, ops, b, qmask, n, L, whole, prec, herm);
     return;
   }
   StageDesc sd;
@@ -329,6 +355,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
     for (int b = 0; b < 2 * n; b++) in_tile[b] = true;
   } else {
     for (int b = 0; b < std::min(L, n); b++) in_tile[b] = true;
+    if (herm)
+      for (int b = 0; b < std::min(L, n); b++) in_tile[b + n] = true;
     for (int q = 0; q < n; q++)
       if (qmask >> q & 1) in_tile[q] = in_tile[q + n] = true;
   }
@@ -341,6 +369,12 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
       local[b] = -1;
       sd.rest[sd.nrest++] = b;
     }
+  }
+  sd.herm = herm && !whole && sd.nrest > 0;
+  sd.frac = 1.0;
+  if (sd.herm) {
+    const double K = std::ldexp(1.0, sd.nrest / 2);
+    sd.frac = (K + 1.0) / (2.0 * K);
   }
   sd.block_begin = (int)plan.blocks.size();
   sd.coef_begin = (int)plan.coef.size();
@@ -382,8 +416,10 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   plan.stages.push_back(sd);
 }
 
-FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qubits, TileShape shape) {
+FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qubits, TileShape shape, bool herm) {
   FusedPlan plan;
+  for (size_t i = 0; i < ops_in.size() && herm; i++) herm = preserves_hermiticity(ops_in[i]);
+  plan.herm = herm;
   std::vector<Op> ops;
   ops.reserve(ops_in.size());
   for (const Op& o : ops_in) {
@@ -395,10 +431,14 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
       ops.push_back(o);
     }
   }
-  const int budget = shape.tile_bits > 0 ? shape.tile_bits : tile_bits_budget(prec);
-  const int Lset = shape.passengers >= 0 ? shape.passengers : default_passengers(prec);
-  if (budget > tile_bits_budget(prec) || Lset > 3 || budget < 4 + Lset)
+  const int tb = shape.tile_bits > 0 ? shape.tile_bits : tile_bits_budget(prec);
+  const int Lset = shape.passengers >= 0 ? shape.passengers : default_passengers(prec, herm);
+  if (tb > tile_bits_budget(prec) || Lset > 3 || tb < 4 + Lset)
     throw Error(VQD_EINVAL, "tile shape: need 4 + passengers <= tile bits <= the precision's maximum, passengers <= 3");
+  // a Hermitian tile has an even number of bits and room for a two-qubit operator beside the passengers
+  const int budget = herm ? tb & ~1 : tb;
+  if (herm && budget < 2 * (Lset + 2))
+    throw Error(VQD_EINVAL, "tile shape: a Hermitian plan needs 2 (passengers + 2) <= tile bits");
   const int L = std::min(Lset, n);
   int f = fuse_qubits <= 0 ? default_fuse(prec) : fuse_qubits;
   if (f < 2 || f > VQD_MAX_FUSE) throw Error(VQD_EINVAL, "fuse_qubits must be in 2..6");
@@ -406,7 +446,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
   if (2 * n <= budget) {  // the whole state is one tile: one stage holds every operator
     std::vector<int> all(ops.size());
     for (size_t i = 0; i < ops.size(); i++) all[i] = (int)i;
-    build_stage(plan, ops, all, (1u << n) - 1, n, L, true, prec);
+    build_stage(plan, ops, all, (1u << n) - 1, n, L, true, prec, herm);
     return plan;
   }
   const uint32_t full = (1u << n) - 1;
@@ -428,7 +468,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
         dmask |= m;
       } else {
         uint32_t q2 = q | m;
-        if (popc(q2) <= f && stage_bit_count(q2, L) <= budget) {
+        if (popc(q2) <= f && stage_bit_count(q2, L, herm) <= budget) {
           q = q2;
           stage.push_back(remaining[i]);
         } else {
@@ -441,7 +481,7 @@ FusedPlan plan_fused(const std::vector<Op>& ops_in, int n, int prec, int fuse_qu
         break;
       }
     }
-    build_stage(plan, ops, stage, q, n, L, false, prec);
+    build_stage(plan, ops, stage, q, n, L, false, prec, herm);
     std::vector<int> next;
     next.reserve(deferred.size() + remaining.size() - i);
     next.insert(next.end(), deferred.begin(), deferred.end());
@@ -500,7 +540,7 @@ BatchPlan merge_batch(const std::vector<FusedPlan>& plans, const std::vector<int
       const BatchInst& bi = bp.inst[i];
       if ((int)w >= bi.stage_end - bi.stage_begin) continue;
       const int s = bi.stage_begin + (int)w;
-      const uint32_t ntiles = 1u << bp.all.stages[s].nrest;
+      const uint32_t ntiles = (uint32_t)stage_work_tiles(bp.all.stages[s]);
       for (uint32_t t = 0; t < ntiles; t += kChunk) bp.items.push_back({i, s, t, std::min(kChunk, ntiles - t)});
     }
   }
@@ -635,6 +675,93 @@ __device__ __forceinline__ void tile_load_async(const cx<T>* __restrict__ st, cx
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---- Hermitian stages.  Tile u of a Hermitian stage is the u-th pair (R, C), R <= C, of row and column
+// rest indices, ordered by C then R: C = floor((sqrt(8u + 1) - 1) / 2), R = u - C (C + 1) / 2.
+__device__ __forceinline__ void tri_pair(uint64_t u, uint64_t& R, uint64_t& C) {
+  uint64_t c = (uint64_t)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
+  while (c > 0 && c * (c + 1) / 2 > u) c--;  // the FP64 root is off by at most one either way
+  while ((c + 1) * (c + 2) / 2 <= u) c++;
+  C = c;
+  R = u - c * (c + 1) / 2;
+}
+
+// Tile-local bits of a Hermitian stage: l = i | j << h, i the row index and j the column index over the
+// same h qubits.  The mirror store walks local bit order(k): row bits 0..r0-1 (distinct shared-memory banks
+// across a quarter warp), then the column bits (the mirror's row bits, so contiguous DRAM runs), then the
+// remaining row bits.
+__device__ __forceinline__ int mirror_order(int k, int h, int r0) {
+  return k < r0 ? k : (k < r0 + h ? h + (k - r0) : k - h);
+}
+
+// Write the conjugate transpose of the tile in shared memory to its mirror tile at base64: element (i, j)
+// goes to row j, column i.  A tile bit at local position b < h (row) is a column bit of the mirror,
+// global position bits[b + h]; a column bit (b >= h) is a row bit of the mirror, bits[b - h].
+template <class T>
+__device__ __forceinline__ void tile_store_mirror(cx<T>* __restrict__ st, const cx<T>* __restrict__ sm, uint64_t base64,
+                                                  const int* bits, int nbits) {
+  const uint32_t size = 1u << nbits;
+  if (threadIdx.x >= size) return;
+  const int h = nbits >> 1, r0 = min(h, 3), lowbits = min(nbits, 8);
+  cx<T>* __restrict__ sb = st + base64;
+  uint32_t lt = 0, gt = 0;
+  for (int k = 0; k < lowbits; k++)
+    if (threadIdx.x >> k & 1u) {
+      const int b = mirror_order(k, h, r0);
+      lt |= 1u << b;
+      gt |= 1u << bits[b < h ? b + h : b - h];
+    }
+  const int hib = nbits - lowbits;
+  const int iters = 1 << hib;
+  constexpr int K = 8;
+  for (int it0 = 0; it0 < iters; it0 += K) {
+    cx<T> v[K];
+    uint32_t g[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (it0 + k < iters) {
+        const uint32_t it = (uint32_t)(it0 + k);
+        uint32_t l = lt, gg = gt;
+        for (int e = 0; e < hib; e++)
+          if (it >> e & 1u) {
+            const int b = mirror_order(lowbits + e, h, r0);
+            l |= 1u << b;
+            gg |= 1u << bits[b < h ? b + h : b - h];
+          }
+        v[k] = sm[sw<T>(l)];
+        v[k].y = -v[k].y;
+        g[k] = gg;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+      if (it0 + k < iters) sb[g[k]] = v[k];
+  }
+}
+
+// Store a diagonal tile (R = C) of a Hermitian stage: the upper triangle (i < j) as computed, the lower one
+// as its conjugate transpose and the diagonal with its imaginary part dropped, so that the stored state is
+// exactly Hermitian (the mathematical result is; the two triangles differ only by rounding).
+template <class T>
+__device__ __forceinline__ void tile_store_diag(cx<T>* __restrict__ st, const cx<T>* __restrict__ sm, uint64_t base64,
+                                                const int* bits, int nbits) {
+  const uint32_t size = 1u << nbits, h = (uint32_t)nbits >> 1, hm = (1u << h) - 1u;
+  cx<T>* __restrict__ sb = st + base64;
+  for (uint32_t l = threadIdx.x; l < size; l += kThreads) {
+    const uint32_t i = l & hm, j = l >> h;
+    cx<T> v;
+    if (i > j) {
+      v = sm[sw<T>(j | i << h)];
+      v.y = -v.y;
+    } else {
+      v = sm[sw<T>(l)];
+      if (i == j) v.y = T(0.0);
+    }
+    uint32_t g = 0;
+    for (int b = 0; b < nbits; b++) g |= ((l >> b) & 1u) << bits[b];
+    sb[g] = v;
+  }
 }
 
 // Structured arithmetic (coefficient flags, see compose_stage) for FP64 and float-float; complex64
@@ -934,6 +1061,54 @@ __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>*
   }
 }
 
+// Tile index of work item u: u itself, or in a Hermitian stage the pair (R, C) of tri_pair, t = R | C << m.
+// Returns 0 for a general tile, 1 for a diagonal tile of a Hermitian stage, 2 for an off-diagonal one
+// (whose mirror tile index C | R << m goes to *tm).
+__device__ __forceinline__ int tile_of(uint64_t u, bool herm, int nrest, uint64_t* t, uint64_t* tm) {
+  if (!herm) {
+    *t = u;
+    return 0;
+  }
+  const int m = nrest >> 1;
+  uint64_t R, C;
+  tri_pair(u, R, C);
+  *t = R | C << m;
+  *tm = C | R << m;
+  return R == C ? 1 : 2;
+}
+
+// Store phase of a tile (kept out of line, so that the sweeps' register allocation is that of the general
+// stage): the tile itself, and in a Hermitian stage the mirror or the symmetrised diagonal tile.
+template <class T>
+__device__ __noinline__ void stage_tile_store(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, const int* s_bits,
+                                              int nbits, const int* s_rest, int nrest, bool herm, uint64_t u) {
+  uint64_t t, tm = 0;
+  const int kind = tile_of(u, herm, nrest, &t, &tm);
+  const uint64_t base = deposit(t, s_rest, nrest);
+  if (kind == 1) {
+    tile_store_diag<T>(st, sm, base, s_bits, nbits);
+  } else {
+    tile_io<T, false>(st, sm, base, s_bits, nbits);
+    if (kind == 2) tile_store_mirror<T>(st, sm, deposit(tm, s_rest, nrest), s_bits, nbits);
+  }
+}
+
+// One tile of a stage: load, apply the stage's blocks, store (and, in a Hermitian stage, the mirror).
+template <class T, bool SUP2>
+__device__ __forceinline__ void stage_tile(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
+                                           const uint8_t* __restrict__ fsm, const int* s_bits, int nbits,
+                                           const int* s_rest, int nrest, bool herm, uint64_t u,
+                                           const TileBlock* __restrict__ blocks, int bb, int be,
+                                           const BlockOp* __restrict__ sops, int op0) {
+  uint64_t t, tm;
+  tile_of(u, herm, nrest, &t, &tm);
+  tile_load_async<T>(st, sm, deposit(t, s_rest, nrest), s_bits, nbits);
+  __syncthreads();
+  tile_blocks<T, SUP2>(sm, csm, fsm, nbits, blocks, bb, be, sops, op0);
+  stage_tile_store<T>(st, sm, s_bits, nbits, s_rest, nrest, herm, u);
+  __syncthreads();
+}
+
 template <class T>
 __device__ __forceinline__ void stage_coefs(cx<T>* __restrict__ csm, const cx<T>* __restrict__ coef,
                                             uint8_t* __restrict__ fsm, const uint8_t* __restrict__ flag, int cb, int ce,
@@ -964,15 +1139,10 @@ __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const 
   uint8_t* fsm = reinterpret_cast<uint8_t*>(sops + kOpCap);
   stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
   __syncthreads();
-  const uint64_t ntiles = 1ull << nrest;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = deposit(t, s_rest, nrest);
-    tile_load_async<T>(st, sm, base, s_bits, nbits);
-    __syncthreads();
-    tile_blocks<T, SUP2>(sm, csm, fsm, nbits, blocks, bb, be, sops, S.op_begin);
-    tile_io<T, false>(st, sm, base, s_bits, nbits);
-    __syncthreads();
-  }
+  const uint64_t ntiles = stage_work_tiles(S);
+  for (uint64_t u = blockIdx.x; u < ntiles; u += gridDim.x)
+    stage_tile<T, SUP2>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, S.herm != 0, u, blocks, bb, be, sops,
+                        S.op_begin);
 }
 
 // One wave of the batched path: CTAs take (instance, stage, tile chunk) items from an atomic
@@ -1014,14 +1184,10 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
     }
     cx<T>* st = all + inst[W.inst].offset_amps;
     const int nbits = S.nbits, nrest = S.nrest, op0 = S.op_begin;
-    for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++) {
-      const uint64_t base = deposit(t, s_rest, nrest);
-      tile_load_async<T>(st, sm, base, s_bits, nbits);
-      __syncthreads();
-      tile_blocks<T>(sm, csm, fsm, nbits, blocks, S.block_begin, S.block_end, sops, op0);
-      tile_io<T, false>(st, sm, base, s_bits, nbits);
-      __syncthreads();
-    }
+    const bool herm = S.herm != 0;
+    for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++)
+      stage_tile<T, true>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, herm, t, blocks, S.block_begin,
+                          S.block_end, sops, op0);
   }
 }
 
@@ -1109,7 +1275,7 @@ static cudaError_t stage_kt(FusedCache& c, const StageDesc& S, void* state, cuda
   const size_t smem = stage_smem<T>(S.nbits);
   cudaError_t e = cudaFuncSetAttribute(k_stage<T, SUP2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  unsigned grid = persistent_grid(k_stage<T, SUP2>, smem, 1ull << S.nrest);
+  unsigned grid = persistent_grid(k_stage<T, SUP2>, smem, stage_work_tiles(S));
   k_stage<T, SUP2><<<grid, 256, smem, s>>>((cx<T>*)state, S, (const TileBlock*)c.d_blocks, (const BlockOp*)c.d_ops,
                                            (const cx<T>*)c.d_coef, (const uint8_t*)c.d_flag);
   return cudaGetLastError();

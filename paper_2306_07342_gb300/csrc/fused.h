@@ -43,9 +43,21 @@ struct StageDesc {
   double weight;             // original operations applied by this stage
   double fma_per_amp;        // real multiply-adds of the stage's sweeps per amplitude of the state (arithmetic as
                              // the kernel performs it: dense for complex64, structured for FP64 and float-float)
+  int herm;                  // 1: Hermitian stage (see plan_fused): rows and columns of the tile on the same qubits,
+                             // rest[] = the m row rest bits then the same qubits' m column rest bits (nrest = 2m),
+                             // and only the tiles whose row rest index is <= their column rest index run
+  double frac;               // fraction of the state's amplitudes this stage reads (1, or (K + 1) / 2K for K = 2^m)
 };
 
+// Tiles that one pass of the stage processes: 2^nrest, or K (K + 1) / 2 for a Hermitian stage.
+__host__ __device__ inline uint64_t stage_work_tiles(const StageDesc& s) {
+  if (!s.herm) return 1ull << s.nrest;
+  const uint64_t K = 1ull << (s.nrest / 2);
+  return K * (K + 1) / 2;
+}
+
 struct FusedPlan {
+  bool herm = false;  // planned on symmetric tiles (Hermitian stages)
   std::vector<StageDesc> stages;
   std::vector<TileBlock> blocks;
   std::vector<BlockOp> ops;
@@ -63,7 +75,15 @@ struct TileShape {
 
 // Group the compiled operators of one n-qubit instance into stages of at most `fuse_qubits`
 // qubits (0 = default) whose tiles have the given shape.
-FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits, TileShape shape = TileShape());
+// herm: the state is Hermitian (a density matrix).  If every operator also preserves Hermiticity
+// (S[(c,r),(c',r')] = conj S[(r,c),(r',c')], true of every Kraus map), the stages are planned on symmetric
+// tiles (the passenger qubits' column bits join the tile) and each stage runs only the tiles on or above
+// the diagonal of the tile grid; an off-diagonal tile also writes its conjugate transpose into its mirror
+// tile, a diagonal tile writes its upper triangle's conjugate into its lower one (and a real diagonal),
+// so that the whole state stays exactly Hermitian.  Otherwise the plan is the general one.
+FusedPlan plan_fused(const std::vector<Op>& ops, int n, int prec, int fuse_qubits, TileShape shape = TileShape(),
+                     bool herm = false);
+bool preserves_hermiticity(const Op& op);
 
 // Per-instance description used by the batched kernel.
 struct BatchInst {
@@ -115,6 +135,6 @@ cudaError_t launch_batch(FusedCache& c, const BatchPlan& p, int prec, void* base
 
 // Largest tile (index bits) the shared-memory budget allows for a precision, and the defaults.
 int tile_bits_budget(int prec);
-int default_passengers(int prec);
+int default_passengers(int prec, bool herm = false);
 
 }  // namespace vqd

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvqd.so")
 
 VQD_F64, VQD_F32, VQD_F32_SPLIT = 0, 1, 2
-VQD_T2_IS_TOTAL, VQD_NO_CHECK = 1, 2
+VQD_T2_IS_TOTAL, VQD_NO_CHECK, VQD_HERMITIAN = 1, 2, 4
 VQD_OK, VQD_EINVAL, VQD_ENOMEM, VQD_ENOTCP, VQD_EDEVICE, VQD_ENOTSUP = 0, -1, -2, -3, -4, -5
 VQD_MAX_QUBITS = 16
 VQD_MAX_FUSE = 6

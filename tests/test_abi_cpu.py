@@ -225,3 +225,23 @@ def test_tc_plan_blocks_keep_per_qubit_order_and_cover_every_op(vqd):
         prev = info["blocks"]
     with pytest.raises(vqd.VQDError):
         vqd.vqd_tc_plan_info(15, prog.ops, 7)
+
+
+def test_hermitian_plan_symmetric_tiles(vqd):
+    """VQD_HERMITIAN plans (host only): symmetric tiles have an even bit count within the tile budget, the
+    stage count stays close to the general plan's (the passengers' column bits take the place of one
+    passenger row bit), and a shape without room for a two-qubit operator beside the passengers' row and
+    column bits is refused."""
+    from workloads import config2_sc_grid
+    prog = config2_sc_grid()
+    for prec in (vqd.VQD_F64, vqd.VQD_F32_SPLIT, vqd.VQD_F32):
+        gen = vqd.vqd_plan_info(14, prec, prog.ops)
+        herm = vqd.vqd_plan_info(14, prec, prog.ops, flags=vqd.VQD_HERMITIAN)
+        assert herm["max_tile_bits"] % 2 == 0 and herm["max_tile_bits"] <= 12
+        assert herm["native_ops"] == gen["native_ops"]
+        assert 0.8 * gen["stages"] <= herm["stages"] <= 1.35 * gen["stages"], (prec, gen, herm)
+    small = random_program(12, 8, 40).ops
+    assert vqd.vqd_plan_info(8, vqd.VQD_F64, small, tile_bits=6, passenger_bits=2)["stages"] > 0
+    with pytest.raises(vqd.VQDError) as e:
+        vqd.vqd_plan_info(8, vqd.VQD_F64, small, flags=vqd.VQD_HERMITIAN, tile_bits=6, passenger_bits=2)
+    assert e.value.code == vqd.VQD_EINVAL
