@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--path", default="fused", choices=["plain", "fused"], help="path of the headline")
     ap.add_argument("--prec", default="split", choices=["split", "f64", "f32"], help="precision of the headline")
     ap.add_argument("--no-extra", action="store_true", help="only the headline (profiling runs)")
+    ap.add_argument("--fixed-shape", action="store_true",
+                    help="headline without the autotuner: the library's default fusion width and tile shape (profiling)")
     ap.add_argument("--general", action="store_true",
                     help="fused paths without VQD_HERMITIAN (every tile of every stage; the state need not be Hermitian)")
     ap.add_argument("--no-large", action="store_true", help="skip the 15- and 16-qubit lines")
@@ -925,10 +927,10 @@ def main():
     ctx = vqd.vqd_create(n, prec, sh)
     fuse = 0
     choice = None
-    if args.path == "fused":
+    if args.path == "fused" and not args.fixed_shape:
         choice = autotune.tune(n, prec, native, sh, prefix=3 * layer_ops, flags=herm)   # outside the timed region
         fuse = autotune.apply(ctx, choice)
-    run_flags = choice["flags"] if choice else 0
+    run_flags = choice["flags"] if choice else (herm if args.path == "fused" else 0)
     step = make_step(vqd, ctx, n, native, args.path, fuse, flags=run_flags)
     clocks = ClockSampler(local)
     ms, ck = timed_steps(torch, vqd, stream, ctx, step, args.steps, args.warmup, clocks, sync_all)

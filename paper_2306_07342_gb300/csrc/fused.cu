@@ -371,6 +371,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
     }
   }
   sd.herm = herm && !whole && sd.nrest > 0;
+  if (sd.herm && (sd.nbits > 12 || sd.nbits % 2 != 0))
+    throw Error(VQD_EINVAL, "internal: a Hermitian tile has an even number of bits, at most 12");
   sd.frac = 1.0;
   if (sd.herm) {
     const double K = std::ldexp(1.0, sd.nrest / 2);
@@ -601,10 +603,18 @@ __device__ __forceinline__ uint64_t deposit(uint64_t t, const int* pos, int cnt)
   return r;
 }
 
+// Amplitudes a thread moves per batch in the tile and mirror stores (loads from shared memory in flight before
+// the global stores).  The stores follow the sweeps in the same kernel, and larger batches raise the register
+// allocation of the whole stage kernel (spilling in the sweeps): these are the largest batches, per precision,
+// that leave the float-float stage kernels without spills and the others with the fewest.
+template <class T> struct StoreBatch { static constexpr int io = 8, mirror = 2; };
+template <> struct StoreBatch<df> { static constexpr int io = 2, mirror = 2; };
+template <> struct StoreBatch<float> { static constexpr int io = 2, mirror = 4; };
+
 // Move one tile between HBM and shared memory.  Local index l = tid + it * 256; its global offset
 // is deposit(l, bits) = deposit(tid) + deposit(it * 256), the second advanced with the
 // masked-increment identity next = ((x | ~M) + 1) & M.  Each thread moves its amplitudes in
-// batches of 16 independent accesses, so that 16 loads per thread are in flight at once.
+// batches of StoreBatch<T>::io independent accesses (that many loads per thread in flight at once).
 template <class T, bool LOAD>
 __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, uint64_t base64, const int* bits,
                                         int nbits) {
@@ -620,7 +630,7 @@ __device__ __forceinline__ void tile_io(cx<T>* __restrict__ st, cx<T>* __restric
   const int iters = nbits > 8 ? 1 << (nbits - 8) : 1;
   const uint32_t swt = sw<T>(threadIdx.x);
   uint32_t hi = 0;
-  constexpr int K = 8;
+  constexpr int K = StoreBatch<T>::io;
   for (int it0 = 0; it0 < iters; it0 += K) {
     cx<T> v[K];
     uint32_t h = hi;
@@ -695,43 +705,60 @@ __device__ __forceinline__ int mirror_order(int k, int h, int r0) {
   return k < r0 ? k : (k < r0 + h ? h + (k - r0) : k - h);
 }
 
+// Offsets of the mirror store, computed once per stage from the stage's bits into shared memory: entries
+// [0, 16) hold the tile-local offsets of the iteration bits (tile bits walked per iteration, beyond the 8 thread
+// bits) and [16, 32) their mirror global offsets; entries 32 + t and 32 + 256 + t the tile-local and mirror global
+// offsets of thread t's bits.  A Hermitian tile has at most 12 bits, so at most 16 iterations.  (Read from shared
+// memory inside the tile loop, these offsets are not held in registers across the sweeps.)
+constexpr int kMirrorIters = 16;
+constexpr int kMirrorTable = 2 * kMirrorIters + 2 * 256;
+__device__ __forceinline__ void mirror_table(uint32_t* s_mir, const int* bits, int nbits) {
+  const int h = nbits >> 1, r0 = min(h, 3), lowbits = min(nbits, 8), hib = nbits - lowbits;
+  const uint32_t t = threadIdx.x;
+  if (t < (1u << hib) && t < (uint32_t)kMirrorIters) {
+    uint32_t l = 0, g = 0;
+    for (int e = 0; e < hib; e++)
+      if (t >> e & 1u) {
+        const int b = mirror_order(lowbits + e, h, r0);
+        l |= 1u << b;
+        g |= 1u << bits[b < h ? b + h : b - h];
+      }
+    s_mir[t] = l;
+    s_mir[kMirrorIters + t] = g;
+  }
+  uint32_t l = 0, g = 0;
+  for (int k = 0; k < lowbits; k++)
+    if (t >> k & 1u) {
+      const int b = mirror_order(k, h, r0);
+      l |= 1u << b;
+      g |= 1u << bits[b < h ? b + h : b - h];
+    }
+  s_mir[2 * kMirrorIters + t] = l;
+  s_mir[2 * kMirrorIters + 256 + t] = g;
+}
+
 // Write the conjugate transpose of the tile in shared memory to its mirror tile at base64: element (i, j)
 // goes to row j, column i.  A tile bit at local position b < h (row) is a column bit of the mirror,
-// global position bits[b + h]; a column bit (b >= h) is a row bit of the mirror, bits[b - h].
+// global position bits[b + h]; a column bit (b >= h) is a row bit of the mirror, bits[b - h].  Offsets from
+// mirror_table.
 template <class T>
 __device__ __forceinline__ void tile_store_mirror(cx<T>* __restrict__ st, const cx<T>* __restrict__ sm, uint64_t base64,
-                                                  const int* bits, int nbits) {
+                                                  int nbits, const uint32_t* __restrict__ s_mir) {
   const uint32_t size = 1u << nbits;
   if (threadIdx.x >= size) return;
-  const int h = nbits >> 1, r0 = min(h, 3), lowbits = min(nbits, 8);
   cx<T>* __restrict__ sb = st + base64;
-  uint32_t lt = 0, gt = 0;
-  for (int k = 0; k < lowbits; k++)
-    if (threadIdx.x >> k & 1u) {
-      const int b = mirror_order(k, h, r0);
-      lt |= 1u << b;
-      gt |= 1u << bits[b < h ? b + h : b - h];
-    }
-  const int hib = nbits - lowbits;
-  const int iters = 1 << hib;
-  constexpr int K = 8;
+  const uint32_t lt = s_mir[2 * kMirrorIters + threadIdx.x], gt = s_mir[2 * kMirrorIters + 256 + threadIdx.x];
+  const int iters = 1 << (nbits - min(nbits, 8));
+  constexpr int K = StoreBatch<T>::mirror;
   for (int it0 = 0; it0 < iters; it0 += K) {
     cx<T> v[K];
     uint32_t g[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (it0 + k < iters) {
-        const uint32_t it = (uint32_t)(it0 + k);
-        uint32_t l = lt, gg = gt;
-        for (int e = 0; e < hib; e++)
-          if (it >> e & 1u) {
-            const int b = mirror_order(lowbits + e, h, r0);
-            l |= 1u << b;
-            gg |= 1u << bits[b < h ? b + h : b - h];
-          }
-        v[k] = sm[sw<T>(l)];
+        v[k] = sm[sw<T>(lt | s_mir[it0 + k])];
         v[k].y = -v[k].y;
-        g[k] = gg;
+        g[k] = gt | s_mir[kMirrorIters + it0 + k];
       }
     }
 #pragma unroll
@@ -1061,51 +1088,59 @@ __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>*
   }
 }
 
-// Tile index of work item u: u itself, or in a Hermitian stage the pair (R, C) of tri_pair, t = R | C << m.
-// Returns 0 for a general tile, 1 for a diagonal tile of a Hermitian stage, 2 for an off-diagonal one
-// (whose mirror tile index C | R << m goes to *tm).
+// Tile index of work item u: u itself, or in a Hermitian stage the tile (R, C), t = R | C << m, of group
+// u >> 2b (the pair (R_h, C_h) of tri_pair) and item u & (4^b - 1) (R_l | C_l << b), R = R_l | R_h << b and
+// C = C_l | C_h << b.  Returns 0 for a general tile, 1 for a diagonal tile of a Hermitian stage, 2 for an
+// off-diagonal one (whose mirror tile index C | R << m goes to *tm), -1 for an item with nothing to do.
 __device__ __forceinline__ int tile_of(uint64_t u, bool herm, int nrest, uint64_t* t, uint64_t* tm) {
   if (!herm) {
     *t = u;
     return 0;
   }
-  const int m = nrest >> 1;
-  uint64_t R, C;
-  tri_pair(u, R, C);
+  const int m = nrest >> 1, b = herm_group_bits(nrest);
+  uint64_t Rh, Ch;
+  tri_pair(u >> (2 * b), Rh, Ch);
+  const uint64_t w = u & ((1ull << (2 * b)) - 1), Rl = w & ((1ull << b) - 1), Cl = w >> b;
+  if (Rh == Ch && Rl > Cl) return -1;
+  const uint64_t R = Rl | Rh << b, C = Cl | Ch << b;
   *t = R | C << m;
   *tm = C | R << m;
   return R == C ? 1 : 2;
 }
 
-// Store phase of a tile (kept out of line, so that the sweeps' register allocation is that of the general
-// stage): the tile itself, and in a Hermitian stage the mirror or the symmetrised diagonal tile.
-template <class T>
-__device__ __noinline__ void stage_tile_store(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, const int* s_bits,
-                                              int nbits, const int* s_rest, int nrest, bool herm, uint64_t u) {
-  uint64_t t, tm = 0;
-  const int kind = tile_of(u, herm, nrest, &t, &tm);
-  const uint64_t base = deposit(t, s_rest, nrest);
-  if (kind == 1) {
-    tile_store_diag<T>(st, sm, base, s_bits, nbits);
-  } else {
-    tile_io<T, false>(st, sm, base, s_bits, nbits);
-    if (kind == 2) tile_store_mirror<T>(st, sm, deposit(tm, s_rest, nrest), s_bits, nbits);
-  }
-}
-
-// One tile of a stage: load, apply the stage's blocks, store (and, in a Hermitian stage, the mirror).
+// One tile of a stage: load, apply the stage's blocks, store (and, in a Hermitian stage, the mirror tile or the
+// symmetrised diagonal tile).  The tile's offsets and kind pass from before the sweeps to the store phase through
+// shared memory (s_io, written by thread 0 and read after the load's barrier), so that nothing besides the
+// sweeps' own values is held in registers across them.
 template <class T, bool SUP2>
 __device__ __forceinline__ void stage_tile(cx<T>* __restrict__ st, cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
                                            const uint8_t* __restrict__ fsm, const int* s_bits, int nbits,
                                            const int* s_rest, int nrest, bool herm, uint64_t u,
                                            const TileBlock* __restrict__ blocks, int bb, int be,
-                                           const BlockOp* __restrict__ sops, int op0) {
-  uint64_t t, tm;
-  tile_of(u, herm, nrest, &t, &tm);
-  tile_load_async<T>(st, sm, deposit(t, s_rest, nrest), s_bits, nbits);
+                                           const BlockOp* __restrict__ sops, int op0, const uint32_t* s_mir,
+                                           uint64_t* s_io) {
+  {
+    uint64_t t = 0, tm = 0;
+    const int kind = tile_of(u, herm, nrest, &t, &tm);
+    if (kind < 0) return;  // uniform across the CTA
+    const uint64_t base = deposit(t, s_rest, nrest);
+    if (threadIdx.x == 0) {
+      s_io[0] = base;
+      s_io[1] = kind == 2 ? deposit(tm, s_rest, nrest) : 0;
+      s_io[2] = (uint64_t)kind;
+    }
+    tile_load_async<T>(st, sm, base, s_bits, nbits);
+  }
   __syncthreads();
   tile_blocks<T, SUP2>(sm, csm, fsm, nbits, blocks, bb, be, sops, op0);
-  stage_tile_store<T>(st, sm, s_bits, nbits, s_rest, nrest, herm, u);
+  const uint64_t base = s_io[0];
+  const int kind = (int)s_io[2];
+  if (kind == 1) {
+    tile_store_diag<T>(st, sm, base, s_bits, nbits);
+  } else {
+    tile_io<T, false>(st, sm, base, s_bits, nbits);
+    if (kind == 2) tile_store_mirror<T>(st, sm, s_io[1], nbits, s_mir);
+  }
   __syncthreads();
 }
 
@@ -1137,12 +1172,18 @@ __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const 
   const int nbits = S.nbits, nrest = S.nrest, bb = S.block_begin, be = S.block_end;
   BlockOp* sops = reinterpret_cast<BlockOp*>(sm + (1u << nbits));
   uint8_t* fsm = reinterpret_cast<uint8_t*>(sops + kOpCap);
+  __shared__ uint32_t s_mir[kMirrorTable];
+  __shared__ uint64_t s_io[3];
   stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
   __syncthreads();
+  if (S.herm) {
+    mirror_table(s_mir, s_bits, nbits);
+    __syncthreads();
+  }
   const uint64_t ntiles = stage_work_tiles(S);
   for (uint64_t u = blockIdx.x; u < ntiles; u += gridDim.x)
     stage_tile<T, SUP2>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, S.herm != 0, u, blocks, bb, be, sops,
-                        S.op_begin);
+                        S.op_begin, s_mir, s_io);
 }
 
 // One wave of the batched path: CTAs take (instance, stage, tile chunk) items from an atomic
@@ -1166,6 +1207,8 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
   __shared__ int item;
   __shared__ int s_bits[kMaxTileBits];
   __shared__ int s_rest[2 * VQD_MAX_QUBITS];
+  __shared__ uint32_t s_mir[kMirrorTable];
+  __shared__ uint64_t s_io[3];
   int cur = -1;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1);
@@ -1180,6 +1223,10 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
       if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
       stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
       __syncthreads();
+      if (S.herm) {
+        mirror_table(s_mir, s_bits, S.nbits);
+        __syncthreads();
+      }
       cur = W.stage;
     }
     cx<T>* st = all + inst[W.inst].offset_amps;
@@ -1187,7 +1234,7 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
     const bool herm = S.herm != 0;
     for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++)
       stage_tile<T, true>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, herm, t, blocks, S.block_begin,
-                          S.block_end, sops, op0);
+                          S.block_end, sops, op0, s_mir, s_io);
   }
 }
 

@@ -49,11 +49,22 @@ struct StageDesc {
   double frac;               // fraction of the state's amplitudes this stage reads (1, or (K + 1) / 2K for K = 2^m)
 };
 
-// Tiles that one pass of the stage processes: 2^nrest, or K (K + 1) / 2 for a Hermitian stage.
+// Work items of a Hermitian stage come in groups of 2^b x 2^b tiles (b = kHermGroupBits, at most m) that share
+// the high bits of their row and column rest indices: the groups on or above the diagonal of the grid of groups,
+// K_h (K_h + 1) / 2 of them for K_h = K / 2^b, each with every (low row bits, low column bits) pair.  Tiles
+// processed together then fill whole DRAM lines with both their own stores and their mirror stores (the lowest
+// rest bits are the lowest qubits outside the tile).  In a diagonal group the items below the diagonal do
+// nothing.
+constexpr int kHermGroupBits = 2;
+__host__ __device__ inline int herm_group_bits(int nrest) {
+  return nrest / 2 < kHermGroupBits ? nrest / 2 : kHermGroupBits;
+}
+// Work items of one pass of the stage: 2^nrest tiles, or the Hermitian stage's groups of tiles.
 __host__ __device__ inline uint64_t stage_work_tiles(const StageDesc& s) {
   if (!s.herm) return 1ull << s.nrest;
-  const uint64_t K = 1ull << (s.nrest / 2);
-  return K * (K + 1) / 2;
+  const int b = herm_group_bits(s.nrest);
+  const uint64_t Kh = 1ull << (s.nrest / 2 - b);
+  return (Kh * (Kh + 1) / 2) << (2 * b);
 }
 
 struct FusedPlan {
