@@ -995,36 +995,43 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
   const Inserter<4> ins(B.lsorted);
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
-    if (kind == BK_DIAG2) {
-#pragma unroll
+    if (kind == BK_DIAG2) {  // rolled, as the unitary's loops below
+#pragma unroll 1
       for (int s = 0; s < 16; s++)
         if (!(skip >> s & 1u)) {
-          cx<T> x = sm[b ^ soff[s]];
+          const uint32_t o = ((s & 1) ? soff[1] : 0u) ^ ((s & 2) ? soff[2] : 0u) ^ ((s & 4) ? soff[4] : 0u) ^
+                             ((s & 8) ? soff[8] : 0u);
+          cx<T> x = sm[b ^ o];
           cscale_flag<T>(x, c[s], fl[s]);
-          sm[b ^ soff[s]] = x;
+          sm[b ^ o] = x;
         }
     } else if (kind == BK_UNI2) {
-      // columns: A[:, cc] <- U A[:, cc]; then rows: A[r, :] <- A[r, :] U^dagger (A[r][cc] = member r | cc << 2)
-#pragma unroll
+      // columns: A[:, cc] <- U A[:, cc]; then rows: A[r, :] <- A[r, :] U^dagger (A[r][cc] = member r | cc << 2).
+      // The loops stay rolled (one copy of a 4-term body instead of 32 terms): the stage kernel holds every
+      // sweep inline, and its leading stall was instruction fetch.  The swizzle is XOR-linear, so a member's
+      // offset is the XOR of its bits' offsets: soff[r | cc << 2] = soff[r] ^ soff[cc << 2].
+#pragma unroll 1
       for (int cc = 0; cc < 4; cc++) {
+        const uint32_t oc = ((cc & 1) ? soff[4] : 0u) ^ ((cc & 2) ? soff[8] : 0u);
         cx<T> x[4];
 #pragma unroll
-        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[m | (cc << 2)]];
-#pragma unroll
+        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[m] ^ oc];
+#pragma unroll 1
         for (int r = 0; r < 4; r++) {
           CAcc<T> t;
           t.zero();
 #pragma unroll
           for (int m = 0; m < 4; m++) t.mac(c[r * 4 + m], fl[r * 4 + m], x[m]);
-          sm[b ^ soff[r | (cc << 2)]] = t.get();
+          sm[b ^ ((r & 1) ? soff[1] : 0u) ^ ((r & 2) ? soff[2] : 0u) ^ oc] = t.get();
         }
       }
-#pragma unroll
+#pragma unroll 1
       for (int r = 0; r < 4; r++) {
+        const uint32_t orr = ((r & 1) ? soff[1] : 0u) ^ ((r & 2) ? soff[2] : 0u);
         cx<T> x[4];
 #pragma unroll
-        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[r | (m << 2)]];
-#pragma unroll
+        for (int m = 0; m < 4; m++) x[m] = sm[b ^ orr ^ soff[m << 2]];
+#pragma unroll 1
         for (int cc = 0; cc < 4; cc++) {
           CAcc<T> t;
           t.zero();
@@ -1034,7 +1041,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
             uc.y = -uc.y;
             t.mac(uc, fl[cc * 4 + m], x[m]);
           }
-          sm[b ^ soff[r | (cc << 2)]] = t.get();
+          sm[b ^ orr ^ ((cc & 1) ? soff[4] : 0u) ^ ((cc & 2) ? soff[8] : 0u)] = t.get();
         }
       }
     } else if constexpr (SUP2) {
