@@ -342,7 +342,7 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   const std::vector<Op> comp = compose_stage(ops, idx, prec);
   size_t ncoef = 0;
   for (const Op& o : comp) ncoef += is_diag(o) ? (o.k == 1 ? 4 : 16) : (o.k == 1 ? 16 : (o.unitary ? 16 : 256));
-  if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap) && idx.size() > 1) {
+  if ((ncoef > (size_t)kCoefCap || comp.size() > (size_t)kOpCap || comp.size() > (size_t)kBlockCap) && idx.size() > 1) {
     std::vector<int> a(idx.begin(), idx.begin() + idx.size() / 2), b(idx.begin() + idx.size() / 2, idx.end());
     build_stage(plan, ops, a, qmask, n, L, whole, prec, herm);
     build_stage(plan, ops, b, qmask, n, L, whole, prec, herm);
@@ -412,8 +412,8 @@ static void build_stage(FusedPlan& plan, const std::vector<Op>& ops, const std::
   sd.block_end = (int)plan.blocks.size();
   sd.coef_end = (int)plan.coef.size();
   sd.op_end = (int)plan.ops.size();
-  if (sd.coef_end - sd.coef_begin > kCoefCap || sd.op_end - sd.op_begin > kOpCap)
-    throw Error(VQD_EINVAL, "internal: stage coefficients exceed budget");
+  if (sd.coef_end - sd.coef_begin > kCoefCap || sd.op_end - sd.op_begin > kOpCap || sd.block_end - sd.block_begin > kBlockCap)
+    throw Error(VQD_EINVAL, "internal: stage coefficients or blocks exceed budget");
   plan.max_bits = std::max(plan.max_bits, sd.nbits);
   plan.stages.push_back(sd);
 }
@@ -945,13 +945,59 @@ __device__ __forceinline__ void sweep2(cx<T>* __restrict__ sm, int nbits, const 
 // coefficient and structure flag from shared memory (a broadcast: every thread reads the same word)
 // instead of holding all of them in registers, and a two-qubit unitary U A U^dagger is applied as a
 // column pass and a row pass over 4-member vectors.  This keeps the live state to a few amplitudes per
-// thread, so that two CTAs (16 warps) fit on an SM to hide the long dependency chains.
+// thread, so that two CTAs (16 warps) fit on an SM to hide the long dependency chains.  A one-qubit sweep
+// takes two groups per iteration when the tile has at least two per thread: two independent chains per
+// coefficient, and one coefficient read for both.
 template <class T>
 __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, const TileBlock& B, const cx<T>* __restrict__ c,
                                          const uint8_t* __restrict__ fl, uint32_t skip, bool diag) {
   const uint32_t m1 = sw<T>(1u << B.lbit[0]), m2 = sw<T>(1u << B.lbit[1]);
   const uint32_t ng = 1u << (nbits - 2);
   const Inserter<2> ins(B.lsorted);
+  if (ng >= 2 * kThreads) {  // two groups per iteration: each coefficient read serves both
+    for (uint32_t g = threadIdx.x; g < ng; g += 2 * kThreads) {
+      const uint32_t b0 = sw<T>(ins(g)), b1 = sw<T>(ins(g + kThreads));
+      const uint32_t a0[4] = {b0, b0 ^ m1, b0 ^ m2, b0 ^ m1 ^ m2};
+      const uint32_t a1[4] = {b1, b1 ^ m1, b1 ^ m2, b1 ^ m1 ^ m2};
+      if (diag) {
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if (!(skip >> t & 1u)) {
+            cx<T> x0 = sm[a0[t]], x1 = sm[a1[t]];
+            const cx<T> ct = c[t];
+            const int ft = fl[t];
+            cscale_flag<T>(x0, ct, ft);
+            cscale_flag<T>(x1, ct, ft);
+            sm[a0[t]] = x0;
+            sm[a1[t]] = x1;
+          }
+      } else {
+        cx<T> x0[4], x1[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          x0[t] = sm[a0[t]];
+          x1[t] = sm[a1[t]];
+        }
+#pragma unroll 1
+        for (int t = 0; t < 4; t++) {
+          CAcc<T> y0, y1;
+          y0.zero();
+          y1.zero();
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const cx<T> cu = c[t * 4 + u];
+            const int fu = fl[t * 4 + u];
+            y0.mac(cu, fu, x0[u]);
+            y1.mac(cu, fu, x1[u]);
+          }
+          const uint32_t o = ((t & 1) ? m1 : 0u) ^ ((t & 2) ? m2 : 0u);
+          sm[b0 ^ o] = y0.get();
+          sm[b1 ^ o] = y1.get();
+        }
+      }
+    }
+    return;
+  }
   for (uint32_t g = threadIdx.x; g < ng; g += kThreads) {
     const uint32_t b = sw<T>(ins(g));
     const uint32_t a[4] = {b, b ^ m1, b ^ m2, b ^ m1 ^ m2};
@@ -1068,13 +1114,14 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
 // out the dense two-qubit superoperator sweep, whose 16 amplitudes in registers would otherwise set the
 // register allocation (and the spills) of the whole stage kernel in FP64 and float-float; the host picks
 // that instantiation for stages without such a block.
+// blocks[0 .. be - bb) are the stage's block descriptors (in shared memory).
 template <class T, bool SUP2 = true>
 __device__ __forceinline__ void tile_blocks(cx<T>* __restrict__ sm, const cx<T>* __restrict__ csm,
                                             const uint8_t* __restrict__ fsm, int nbits,
                                             const TileBlock* __restrict__ blocks, int bb, int be,
                                             const BlockOp* __restrict__ sops, int op0) {
   for (int b = bb; b < be; b++) {
-    const TileBlock B = blocks[b];
+    const TileBlock B = blocks[b - bb];
     const BlockOp bo = sops[B.op_begin - op0];
     const cx<T>* c = csm + bo.coef;
     const uint8_t* f = fsm + bo.coef;
@@ -1181,7 +1228,9 @@ __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const 
   uint8_t* fsm = reinterpret_cast<uint8_t*>(sops + kOpCap);
   __shared__ uint32_t s_mir[kMirrorTable];
   __shared__ uint64_t s_io[3];
+  __shared__ TileBlock s_blk[kBlockCap];  // the stage's block descriptors, read by every thread for every tile
   stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
+  for (int i = threadIdx.x; i < be - bb && i < kBlockCap; i += kThreads) s_blk[i] = blocks[bb + i];
   __syncthreads();
   if (S.herm) {
     mirror_table(s_mir, s_bits, nbits);
@@ -1189,7 +1238,7 @@ __global__ void __launch_bounds__(256, 2) k_stage(cx<T>* __restrict__ st, const 
   }
   const uint64_t ntiles = stage_work_tiles(S);
   for (uint64_t u = blockIdx.x; u < ntiles; u += gridDim.x)
-    stage_tile<T, SUP2>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, S.herm != 0, u, blocks, bb, be, sops,
+    stage_tile<T, SUP2>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, S.herm != 0, u, s_blk, bb, be, sops,
                         S.op_begin, s_mir, s_io);
 }
 
@@ -1216,6 +1265,7 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
   __shared__ int s_rest[2 * VQD_MAX_QUBITS];
   __shared__ uint32_t s_mir[kMirrorTable];
   __shared__ uint64_t s_io[3];
+  __shared__ TileBlock s_blk[kBlockCap];
   int cur = -1;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1);
@@ -1229,6 +1279,8 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
       if (threadIdx.x < kMaxTileBits) s_bits[threadIdx.x] = S.bits[threadIdx.x];
       if (threadIdx.x < 2 * VQD_MAX_QUBITS) s_rest[threadIdx.x] = S.rest[threadIdx.x];
       stage_coefs<T>(csm, coef, fsm, flag, S.coef_begin, S.coef_end, sops, bops, S.op_begin, S.op_end);
+      for (int i = threadIdx.x; i < S.block_end - S.block_begin && i < kBlockCap; i += kThreads)
+        s_blk[i] = blocks[S.block_begin + i];
       __syncthreads();
       if (S.herm) {
         mirror_table(s_mir, s_bits, S.nbits);
@@ -1240,7 +1292,7 @@ __global__ void __launch_bounds__(256, 2) k_wave(cx<T>* __restrict__ all,
     const int nbits = S.nbits, nrest = S.nrest, op0 = S.op_begin;
     const bool herm = S.herm != 0;
     for (uint32_t t = W.tile_begin; t < W.tile_begin + W.tile_count; t++)
-      stage_tile<T, true>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, herm, t, blocks, S.block_begin,
+      stage_tile<T, true>(st, sm, csm, fsm, s_bits, nbits, s_rest, nrest, herm, t, s_blk, S.block_begin,
                           S.block_end, sops, op0, s_mir, s_io);
   }
 }

@@ -12,6 +12,7 @@ namespace vqd {
 constexpr int kMaxTileBits = 16;
 constexpr int kCoefCap = 2048;  // complex coefficients of one stage, staged in shared memory
 constexpr int kOpCap = 512;     // operator descriptors of one stage, staged in shared memory
+constexpr int kBlockCap = 64;   // blocks (shared-memory sweeps) of one stage, their descriptors staged in shared memory
 
 // Operator kinds inside a block on qubits (a, b); member index s = ra | rb << 1 | ca << 2 | cb << 3.
 enum BlockOpKind { BK_DIAG_A = 0, BK_SUP1_A, BK_DIAG_B, BK_SUP1_B, BK_DIAG2, BK_UNI2, BK_SUP2 };
