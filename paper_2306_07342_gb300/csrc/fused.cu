@@ -1057,37 +1057,56 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
       // sweep inline, and its leading stall was instruction fetch.  The swizzle is XOR-linear, so a member's
       // offset is the XOR of its bits' offsets: soff[r | cc << 2] = soff[r] ^ soff[cc << 2].
 #pragma unroll 1
-      for (int cc = 0; cc < 4; cc++) {
-        const uint32_t oc = ((cc & 1) ? soff[4] : 0u) ^ ((cc & 2) ? soff[8] : 0u);
-        cx<T> x[4];
+      for (int cc = 0; cc < 4; cc += 2) {  // two columns per iteration
+        const uint32_t oc0 = (cc & 2) ? soff[8] : 0u, oc1 = oc0 ^ soff[4];
+        cx<T> x0[4], x1[4];
 #pragma unroll
-        for (int m = 0; m < 4; m++) x[m] = sm[b ^ soff[m] ^ oc];
+        for (int m = 0; m < 4; m++) {
+          x0[m] = sm[b ^ soff[m] ^ oc0];
+          x1[m] = sm[b ^ soff[m] ^ oc1];
+        }
 #pragma unroll 1
         for (int r = 0; r < 4; r++) {
-          CAcc<T> t;
-          t.zero();
+          CAcc<T> t0, t1;
+          t0.zero();
+          t1.zero();
 #pragma unroll
-          for (int m = 0; m < 4; m++) t.mac(c[r * 4 + m], fl[r * 4 + m], x[m]);
-          sm[b ^ ((r & 1) ? soff[1] : 0u) ^ ((r & 2) ? soff[2] : 0u) ^ oc] = t.get();
+          for (int m = 0; m < 4; m++) {
+            const cx<T> cu = c[r * 4 + m];
+            const int fu = fl[r * 4 + m];
+            t0.mac(cu, fu, x0[m]);
+            t1.mac(cu, fu, x1[m]);
+          }
+          const uint32_t orr = ((r & 1) ? soff[1] : 0u) ^ ((r & 2) ? soff[2] : 0u);
+          sm[b ^ orr ^ oc0] = t0.get();
+          sm[b ^ orr ^ oc1] = t1.get();
         }
       }
 #pragma unroll 1
-      for (int r = 0; r < 4; r++) {
-        const uint32_t orr = ((r & 1) ? soff[1] : 0u) ^ ((r & 2) ? soff[2] : 0u);
-        cx<T> x[4];
+      for (int r = 0; r < 4; r += 2) {  // two rows per iteration
+        const uint32_t or0 = (r & 2) ? soff[2] : 0u, or1 = or0 ^ soff[1];
+        cx<T> x0[4], x1[4];
 #pragma unroll
-        for (int m = 0; m < 4; m++) x[m] = sm[b ^ orr ^ soff[m << 2]];
+        for (int m = 0; m < 4; m++) {
+          x0[m] = sm[b ^ or0 ^ soff[m << 2]];
+          x1[m] = sm[b ^ or1 ^ soff[m << 2]];
+        }
 #pragma unroll 1
         for (int cc = 0; cc < 4; cc++) {
-          CAcc<T> t;
-          t.zero();
+          CAcc<T> t0, t1;
+          t0.zero();
+          t1.zero();
 #pragma unroll
           for (int m = 0; m < 4; m++) {
             cx<T> uc = c[cc * 4 + m];
             uc.y = -uc.y;
-            t.mac(uc, fl[cc * 4 + m], x[m]);
+            const int fu = fl[cc * 4 + m];
+            t0.mac(uc, fu, x0[m]);
+            t1.mac(uc, fu, x1[m]);
           }
-          sm[b ^ orr ^ ((cc & 1) ? soff[4] : 0u) ^ ((cc & 2) ? soff[8] : 0u)] = t.get();
+          const uint32_t oc = ((cc & 1) ? soff[4] : 0u) ^ ((cc & 2) ? soff[8] : 0u);
+          sm[b ^ or0 ^ oc] = t0.get();
+          sm[b ^ or1 ^ oc] = t1.get();
         }
       }
     } else if constexpr (SUP2) {
