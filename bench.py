@@ -339,7 +339,7 @@ def roofline_hbm(stats, peak, peak_src, steps=1, exclude=("reduce", "init", "tc_
 DOT2_FP32_OPS = 12  # FP32 operations of one float-float multiply-add in the compensated dot product (dot2_step)
 
 
-def roofline_alu(stats, prec_name, fp32_fma, fp64_fma, kernel="fused_stage"):
+def roofline_alu(stats, prec_name, fp32_fma, fp64_fma, kernel="fused_stage", traffic_key=None):
     """The fused stage as an arithmetic-bound kernel: the real multiply-adds its sweeps perform (the library's
     count: structured for FP64 and float-float, dense complex FMAs for complex64) per second of device time,
     against the measured FMA rate of the pipe that executes them.  A float-float multiply-add (one step of the
@@ -356,7 +356,8 @@ def roofline_alu(stats, prec_name, fp32_fma, fp64_fma, kernel="fused_stage"):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "kernel": kernel, "peak_source": src, "launches": s["launches"],
             "avg_launch_ms": s["total_ms"] / s["launches"], "alg_fma_per_launch": s["alg_fma"] / s["launches"],
-            "traffic": None}
+            "alg_bytes_per_launch": s["alg_bytes"] / s["launches"],
+            "traffic": load_traffic(traffic_key) if traffic_key else None}
 
 
 def fp64_alu_roofline(stats, fma_rate):
@@ -940,7 +941,9 @@ def main():
     fp64_fma = vqd.vqd_measure_fma_rate(0, sh)
     fp32_fma = vqd.vqd_measure_fma_rate(1, sh)
     roof_hbm = roofline_hbm(stats, hbm_peak, peak_src)
-    roof_alu = roofline_alu(stats, args.prec, fp32_fma, fp64_fma) if args.path == "fused" else None
+    # DRAM bytes per launch from a committed ncu capture of this kernel (profiles/traffic.json), if current
+    tkey = f"fused_stage_{args.prec}" + ("_herm" if run_flags & vqd.VQD_HERMITIAN else "")
+    roof_alu = roofline_alu(stats, args.prec, fp32_fma, fp64_fma, traffic_key=tkey) if args.path == "fused" else None
     # the fused stage is bound by its arithmetic, not by HBM: its roofline is the arithmetic one
     roof = roof_alu if roof_alu else roof_hbm
     launches = int(sum(v["launches"] for v in stats.values()))
