@@ -245,3 +245,16 @@ def test_hermitian_plan_symmetric_tiles(vqd):
     with pytest.raises(vqd.VQDError) as e:
         vqd.vqd_plan_info(8, vqd.VQD_F64, small, flags=vqd.VQD_HERMITIAN, tile_bits=6, passenger_bits=2)
     assert e.value.code == vqd.VQD_EINVAL
+
+
+def test_plans_of_long_programs_respect_the_stage_budgets(vqd):
+    """Long random programs of every op kind plan without tripping the stage budgets' internal checks: at most
+    kCoefCap coefficients, kOpCap operators and 64 blocks (shared-memory sweeps) per stage, the planner splitting
+    larger stages; in every precision, general and Hermitian, over fusion widths."""
+    prog = random_program(4242, 8, 2000)
+    for prec in (vqd.VQD_F64, vqd.VQD_F32_SPLIT, vqd.VQD_F32):
+        for flags in (0, vqd.VQD_HERMITIAN):
+            for fuse in (2, 4, 6):
+                info = vqd.vqd_plan_info(8, prec, prog.ops, fuse_qubits=fuse, flags=flags)
+                assert info["native_ops"] == 2000 and 0 < info["stages"] <= 2000
+                assert info["blocks"] >= info["stages"]
