@@ -1010,7 +1010,7 @@ def main():
                     rec["autotuned"] = {k: tuned[k] for k in ("fuse_qubits", "tile_bits", "passenger_bits")}
                 if path == "fused":
                     rec["hermitian_stages"] = bool(fl & vqd.VQD_HERMITIAN)
-                if path == "fused" and nsteps > 1:
+                if path == "fused":  # per-class accounting from one more step, outside the timed region
                     st2 = profiled_step(torch, vqd, c2, s2)
                     rec["roofline"] = roofline_hbm(st2, hbm_peak, peak_src)
                     rec["roofline_alu"] = roofline_alu(st2, {vqd.VQD_F32: "f32", vqd.VQD_F64: "f64",
