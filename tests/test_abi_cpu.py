@@ -258,3 +258,24 @@ def test_plans_of_long_programs_respect_the_stage_budgets(vqd):
                 info = vqd.vqd_plan_info(8, prec, prog.ops, fuse_qubits=fuse, flags=flags)
                 assert info["native_ops"] == 2000 and 0 < info["stages"] <= 2000
                 assert info["blocks"] >= info["stages"]
+
+
+def test_autotuner_candidates_and_run_flags(vqd):
+    """Host logic of the autotuner (no GPU): with Hermitian stages allowed, the Hermitian shapes come first and the
+    general shapes follow; without, only the general ones; explicit 3-tuples take the caller's flag and 4-tuples keep
+    their own; the run flags set or clear VQD_HERMITIAN and keep every other bit."""
+    from paper_2306_07342_gb300 import autotune
+    for prec in (vqd.VQD_F64, vqd.VQD_F32, vqd.VQD_F32_SPLIT):
+        both = autotune._candidates(None, True, autotune.HERM_CANDIDATES[prec], autotune.CANDIDATES[prec])
+        assert both == [(*c, True) for c in autotune.HERM_CANDIDATES[prec]] + [(*c, False) for c in autotune.CANDIDATES[prec]]
+        gen = autotune._candidates(None, False, autotune.HERM_CANDIDATES[prec], autotune.CANDIDATES[prec])
+        assert gen == [(*c, False) for c in autotune.CANDIDATES[prec]]
+        for f, tb, p, h in both:
+            assert tb <= (13 if prec == vqd.VQD_F32 else 12) and 4 + p <= tb
+            if h:
+                assert 2 * (p + 2) <= (tb & ~1)        # a Hermitian tile has room for a two-qubit operator
+    assert autotune._candidates([(6, 12, 1)], True, [], []) == [(6, 12, 1, True)]
+    assert autotune._candidates([(6, 12, 1, False)], True, [], []) == [(6, 12, 1, False)]
+    extra = vqd.VQD_T2_IS_TOTAL
+    assert autotune._run_flags(extra, True) == extra | vqd.VQD_HERMITIAN
+    assert autotune._run_flags(extra | vqd.VQD_HERMITIAN, False) == extra
