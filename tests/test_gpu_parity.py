@@ -490,7 +490,8 @@ def test_ion15_full_size_sample_vs_oracle(vqd):
 
 def test_spin16_max_size_invariants_and_paths_agree(vqd):
     """16 qubits, the largest supported size (complex64 34.4 GB): the first 240 native ops of the spin-chain program
-    through the plain and the fused path; CPTP invariants and agreement of the two paths on sampled amplitudes."""
+    through the plain path, the fused path and the fused path with Hermitian stages (which must leave an exactly
+    Hermitian state); CPTP invariants and agreement of the paths on sampled amplitudes."""
     prog = config5_spin_chain()
     ops = prog.ops[:240]
     n = prog.n
@@ -498,13 +499,13 @@ def test_spin16_max_size_invariants_and_paths_agree(vqd):
     r, c = rng.integers(0, 2 ** n, 8192), rng.integers(0, 2 ** n, 8192)
     idx = r + (c << n)
     samples, reds = {}, {}
-    for path in ("plain", "fused"):
+    for path in ("plain", "fused", "fused_herm"):
         ctx = vqd.vqd_create(n, vqd.VQD_F32)
         try:
             if path == "plain":
                 vqd.vqd_apply_native(ctx, 0, ops)
             else:
-                vqd.vqd_run_program(ctx, 0, ops)
+                vqd.vqd_run_program(ctx, 0, ops, 0, vqd.VQD_HERMITIAN if path == "fused_herm" else 0)
             reds[path] = (vqd.vqd_trace(ctx, 0), vqd.vqd_purity(ctx, 0), vqd.vqd_prob(ctx, 0, [0, 7, 15]))
             flat = vqd.vqd_get_state(ctx, 0)
             samples[path] = flat[idx]
@@ -515,8 +516,11 @@ def test_spin16_max_size_invariants_and_paths_agree(vqd):
         tr, pur, pr = reds[path]
         assert abs(tr - 1) < 1e-4 and pur <= 1 + 1e-5 and herm < 1e-6
         assert abs(pr.sum() - tr.real) < 1e-9 and pr.min() > -1e-7
-    assert np.abs(samples["plain"] - samples["fused"]).max() < tol_f32(len(ops))
-    assert abs(reds["plain"][1] - reds["fused"][1]) < 1e-5
+        if path == "fused_herm":
+            assert herm == 0.0
+    for path in ("fused", "fused_herm"):
+        assert np.abs(samples["plain"] - samples[path]).max() < tol_f32(len(ops))
+        assert abs(reds["plain"][1] - reds[path][1]) < 1e-5
 
 
 # ---------------------------------------------------------------- tile shapes and the autotuner
