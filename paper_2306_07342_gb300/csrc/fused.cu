@@ -793,6 +793,8 @@ __device__ __forceinline__ void tile_store_diag(cx<T>* __restrict__ st, const cx
 
 // Structured arithmetic (coefficient flags, see compose_stage) for FP64 and float-float; complex64
 // keeps straight-line FMAs.
+// FP64 structured sweeps test a coefficient's complex case first (numeric.h, cmac_flag)
+template <class T> constexpr bool kCplxFirst = std::is_same<T, double>::value;
 template <class T> struct Structured { static constexpr bool value = true; };
 template <> struct Structured<float> { static constexpr bool value = false; };
 
@@ -966,8 +968,8 @@ __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, cons
             cx<T> x0 = sm[a0[t]], x1 = sm[a1[t]];
             const cx<T> ct = c[t];
             const int ft = fl[t];
-            cscale_flag<T>(x0, ct, ft);
-            cscale_flag<T>(x1, ct, ft);
+            cscale_flag<T, kCplxFirst<T>>(x0, ct, ft);
+            cscale_flag<T, kCplxFirst<T>>(x1, ct, ft);
             sm[a0[t]] = x0;
             sm[a1[t]] = x1;
           }
@@ -1006,7 +1008,7 @@ __device__ __forceinline__ void sweep1_s(cx<T>* __restrict__ sm, int nbits, cons
       for (int t = 0; t < 4; t++)
         if (!(skip >> t & 1u)) {
           cx<T> x = sm[a[t]];
-          cscale_flag<T>(x, c[t], fl[t]);
+          cscale_flag<T, kCplxFirst<T>>(x, c[t], fl[t]);
           sm[a[t]] = x;
         }
     } else {
@@ -1048,7 +1050,7 @@ __device__ __forceinline__ void sweep2_s(cx<T>* __restrict__ sm, int nbits, cons
           const uint32_t o = ((s & 1) ? soff[1] : 0u) ^ ((s & 2) ? soff[2] : 0u) ^ ((s & 4) ? soff[4] : 0u) ^
                              ((s & 8) ? soff[8] : 0u);
           cx<T> x = sm[b ^ o];
-          cscale_flag<T>(x, c[s], fl[s]);
+          cscale_flag<T, kCplxFirst<T>>(x, c[s], fl[s]);
           sm[b ^ o] = x;
         }
     } else if (kind == BK_UNI2) {

@@ -11,6 +11,7 @@
 // one FMA chain).  The CUDA sources are compiled without fast-math, so no float operation below is
 // reassociated.
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -85,9 +86,18 @@ template <> struct V2<double> { using t = double2; };
 template <> struct V2<df> { using t = cdf; };
 template <class T> using cx = typename V2<T>::t;
 
-// acc += c x for a coefficient of structure fl
-template <class T>
+// acc += c x for a coefficient of structure fl.  CPLX_FIRST tests the complex case first: most terms of a
+// composed (fused) operator are complex, and the FP64 fused sweeps measured 10% faster so; the plain FP64
+// passes and the float-float accumulator below measured faster with the complex case last.
+template <class T, bool CPLX_FIRST = false>
 __device__ __forceinline__ void cmac_flag(cx<T>& acc, const cx<T>& c, int fl, const cx<T>& x) {
+  if (CPLX_FIRST && fl == FL_CPLX) {
+    acc.x = fma(c.x, x.x, acc.x);
+    acc.x = fma(-c.y, x.y, acc.x);
+    acc.y = fma(c.x, x.y, acc.y);
+    acc.y = fma(c.y, x.x, acc.y);
+    return;
+  }
   if (fl == FL_ZERO) return;
   if (fl == FL_ONE) { acc.x += x.x; acc.y += x.y; return; }
   if (fl == FL_REAL) { acc.x = fma(c.x, x.x, acc.x); acc.y = fma(c.x, x.y, acc.y); return; }
@@ -98,9 +108,15 @@ __device__ __forceinline__ void cmac_flag(cx<T>& acc, const cx<T>& c, int fl, co
   acc.y = fma(c.y, x.x, acc.y);
 }
 
-// x <- f x for a diagonal factor of structure fl (FL_ONE leaves x as it is)
-template <class T>
+// x <- f x for a diagonal factor of structure fl (FL_ONE leaves x as it is); CPLX_FIRST as in cmac_flag
+template <class T, bool CPLX_FIRST = false>
 __device__ __forceinline__ void cscale_flag(cx<T>& x, const cx<T>& f, int fl) {
+  if (CPLX_FIRST && fl == FL_CPLX) {
+    const T re = fma(x.x, f.x, -(x.y * f.y));
+    x.y = fma(x.x, f.y, x.y * f.x);
+    x.x = re;
+    return;
+  }
   if (fl == FL_ONE) return;
   if (fl == FL_ZERO) { x.x = T(0.0f); x.y = T(0.0f); return; }
   if (fl == FL_REAL) { x.x = x.x * f.x; x.y = x.y * f.x; return; }
@@ -121,7 +137,9 @@ template <class T>
 struct CAcc {
   cx<T> v;
   __device__ __forceinline__ void zero() { v.x = T(0.0f); v.y = T(0.0f); }
-  __device__ __forceinline__ void mac(const cx<T>& c, int fl, const cx<T>& x) { cmac_flag<T>(v, c, fl, x); }
+  __device__ __forceinline__ void mac(const cx<T>& c, int fl, const cx<T>& x) {
+    cmac_flag<T, std::is_same<T, double>::value>(v, c, fl, x);
+  }
   __device__ __forceinline__ cx<T> get() const { return v; }
 };
 
