@@ -279,3 +279,15 @@ def test_autotuner_candidates_and_run_flags(vqd):
     extra = vqd.VQD_T2_IS_TOTAL
     assert autotune._run_flags(extra, True) == extra | vqd.VQD_HERMITIAN
     assert autotune._run_flags(extra | vqd.VQD_HERMITIAN, False) == extra
+
+
+def test_single_tile_states_plan_the_same_with_or_without_hermitian_stages(vqd):
+    """A state whose whole index fits one tile (2n <= 12 bits: n <= 6) is planned on whole-state tiles (split only
+    by the per-stage coefficient and block budgets), in every precision; VQD_HERMITIAN changes nothing there (a
+    single tile is its own mirror)."""
+    for n in (1, 3, 6):
+        prog = random_program(600 + n, n, 80)
+        for prec in (vqd.VQD_F64, vqd.VQD_F32_SPLIT, vqd.VQD_F32):
+            gen = vqd.vqd_plan_info(n, prec, prog.ops)
+            herm = vqd.vqd_plan_info(n, prec, prog.ops, flags=vqd.VQD_HERMITIAN)
+            assert gen["max_tile_bits"] == 2 * n and gen == herm, (n, prec, gen, herm)
